@@ -1,0 +1,155 @@
+"""Pins of the oracle's CEM stages (Alg. 1, eqs. update_mean /
+update_covariance): elite selection vs brute force, refit special cases vs
+textbook statistics, Cholesky vs LAPACK, the host Gaussian stream's
+statistics, and the composition of Alg. 1.  No GPU."""
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from paper_2309_08235_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def brute_select(r, c, n_proj, n_elite):
+    idx = sorted(range(len(r)), key=lambda i: (r[i], i))[:n_proj]
+    return np.array(idx), np.array(sorted(idx, key=lambda i: (c[i], i))[:n_elite])
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_select_matches_brute_force(oracle, seed):
+    rng = np.random.default_rng(seed)
+    N = int(rng.integers(2, 17))
+    # coarse values so ties are common
+    r = rng.integers(0, 4, N).astype(float) * 0.25
+    c = rng.integers(0, 5, N).astype(float)
+    n_proj = int(rng.integers(1, N + 1))
+    n_elite = int(rng.integers(1, n_proj + 1))
+    pi, ei = oracle.select(r, c + r, n_proj, n_elite)
+    bp, be = brute_select(r, c + r, n_proj, n_elite)
+    np.testing.assert_array_equal(pi, bp)
+    np.testing.assert_array_equal(ei, be)
+
+
+def test_select_paper_counts(oracle):
+    g = json.load(open(os.path.join(GOLDEN, "paper_parameters.json")))
+    rng = np.random.default_rng(0)
+    r = rng.random(g["n_samples"])
+    c = rng.random(g["n_samples"]) * 10
+    pi, ei = oracle.select(r, c + r, g["n_proj"], g["n_elite"])
+    assert len(set(pi)) == g["n_proj"] and len(set(ei)) == g["n_elite"]
+    assert set(ei) <= set(pi)
+    # every ConstraintEliteSet member has r no larger than any excluded sample
+    assert r[pi].max() <= np.delete(r, pi).min()
+
+
+def test_refit_textbook_limits(oracle):
+    rng = np.random.default_rng(1)
+    el = rng.normal(size=(30, 7))
+    c = rng.random(30)
+    mu0 = rng.normal(size=7)
+    cov0 = np.eye(7)
+    # sigma = 1, gamma -> inf: plain mean and (biased) covariance of the elites
+    mu, cov = oracle.refit(el, c, mu0, cov0, 1.0, 1e300)
+    np.testing.assert_allclose(mu, el.mean(0), atol=1e-13)
+    np.testing.assert_allclose(cov, np.cov(el.T, bias=True), atol=1e-12)
+    # sigma = 0 leaves the distribution unchanged
+    mu, cov = oracle.refit(el, c, mu0, cov0, 0.0, 1.0)
+    np.testing.assert_array_equal(mu, mu0)
+    np.testing.assert_array_equal(cov, cov0)
+    # identical elites with sigma = 1 collapse the covariance
+    same = np.repeat(el[:1], 5, 0)
+    mu, cov = oracle.refit(same, c[:5], mu0, cov0, 1.0, 1.0)
+    np.testing.assert_allclose(mu, el[0], atol=1e-14)
+    np.testing.assert_allclose(cov, 0.0, atol=1e-14)
+
+
+def test_refit_weights_favour_low_cost(oracle):
+    """Two elites: weights exp(-(c - min c)/gamma), the best gets weight 1."""
+    a, b = np.array([[1.0, 0.0]]), np.array([[0.0, 1.0]])
+    el = np.vstack([a, b])
+    c = np.array([0.0, np.log(3.0)])   # w = (1, 1/3)
+    mu, cov = oracle.refit(el, c, np.zeros(2), np.zeros((2, 2)), 1.0, 1.0)
+    np.testing.assert_allclose(mu, [0.75, 0.25], atol=1e-15)
+    d = el - mu
+    want = (1.0 * np.outer(d[0], d[0]) + (1 / 3) * np.outer(d[1], d[1])) / (4 / 3)
+    np.testing.assert_allclose(cov, want, atol=1e-15)
+
+
+def test_refit_covariance_is_symmetric_psd(oracle):
+    rng = np.random.default_rng(2)
+    el = rng.normal(size=(20, 22))
+    mu, cov = oracle.refit(el, rng.random(20) * 5, rng.normal(size=22), np.eye(22) * 4, 0.5, 1.0)
+    np.testing.assert_allclose(cov, cov.T, atol=1e-14)
+    assert np.linalg.eigvalsh(cov).min() > -1e-12
+
+
+def test_cholesky_against_lapack(oracle):
+    rng = np.random.default_rng(3)
+    for D in (1, 5, 22, 33):
+        X = rng.normal(size=(D + 3, D))
+        S = X.T @ X + 1e-3 * np.eye(D)
+        L = oracle.cholesky(S)
+        np.testing.assert_allclose(L, np.linalg.cholesky(S), rtol=1e-12, atol=1e-13)
+        assert np.abs(L @ L.T - S).max() <= 1e-13 * np.abs(S).max()
+    with pytest.raises(oracle.OracleError):
+        oracle.cholesky(np.diag([1.0, -1.0, 2.0]))
+
+
+def test_rng_stream_statistics(oracle):
+    z = oracle.rng_normal(12345, 200_000)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # deterministic, and a prefix of a longer draw
+    np.testing.assert_array_equal(z[:1001], oracle.rng_normal(12345, 1001))
+    assert not np.array_equal(z[:100], oracle.rng_normal(12346, 100))
+    # consecutive pairs are uncorrelated (Box-Muller cos / sin halves)
+    assert abs(np.corrcoef(z[0::2], z[1::2])[0, 1]) < 0.01
+
+
+def test_plan_composes_alg1(oracle):
+    """orc_plan equals Alg. 1 assembled from the oracle's own stage functions."""
+    p = W.scene_small_2d(n_obs=6, n_p=30)
+    cem = W.cem_settings(24, 8, 3, n_proj=16, n_elite=5)
+    D = 22
+    z = W.normals(9, (cem["cem_iters"], cem["n_samples"], D))
+    got = oracle.plan(p, cem, z=z)
+    mu = oracle.default_mean(p)
+    cov = np.eye(D) * cem["init_std"] ** 2
+    for l in range(cem["cem_iters"]):
+        S = cov + cem["chol_eps"] * np.trace(cov) / D * np.eye(D)
+        L = oracle.cholesky(S)
+        xi = mu + z[l] @ L.T
+        xb, _ = oracle.project(p, xi, cem["proj_iters"])
+        r, c1 = oracle.residual_cost(p, xb)
+        _, ei = oracle.select(r, c1 + r, cem["n_proj"], cem["n_elite"])
+        mu, cov = oracle.refit(xb[ei], (c1 + r)[ei], mu, cov, cem["sigma_lr"], cem["gamma"])
+    np.testing.assert_allclose(got["best"], xb[ei[0]], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(got["elites"], ei)
+    np.testing.assert_allclose(got["mu"], mu, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got["cov"], cov, rtol=1e-11, atol=1e-12)
+    assert got["r"] == pytest.approx(r[ei[0]], abs=1e-12)
+    # with z = None the oracle draws from its own stream
+    zz = oracle.rng_normal(77, cem["cem_iters"] * cem["n_samples"] * D)
+    a = oracle.plan(p, cem, seed=77)
+    b = oracle.plan(p, cem, z=zz)
+    np.testing.assert_array_equal(a["best"], b["best"])
+
+
+def test_plan_teaser_scene_finds_collision_free(oracle):
+    """Fig. teaser: with every initial sample inside the obstacle, PRIEST returns
+    a trajectory that clears it (paper's N_b / N_proj / N_elite, fewer iters)."""
+    from test_oracle_projection import teaser_problem
+
+    g = json.load(open(os.path.join(GOLDEN, "paper_parameters.json")))
+    p = teaser_problem(n_p=60)
+    cem = W.cem_settings(g["n_samples"], 30, 4, n_proj=g["n_proj"], n_elite=g["n_elite"])
+    cem["init_std"] = 1.0
+    out = oracle.plan(p, cem, seed=3)
+    r, _ = oracle.residual_cost(p, out["best"][None])
+    mu_r, _ = oracle.residual_cost(p, oracle.project_eq(p, oracle.default_mean(p)[None]))
+    assert mu_r[0] > 1.0
+    assert r[0] < 0.05 * mu_r[0]
