@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the PRIEST hot path on GB300: projected sample-iterations per
+second of full solves (Alg. 1: sample, K projection iterations, residual and
+cost, elites, refit, Cholesky) on the 2-D clutter workload.
+
+One step = one full solve of one problem: N = 1000 samples, n_p = 100 time
+stamps, 90 static + 10 moving circles in a 30 x 30 m box, degree 10,
+K = 100 projection iterations, L = 5 CEM iterations, 100 elites, FP32
+projection (FP64 sampling / refit / Cholesky / KKT block).  Units per step:
+N * K * L = 5e5 projected sample-iterations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica (no collective on the data
+path); rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "clutter2d_fp32"
+METRIC = "projected sample-iters/s; solves/s & p99 latency vs plain GPU path, at oracle tol"
+UNIT = "sample-iters/s"
+N_SM = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+
+
+def workload_desc(p, cem):
+    return (f"2-D clutter: {p['n_obs'] - int(np.count_nonzero(np.abs(p['vel']).sum(1)))} static + "
+            f"{int(np.count_nonzero(np.abs(p['vel']).sum(1)))} moving circles in 30x30 m, "
+            f"N={cem['n_samples']} samples, n_p={p['n_p']}, degree {p['degree']}, "
+            f"K={cem['proj_iters']} projection iters, L={cem['cem_iters']} CEM iters, "
+            f"{cem['n_elite']} elites, FP32 projection")
+
+
+def flops_per_sample_iter(p, nf=5):
+    """Algorithmic FP32 flops of one projected sample-iteration (FMA = 2):
+    7 per (point, obstacle) pair (2 differences, scaled squared distance,
+    activity test; the work of the rare active pairs is not counted), plus per
+    point the trajectory evaluation and the transposed basis product on the
+    free coefficients (2 x 3 x dims x nf FMA) and the velocity / acceleration
+    tests (~10), plus the shared-inverse step (2 nf^2 FMA per axis)."""
+    dims, n_p, n_o = p["dims"], p["n_p"], p["n_obs"]
+    pair = 7 if dims == 2 else 11
+    per_point = 2 * (2 * 3 * dims * nf) + 10
+    return n_p * n_o * pair + n_p * per_point + dims * 2 * 2 * nf * nf
+
+
+def fp32_peak_tflops():
+    return N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.device)], stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        busy = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[6 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def cpu_oracle_rate(p, cem, n_samples, seed=0):
+    """Projected sample-iterations/s of the FP64 oracle (single thread) on
+    n_samples samples of the workload (K projection iterations + residual)."""
+    import oracle as O
+    from paper_2309_08235_gb300 import workloads as W
+
+    O.build()
+    D = p["dims"] * (p["degree"] + 1)
+    xi = O.default_mean(p) + cem["init_std"] * W.normals(seed, (n_samples, D))
+    t0 = time.perf_counter()
+    xb, _ = O.project(p, xi, cem["proj_iters"])
+    O.residual_cost(p, xb)
+    dt = time.perf_counter() - t0
+    return n_samples * cem["proj_iters"] / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2309_08235_gb300 import workloads as W
+
+    p, cem = W.workload(WORKLOAD)
+    # calibrate, then size each step so the whole run stays within ~2 minutes
+    rate, _ = cpu_oracle_rate(p, dict(cem, proj_iters=10), 1)
+    per_step_s = 120.0 / max(1, args.steps + args.warmup)
+    m = max(1, int(per_step_s * rate / cem["proj_iters"]))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(p, cem, m)
+    times = []
+    for k in range(args.steps):
+        _, dt = cpu_oracle_rate(p, cem, m, seed=k + 1)
+        times.append(dt)
+    units = m * cem["proj_iters"]
+    value = units * len(times) / sum(times)
+    sample = (f"{m} samples x {cem['proj_iters']} projection iterations (+ residual/cost) of the "
+              f"{WORKLOAD} workload per step, FP64 oracle, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(p, cem), "impl": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2309_08235_gb300 import build as B
+    from paper_2309_08235_gb300 import priest as P
+    from paper_2309_08235_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    B.build()
+    p, cem = W.workload(WORKLOAD)
+    N, K, L = cem["n_samples"], cem["proj_iters"], cem["cem_iters"]
+    D = p["dims"] * (p["degree"] + 1)
+    units = N * K * L
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = P.Context(p, cem, precision=P.PRIEST_FP32, stream=stream.cuda_stream)
+    prob, keep = P.make_problem(p, cem)
+    h = P.priest_load(ctx.h, prob)
+    z_host = torch.from_numpy(W.normals(1000 + rank, (L, N, D))).pin_memory()
+    z_dev = z_host.to(dev)
+    out = torch.zeros(D + 4, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        P.priest_plan_device(ctx.h, h, z_dev.data_ptr(), out.data_ptr())
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+    stream.synchronize()
+    P.priest_sync(ctx.h)
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    P.priest_profile_read(ctx.h)
+    P.priest_profile_enable(ctx.h, 1)
+    l0 = ctx.launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            step()
+            e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    P.priest_profile_enable(ctx.h, 0)
+    launches = ctx.launches() - l0
+    n_proj_launch, proj_ms = P.priest_profile_read(ctx.h)
+    P.priest_sync(ctx.h)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units * args.steps * world / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the fused projection)
+    avg_proj_ms = proj_ms / max(1, n_proj_launch)
+    flops_launch = flops_per_sample_iter(p) * N * K
+    achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops()
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof_path):
+        try:
+            traffic = json.load(open(prof_path)).get("project_kernel_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "project_kernel<float,2,4>",
+                "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
+                "flops_per_launch": flops_launch,
+                "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
+
+    # ---- end to end through the host-pointer C ABI (pinned z in, result out)
+    res = P.priest_result()
+    z_np = z_host.numpy()
+    for _ in range(2):
+        P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
+    e2e_steps = max(3, min(args.steps, 50))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    obs_bytes = 8 * (p["n_obs"] * (2 * p["dims"] + 2))
+    e2e = {"value": units * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(z_np.nbytes + obs_bytes),
+           "d2h_bytes_per_step": int(8 * (D + 4 + D)),
+           "api": "priest_plan_z (host buffers, blocking)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(p, cem), "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "units_per_step": units},
+            "solves_per_s": args.steps * world / (total_ms / 1e3),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(p, cem, args.cpu_samples)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_samples} samples x {K} projection iterations (+ residual/cost) "
+                                          f"of the same workload, FP64 oracle, 1 thread, {dt:.1f} s"}
+    P.priest_unload(ctx.h, h)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-samples", type=int, default=160)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * priest.h -- C ABI of the GB300 (sm_103a) PRIEST library.
+ *
+ * PRIEST (Rastgar et al., "PRIEST: Projection Guided Sampling-Based
+ * Optimization for Autonomous Navigation", arXiv 2309.08235) draws Gaussian
+ * samples of Bernstein trajectory coefficients, pushes every sample towards
+ * the feasible set with a batched projection (alternating minimisation over
+ * polar-form obstacle / velocity / acceleration residuals and one shared KKT
+ * inverse, Sec. III-A and Appendix), scores the projected samples, keeps
+ * elites and refits the sampling distribution (Alg. 1, eqs. update_mean /
+ * update_covariance).  Every step of that path runs in CUDA kernels for
+ * sm_103a; there is no CPU fallback: a missing or unusable GPU is reported
+ * as PRIEST_ERR_CUDA.
+ *
+ * Conventions shared by all entry points
+ *   - Coefficients of one sample are stored axis-major:
+ *     [c_x(0..n_v-1), c_y(0..n_v-1), (c_z(0..n_v-1))], D = dims * n_v,
+ *     n_v = degree + 1; batches are row-major N x D, FP64 at the boundary.
+ *   - Host pointers are read (or written) during the call only and remain
+ *     owned by the caller.  Device memory used internally is owned by the
+ *     context.  Entry points named *_device take device pointers owned by the
+ *     caller and run asynchronously on the context's stream.
+ *   - Errors are returned as priest_status; nothing is thrown across the ABI.
+ *     priest_last_error() gives a message for the last failure of a context.
+ *   - A context is used by one host thread at a time, except priest_submit /
+ *     priest_poll, which lock internally.
+ */
+#ifndef PRIEST_H
+#define PRIEST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PRIEST_MAX_DIMS 3
+#define PRIEST_MAX_NV 16        /* degree <= 15 */
+#define PRIEST_MAX_D 48         /* PRIEST_MAX_DIMS * PRIEST_MAX_NV */
+#define PRIEST_MAX_NP 512       /* time stamps per trajectory */
+#define PRIEST_MAX_OBS 2048     /* obstacles per problem */
+#define PRIEST_MAX_SAMPLES 8192 /* N_b per problem */
+#define PRIEST_MAX_ELITE 1024
+
+typedef enum {
+    PRIEST_OK = 0,
+    PRIEST_PENDING = 1,        /* priest_poll: request not finished yet */
+    PRIEST_ERR_INVALID = -1,   /* rejected argument (sizes, NaN, radius <= 0, ...) */
+    PRIEST_ERR_NOMEM = -2,     /* device allocation failed */
+    PRIEST_ERR_BUDGET = -3,    /* request does not fit the context's HBM budget */
+    PRIEST_ERR_CUDA = -4,      /* CUDA runtime error or no usable GPU */
+    PRIEST_ERR_TIMEOUT = -5,   /* a bounded wait gave up */
+    PRIEST_ERR_NUMERIC = -6    /* non-positive pivot in a Cholesky / KKT factor, NaN */
+} priest_status;
+
+typedef enum {
+    PRIEST_FP64_CHECK = 0,     /* every step in FP64 (parity mode) */
+    PRIEST_FP32 = 1,           /* projection in FP32, sampling / refit / Cholesky / KKT in FP64 */
+    PRIEST_MIXED_BF16 = 2      /* reserved: BF16 basis products, FP32 final sweep */
+} priest_precision;
+
+typedef struct priest_ctx priest_ctx;
+typedef struct priest_loaded priest_loaded;
+
+/* Context-wide settings and defaults (Alg. 1 and Sec. V-A constants; the
+ * constants the paper leaves open are fields). */
+typedef struct {
+    int dims;              /* 2 or 3 (default for problems that give 0) */
+    int degree;            /* Bernstein degree n, 5..15; n_v = n + 1 */
+    int n_p;               /* time stamps (default) */
+    double horizon;        /* T_h in seconds (default) */
+    double rho;            /* augmented-Lagrangian weight of eq. lagrange */
+    int proj_iters;        /* K projection iterations per CEM iteration */
+    int cem_iters;         /* L CEM iterations (the paper's N) */
+    int n_samples;         /* N_b (default) */
+    int n_proj;            /* N_proj (default; 0 -> floor(80 N_b / 110)) */
+    int n_elite;           /* N_elite (default; 0 -> N_b / 10) */
+    double sigma_lr;       /* sigma of eqs. update_mean / update_covariance */
+    double gamma;          /* temperature of the refit weights */
+    double chol_eps;       /* Cholesky jitter, relative: Sigma + chol_eps tr(Sigma)/D I */
+    double init_std;       /* default Sigma_0 = init_std^2 I */
+    double vmax, amax;     /* velocity / acceleration bounds (default) */
+    int use_bounds;        /* workspace bounds G xi <= tau (eq. bound_con) */
+    double smin[3], smax[3];
+    int precision;         /* priest_precision */
+    size_t hbm_budget;     /* bytes the serving loop may hold on the device; 0 = no limit */
+} priest_config;
+
+/* One planning problem (Sec. II-A: eqs. acc_cost .. coll_multiagent). */
+typedef struct {
+    int n_obs;
+    const double *center;  /* n_obs x dims, obstacle centres at t = 0 */
+    const double *vel;     /* n_obs x dims, constant velocities (NULL = static) */
+    const double *semi;    /* n_obs x 2: semi-axes (a, b) of an (a, a, b) ellipsoid; 2-D uses a */
+    double b0[3][3];       /* [axis][q]: start position, velocity, acceleration */
+    double bf[3][3];       /* [axis][q]: final values */
+    int bc_final_mask;     /* bit q: q-th derivative fixed at t_f; 1, 3 or 7 (0 = free end) */
+    uint64_t seed;         /* seed of the host Gaussian stream (priest_plan, priest_submit) */
+    int64_t robot_id;      /* >= 0: warm-start key for priest_submit; -1: none */
+    /* per-problem overrides; 0 keeps the context default */
+    int dims, n_p, n_samples, n_proj, n_elite;
+    double horizon, vmax, amax;
+} priest_problem;
+
+/* Result of one solve. */
+typedef struct {
+    int status;            /* priest_status of the solve */
+    int D;                 /* coefficients per sample */
+    int best_index;        /* sample index of the returned trajectory in the last iteration */
+    double xi_best[PRIEST_MAX_D]; /* Alg. 1 output: lowest c_aug member of the last EliteSet */
+    double resid;          /* r(xi_best) */
+    double cost;           /* c_1(xi_best): summed squared acceleration */
+    double c_aug;          /* cost + resid */
+    double mu[PRIEST_MAX_D]; /* sampling mean after the last refit */
+    double latency_ms;     /* priest_poll: submit-to-completion time */
+} priest_result;
+
+/* Creates a context bound to the current CUDA device.  cuda_stream: a
+ * cudaStream_t to run on, or NULL for a stream the context creates and owns.
+ * Errors: PRIEST_ERR_INVALID (bad config), PRIEST_ERR_CUDA (no usable GPU). */
+priest_status priest_create(const priest_config *cfg, void *cuda_stream, priest_ctx **out);
+
+/* Waits for outstanding work, stops the serving worker and frees everything
+ * the context owns.  NULL is accepted. */
+priest_status priest_destroy(priest_ctx *ctx);
+
+/* Message of the context's last failure ("" if none).  Valid until the next call. */
+const char *priest_last_error(const priest_ctx *ctx);
+
+/* Projection only (Sec. III-A; Appendix eqs. comp_alpha .. comp_zeta):
+ * xi_bar^0 = Pi_A(xi) (the boundary-condition coefficients set exactly),
+ * lambda^0 = lambda_io (or 0 if NULL), then cfg.proj_iters alternating-
+ * minimisation iterations, then r and c_1 of the result (Alg. 1 residual and
+ * cost).  xi: n x D (host, read); lambda_io: n x D (host, updated) or NULL;
+ * xi_bar_out: n x D (host, written); resid_out, cost_out: n (host) or NULL.
+ * n may be 0.  Blocks until done. */
+priest_status priest_project(priest_ctx *ctx, const priest_problem *prob, int n, const double *xi,
+                             double *lambda_io, double *xi_bar_out, double *resid_out,
+                             double *cost_out);
+
+/* Full solve (Alg. 1): L CEM iterations of sample -> project -> residual/cost
+ * -> ConstraintEliteSet -> EliteSet -> refit, Gaussian draws from the host
+ * stream seeded by prob->seed (see priest_rng_normal).  mu0 (D) and cov0
+ * (D x D) may be NULL: straight-line Bernstein mean and init_std^2 I.
+ * Blocks until done. */
+priest_status priest_plan(priest_ctx *ctx, const priest_problem *prob, const double *mu0,
+                          const double *cov0, priest_result *out);
+
+/* As priest_plan with the standard-normal draws given explicitly:
+ * z is L x N x D (host, read). */
+priest_status priest_plan_z(priest_ctx *ctx, const priest_problem *prob, const double *mu0,
+                            const double *cov0, const double *z, priest_result *out);
+
+/* Serving: enqueue a solve (inputs copied before return) and get a ticket.
+ * The worker admits requests while their device memory fits cfg.hbm_budget,
+ * runs admitted requests together, and keeps per robot_id warm-start state
+ * (the last mean / covariance) on the device; a request with a known
+ * robot_id starts from it.  Errors: PRIEST_ERR_INVALID,
+ * PRIEST_ERR_BUDGET (a single request larger than the budget). */
+priest_status priest_submit(priest_ctx *ctx, const priest_problem *prob, uint64_t *ticket);
+
+/* PRIEST_PENDING until the ticket's solve is done, then its result (and the
+ * ticket is released).  PRIEST_ERR_INVALID for an unknown ticket. */
+priest_status priest_poll(priest_ctx *ctx, uint64_t ticket, priest_result *out);
+
+/* The host Gaussian stream used by priest_plan: SplitMix64 (Steele, Lea,
+ * Flood 2014) seeded with `seed`, 53-bit uniforms u = (x >> 11) 2^-53,
+ * Box-Muller on (1 - u1, u2) giving cos then sin.  count >= 0 values.
+ * Host-only; needs no GPU. */
+priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out);
+
+/* Device-resident problems for callers that keep inputs in HBM.
+ * priest_load copies the problem (obstacles, boundary values) to device
+ * memory owned by the returned handle and sizes its work buffers. */
+priest_status priest_load(priest_ctx *ctx, const priest_problem *prob, priest_loaded **out);
+priest_status priest_unload(priest_ctx *ctx, priest_loaded *h);
+
+/* Full solve of a loaded problem, asynchronous on the context stream.
+ * z_dev: L x N x D standard normals in device memory (caller-owned).
+ * out_dev: device buffer of D + 4 doubles, written with
+ * [xi_best (D), resid, cost, c_aug, best_index]. */
+priest_status priest_plan_device(priest_ctx *ctx, priest_loaded *h, const double *z_dev,
+                                 double *out_dev);
+
+/* Projection of n caller-provided samples of a loaded problem, asynchronous
+ * on the context stream; device pointers as in priest_project. */
+priest_status priest_project_device(priest_ctx *ctx, priest_loaded *h, int n, const double *xi_dev,
+                                    double *lambda_dev, double *xi_bar_dev, double *resid_dev,
+                                    double *cost_dev);
+
+/* Waits for the context stream and reports any kernel-side error status. */
+priest_status priest_sync(priest_ctx *ctx);
+
+/* Number of kernels this context has launched so far (instrumentation). */
+int64_t priest_kernel_launches(const priest_ctx *ctx);
+
+/* Instrumentation: while enabled, every projection-kernel launch of the
+ * context is bracketed by CUDA events recorded on the stream it runs on.
+ * priest_profile_read waits for those events and returns how many launches
+ * were bracketed and their summed device time in milliseconds, then clears
+ * the record.  Off by default; enabling it adds two event records per launch. */
+priest_status priest_profile_enable(priest_ctx *ctx, int enable);
+priest_status priest_profile_read(priest_ctx *ctx, int64_t *launches, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,925 @@
+// api.cu -- the C ABI of priest.h: contexts, validation, device-resident
+// problems, the plan / project pipelines (Alg. 1 as a sequence of kernel
+// launches on one stream), the host Gaussian stream and the serving worker.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "priest_internal.cuh"
+
+using namespace priest;
+
+// ---------------------------------------------------------------------------
+// Device-resident problem: one allocation carved into all buffers of a solve.
+// ---------------------------------------------------------------------------
+struct priest_loaded {
+    Shape sh;
+    void *block = nullptr;
+    size_t bytes = 0;
+    double *center = nullptr, *vel = nullptr, *semi = nullptr;
+    double *tab64 = nullptr;
+    float *tab32 = nullptr;
+    double *cB = nullptr;
+    double *mu = nullptr, *cov = nullptr, *L = nullptr, *mu_new = nullptr;
+    double *xb = nullptr, *r = nullptr, *c1 = nullptr;
+    int *elite = nullptr;
+    double *out = nullptr;
+    unsigned *counter = nullptr;
+    double *z = nullptr;    // L x N x D (host-driven solves)
+    double *xi = nullptr;   // N x D (host-driven projections)
+    double *lam = nullptr;  // N x D
+    bool default_mu = true, default_cov = true;
+};
+
+struct ServeRequest {
+    uint64_t ticket;
+    Shape sh;
+    std::vector<double> center, vel, semi;
+    uint64_t seed;
+    int64_t robot_id;
+    std::chrono::steady_clock::time_point t_submit;
+    size_t bytes;
+};
+
+struct WarmState {
+    int D = 0;
+    std::vector<double> mu, cov;
+};
+
+struct priest_ctx {
+    priest_config cfg;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, n_sm = 0;
+    int *d_status = nullptr;
+    std::string err;
+    std::atomic<int64_t> launches{0};
+    priest_loaded *scratch = nullptr;  // reused by the host-pointer entry points
+    // serving
+    std::mutex mu_q;
+    std::condition_variable cv;
+    std::deque<ServeRequest> queue;
+    std::unordered_map<uint64_t, priest_result> done;
+    std::unordered_map<int64_t, WarmState> warm;
+    std::thread worker;
+    bool stop = false, worker_started = false;
+    uint64_t next_ticket = 1;
+    size_t in_flight_bytes = 0;
+    cudaStream_t serve_stream = nullptr;
+    int *serve_status = nullptr;
+    // instrumentation
+    bool profile = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_used, prof_free;
+};
+
+namespace {
+
+priest_status fail(priest_ctx *ctx, priest_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+priest_status cuda_fail(priest_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, PRIEST_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PRIEST_CUDA(ctx, call)                                      \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
+    } while (0)
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+// Resolves the shape of a problem against the context defaults and checks it.
+priest_status resolve(priest_ctx *ctx, const priest_problem *pr, int n_override, Shape &sh)
+{
+    const priest_config &c = ctx->cfg;
+    if (!pr) return fail(ctx, PRIEST_ERR_INVALID, "problem is NULL");
+    std::memset(&sh, 0, sizeof(sh));
+    sh.dims = pr->dims ? pr->dims : c.dims;
+    sh.degree = c.degree;
+    sh.nv = sh.degree + 1;
+    sh.n_p = pr->n_p ? pr->n_p : c.n_p;
+    sh.horizon = pr->horizon > 0 ? pr->horizon : c.horizon;
+    sh.rho = c.rho;
+    sh.vmax = pr->vmax > 0 ? pr->vmax : c.vmax;
+    sh.amax = pr->amax > 0 ? pr->amax : c.amax;
+    sh.use_bounds = c.use_bounds ? 1 : 0;
+    sh.bc_mask = pr->bc_final_mask;
+    sh.n_obs = pr->n_obs;
+    if (sh.dims != 2 && sh.dims != 3) return fail(ctx, PRIEST_ERR_INVALID, "dims must be 2 or 3");
+    if (sh.degree < 5 || sh.degree > 15) return fail(ctx, PRIEST_ERR_INVALID, "degree must be in [5, 15]");
+    if (sh.n_p < 2 || sh.n_p > PRIEST_MAX_NP) return fail(ctx, PRIEST_ERR_INVALID, "n_p out of range");
+    if (!(sh.horizon > 0) || !is_fin(sh.horizon)) return fail(ctx, PRIEST_ERR_INVALID, "horizon must be > 0");
+    if (!(sh.rho > 0) || !is_fin(sh.rho)) return fail(ctx, PRIEST_ERR_INVALID, "rho must be > 0");
+    if (!(sh.vmax > 0) || !(sh.amax > 0) || !is_fin(sh.vmax) || !is_fin(sh.amax))
+        return fail(ctx, PRIEST_ERR_INVALID, "vmax and amax must be > 0");
+    if (sh.bc_mask != 0 && sh.bc_mask != 1 && sh.bc_mask != 3 && sh.bc_mask != 7)
+        return fail(ctx, PRIEST_ERR_INVALID, "bc_final_mask must be 0, 1, 3 or 7");
+    if (sh.n_obs < 0 || sh.n_obs > PRIEST_MAX_OBS) return fail(ctx, PRIEST_ERR_INVALID, "n_obs out of range");
+    if (sh.n_obs > 0 && (!pr->center || !pr->semi))
+        return fail(ctx, PRIEST_ERR_INVALID, "obstacle arrays are NULL");
+    for (int ax = 0; ax < sh.dims; ++ax)
+        for (int q = 0; q < 3; ++q) {
+            if (!is_fin(pr->b0[ax][q]) || !is_fin(pr->bf[ax][q]))
+                return fail(ctx, PRIEST_ERR_INVALID, "boundary values must be finite");
+            sh.b0[ax][q] = pr->b0[ax][q];
+            sh.bf[ax][q] = pr->bf[ax][q];
+        }
+    for (int ax = 0; ax < 3; ++ax) {
+        sh.smin[ax] = c.smin[ax];
+        sh.smax[ax] = c.smax[ax];
+    }
+    for (int j = 0; j < sh.n_obs; ++j) {
+        const double a = pr->semi[2 * j], b = pr->semi[2 * j + 1];
+        if (!(a > 0) || !is_fin(a) || (sh.dims == 3 && (!(b > 0) || !is_fin(b))))
+            return fail(ctx, PRIEST_ERR_INVALID, "obstacle semi-axes must be finite and > 0");
+        for (int ax = 0; ax < sh.dims; ++ax) {
+            if (!is_fin(pr->center[j * sh.dims + ax]))
+                return fail(ctx, PRIEST_ERR_INVALID, "obstacle centre is not finite");
+            if (pr->vel && !is_fin(pr->vel[j * sh.dims + ax]))
+                return fail(ctx, PRIEST_ERR_INVALID, "obstacle velocity is not finite");
+        }
+    }
+    sh.nf = sh.nv - kFree0 - final_fixed(sh.bc_mask);
+    sh.D = sh.dims * sh.nv;
+    sh.N = n_override >= 0 ? n_override : (pr->n_samples ? pr->n_samples : c.n_samples);
+    if (sh.N < 0 || sh.N > PRIEST_MAX_SAMPLES) return fail(ctx, PRIEST_ERR_INVALID, "sample count out of range");
+    if (n_override < 0) {
+        if (sh.N < 1) return fail(ctx, PRIEST_ERR_INVALID, "n_samples must be >= 1");
+        int np = pr->n_proj ? pr->n_proj : c.n_proj;
+        int ne = pr->n_elite ? pr->n_elite : c.n_elite;
+        if (np <= 0) np = std::max(1, (80 * sh.N) / 110);
+        if (ne <= 0) ne = std::max(1, std::min(np, sh.N / 10));
+        if (np > sh.N || ne > np || ne > PRIEST_MAX_ELITE)
+            return fail(ctx, PRIEST_ERR_INVALID, "need n_elite <= n_proj <= n_samples");
+        sh.n_proj = np;
+        sh.n_elite = ne;
+    }
+    return PRIEST_OK;
+}
+
+// Stable static-first order of the obstacles (moving ones, |v| > 0, last).
+void order_obstacles(const Shape &sh, const double *center, const double *vel, const double *semi,
+                     std::vector<double> &c, std::vector<double> &v, std::vector<double> &s, int &n_static)
+{
+    const int n = sh.n_obs, d = sh.dims;
+    c.assign(size_t(std::max(n, 1)) * d, 0.0);
+    v.assign(size_t(std::max(n, 1)) * d, 0.0);
+    s.assign(size_t(std::max(n, 1)) * 2, 1.0);
+    std::vector<int> order;
+    order.reserve(n);
+    auto moving = [&](int j) {
+        if (!vel) return false;
+        for (int ax = 0; ax < d; ++ax)
+            if (vel[j * d + ax] != 0.0) return true;
+        return false;
+    };
+    for (int j = 0; j < n; ++j)
+        if (!moving(j)) order.push_back(j);
+    n_static = int(order.size());
+    for (int j = 0; j < n; ++j)
+        if (moving(j)) order.push_back(j);
+    for (int k = 0; k < n; ++k) {
+        const int j = order[k];
+        for (int ax = 0; ax < d; ++ax) {
+            c[k * d + ax] = center[j * d + ax];
+            v[k * d + ax] = vel ? vel[j * d + ax] : 0.0;
+        }
+        s[2 * k] = semi[2 * j];
+        s[2 * k + 1] = (d == 3) ? semi[2 * j + 1] : semi[2 * j];
+    }
+}
+
+size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Byte layout of a loaded problem (also used to admit serving requests).
+struct Carve {
+    size_t center, vel, semi, tab64, tab32, cB, mu, cov, L, mu_new, xb, r, c1, elite, out, counter, z, xi, lam,
+        total;
+};
+
+Carve carve(const Shape &sh, bool fp32, int z_iters, bool proj_buffers)
+{
+    Carve k;
+    size_t o = 0;
+    const int nob = std::max(sh.n_obs, 1);
+    const TableLayout lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
+    const size_t N = size_t(std::max(sh.N, 1)), D = size_t(sh.D);
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = round_up(o + bytes);
+        return at;
+    };
+    k.center = take(sizeof(double) * nob * sh.dims);
+    k.vel = take(sizeof(double) * nob * sh.dims);
+    k.semi = take(sizeof(double) * nob * 2);
+    k.tab64 = take(sizeof(double) * lay.total);
+    k.tab32 = take(fp32 ? sizeof(float) * lay.total : 0);
+    k.cB = take(sizeof(double) * 3 * kMaxNv);
+    k.mu = take(sizeof(double) * D);
+    k.cov = take(sizeof(double) * D * D);
+    k.L = take(sizeof(double) * D * D);
+    k.mu_new = take(sizeof(double) * D);
+    k.xb = take(sizeof(double) * N * D);
+    k.r = take(sizeof(double) * N);
+    k.c1 = take(sizeof(double) * N);
+    k.elite = take(sizeof(int) * std::max(sh.n_elite, 1));
+    k.out = take(sizeof(double) * (D + 4));
+    k.counter = take(sizeof(unsigned));
+    k.z = take(sizeof(double) * size_t(z_iters) * N * D);
+    k.xi = take(proj_buffers ? sizeof(double) * N * D : 0);
+    k.lam = take(proj_buffers ? sizeof(double) * N * D : 0);
+    k.total = o;
+    return k;
+}
+
+void free_loaded(priest_loaded *h)
+{
+    if (!h) return;
+    if (h->block) cudaFree(h->block);
+    delete h;
+}
+
+// Allocates and fills a loaded problem (obstacles uploaded on `st`).
+priest_status make_loaded(priest_ctx *ctx, const Shape &sh_in, const double *center, const double *vel,
+                          const double *semi, int z_iters, bool proj_buffers, cudaStream_t st,
+                          priest_loaded **out)
+{
+    Shape sh = sh_in;
+    std::vector<double> c, v, s;
+    order_obstacles(sh, center, vel, semi, c, v, s, sh.n_static);
+    const bool fp32 = ctx->cfg.precision != PRIEST_FP64_CHECK;
+    const Carve k = carve(sh, fp32, z_iters, proj_buffers);
+    priest_loaded *h = new (std::nothrow) priest_loaded();
+    if (!h) return fail(ctx, PRIEST_ERR_NOMEM, "host allocation failed");
+    h->sh = sh;
+    cudaError_t e = cudaMalloc(&h->block, k.total);
+    if (e != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return fail(ctx, PRIEST_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->bytes = k.total;
+    char *b = static_cast<char *>(h->block);
+    h->center = reinterpret_cast<double *>(b + k.center);
+    h->vel = reinterpret_cast<double *>(b + k.vel);
+    h->semi = reinterpret_cast<double *>(b + k.semi);
+    h->tab64 = reinterpret_cast<double *>(b + k.tab64);
+    h->tab32 = fp32 ? reinterpret_cast<float *>(b + k.tab32) : nullptr;
+    h->cB = reinterpret_cast<double *>(b + k.cB);
+    h->mu = reinterpret_cast<double *>(b + k.mu);
+    h->cov = reinterpret_cast<double *>(b + k.cov);
+    h->L = reinterpret_cast<double *>(b + k.L);
+    h->mu_new = reinterpret_cast<double *>(b + k.mu_new);
+    h->xb = reinterpret_cast<double *>(b + k.xb);
+    h->r = reinterpret_cast<double *>(b + k.r);
+    h->c1 = reinterpret_cast<double *>(b + k.c1);
+    h->elite = reinterpret_cast<int *>(b + k.elite);
+    h->out = reinterpret_cast<double *>(b + k.out);
+    h->counter = reinterpret_cast<unsigned *>(b + k.counter);
+    h->z = z_iters ? reinterpret_cast<double *>(b + k.z) : nullptr;
+    h->xi = proj_buffers ? reinterpret_cast<double *>(b + k.xi) : nullptr;
+    h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
+    const size_t ob = sizeof(double) * c.size();
+    e = cudaMemcpyAsync(h->center, c.data(), ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->vel, v.data(), ob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->semi, s.data(), sizeof(double) * s.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned), st);
+    // the vectors above must outlive the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_loaded(h);
+        return cuda_fail(ctx, e, "upload of the problem");
+    }
+    *out = h;
+    return PRIEST_OK;
+}
+
+// Host-pointer entry points reuse one scratch problem while it is big enough.
+priest_status scratch_for(priest_ctx *ctx, const Shape &sh, const priest_problem *pr, int z_iters,
+                          bool proj_buffers, priest_loaded **out)
+{
+    priest_loaded *h = ctx->scratch;
+    const bool fp32 = ctx->cfg.precision != PRIEST_FP64_CHECK;
+    if (h && carve(sh, fp32, z_iters, proj_buffers).total <= h->bytes && sh.dims == h->sh.dims) {
+        // re-carve in place with the new shape
+        const Carve k = carve(sh, fp32, z_iters, proj_buffers);
+        char *b = static_cast<char *>(h->block);
+        Shape s2 = sh;
+        std::vector<double> c, v, s;
+        order_obstacles(s2, pr->center, pr->vel, pr->semi, c, v, s, s2.n_static);
+        h->sh = s2;
+        h->center = reinterpret_cast<double *>(b + k.center);
+        h->vel = reinterpret_cast<double *>(b + k.vel);
+        h->semi = reinterpret_cast<double *>(b + k.semi);
+        h->tab64 = reinterpret_cast<double *>(b + k.tab64);
+        h->tab32 = fp32 ? reinterpret_cast<float *>(b + k.tab32) : nullptr;
+        h->cB = reinterpret_cast<double *>(b + k.cB);
+        h->mu = reinterpret_cast<double *>(b + k.mu);
+        h->cov = reinterpret_cast<double *>(b + k.cov);
+        h->L = reinterpret_cast<double *>(b + k.L);
+        h->mu_new = reinterpret_cast<double *>(b + k.mu_new);
+        h->xb = reinterpret_cast<double *>(b + k.xb);
+        h->r = reinterpret_cast<double *>(b + k.r);
+        h->c1 = reinterpret_cast<double *>(b + k.c1);
+        h->elite = reinterpret_cast<int *>(b + k.elite);
+        h->out = reinterpret_cast<double *>(b + k.out);
+        h->counter = reinterpret_cast<unsigned *>(b + k.counter);
+        h->z = z_iters ? reinterpret_cast<double *>(b + k.z) : nullptr;
+        h->xi = proj_buffers ? reinterpret_cast<double *>(b + k.xi) : nullptr;
+        h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
+        const size_t ob = sizeof(double) * c.size();
+        cudaError_t e = cudaMemcpyAsync(h->center, c.data(), ob, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h->vel, v.data(), ob, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->semi, s.data(), sizeof(double) * s.size(), cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->counter, 0, sizeof(unsigned), ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "upload of the problem");
+        *out = h;
+        return PRIEST_OK;
+    }
+    if (h) {
+        cudaStreamSynchronize(ctx->stream);
+        free_loaded(h);
+        ctx->scratch = nullptr;
+    }
+    priest_status st = make_loaded(ctx, sh, pr->center, pr->vel, pr->semi, z_iters, proj_buffers, ctx->stream, &h);
+    if (st != PRIEST_OK) return st;
+    ctx->scratch = h;
+    *out = h;
+    return PRIEST_OK;
+}
+
+template <typename Real>
+ProjParams<Real> proj_params(priest_ctx *ctx, priest_loaded *h, const Tiling &t)
+{
+    const Shape &sh = h->sh;
+    ProjParams<Real> p;
+    std::memset(&p, 0, sizeof(p));
+    p.dims = sh.dims;
+    p.nv = sh.nv;
+    p.nf = sh.nf;
+    p.n_p = sh.n_p;
+    p.n_obs = sh.n_obs;
+    p.n_static = sh.n_static;
+    p.use_bounds = sh.use_bounds;
+    p.K = ctx->cfg.proj_iters;
+    p.S = t.S;
+    p.C = t.C;
+    p.rho = Real(sh.rho);
+    p.vmax = Real(sh.vmax);
+    p.amax = Real(sh.amax);
+    for (int ax = 0; ax < 3; ++ax) {
+        p.smin[ax] = Real(sh.smin[ax]);
+        p.smax[ax] = Real(sh.smax[ax]);
+    }
+    p.tab = std::is_same<Real, double>::value ? reinterpret_cast<const Real *>(h->tab64)
+                                              : reinterpret_cast<const Real *>(h->tab32);
+    p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
+    p.cB = h->cB;
+    return p;
+}
+
+priest_status enqueue_setup(priest_ctx *ctx, priest_loaded *h, bool plan_mode, cudaStream_t st, int *status)
+{
+    SetupParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.sh = h->sh;
+    sp.center = h->center;
+    sp.vel = h->vel;
+    sp.semi = h->semi;
+    sp.tab64 = h->tab64;
+    sp.tab = h->tab32 ? static_cast<void *>(h->tab32) : static_cast<void *>(h->tab64);
+    sp.real_is_double = h->tab32 ? 0 : 1;
+    sp.cB = h->cB;
+    if (plan_mode) {
+        sp.mu = h->mu;
+        sp.cov = h->cov;
+        sp.L = h->L;
+        sp.default_mu = h->default_mu;
+        sp.default_cov = h->default_cov;
+    }
+    sp.init_std = ctx->cfg.init_std;
+    sp.chol_eps = ctx->cfg.chol_eps;
+    sp.status = status;
+    cudaError_t e = launch_setup(sp, st);
+    ctx->launches++;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "setup kernel");
+    return PRIEST_OK;
+}
+
+template <typename Real>
+priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi,
+                              const double *z, const double *lam_in, double *lam_out, double *xb, double *r,
+                              double *c1, cudaStream_t st)
+{
+    Shape sh = h->sh;
+    sh.N = N;
+    const Tiling t = choose_tiling<Real>(sh, N, ctx->n_sm);
+    if (t.smem > size_t(227) * 1024)
+        return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory (reduce n_p / n_obs)");
+    ProjParams<Real> p = proj_params<Real>(ctx, h, t);
+    p.N = N;
+    p.mode = mode;
+    p.xi_in = xi;
+    p.mu = h->mu;
+    p.Lc = h->L;
+    p.z = z;
+    p.lam_in = lam_in;
+    p.lam_out = lam_out;
+    p.want_lambda = lam_out != nullptr;
+    p.xi_bar = xb;
+    p.r_out = r;
+    p.c1_out = c1;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->profile && st == ctx->stream) {
+        if (!ctx->prof_free.empty()) {
+            ev = ctx->prof_free.back();
+            ctx->prof_free.pop_back();
+        } else {
+            cudaEventCreate(&ev.first);
+            cudaEventCreate(&ev.second);
+        }
+        cudaEventRecord(ev.first, st);
+    }
+    cudaError_t e = launch_project<Real>(p, t, st);
+    ctx->launches++;
+    if (ev.first) {
+        cudaEventRecord(ev.second, st);
+        ctx->prof_used.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "projection kernel");
+    return PRIEST_OK;
+}
+
+priest_status enqueue_project_any(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi,
+                                  const double *z, const double *lam_in, double *lam_out, double *xb, double *r,
+                                  double *c1, cudaStream_t st)
+{
+    if (ctx->cfg.precision == PRIEST_FP64_CHECK)
+        return enqueue_project<double>(ctx, h, N, mode, xi, z, lam_in, lam_out, xb, r, c1, st);
+    return enqueue_project<float>(ctx, h, N, mode, xi, z, lam_in, lam_out, xb, r, c1, st);
+}
+
+// Alg. 1 on a loaded problem: setup, then per CEM iteration
+// project(sample) -> select -> refit(+Cholesky).  z: L x N x D (device).
+priest_status enqueue_plan(priest_ctx *ctx, priest_loaded *h, const double *z, double *out, cudaStream_t st,
+                           int *status)
+{
+    const Shape &sh = h->sh;
+    priest_status s = enqueue_setup(ctx, h, true, st, status);
+    if (s != PRIEST_OK) return s;
+    const size_t step = size_t(sh.N) * sh.D;
+    for (int l = 0; l < ctx->cfg.cem_iters; ++l) {
+        s = enqueue_project_any(ctx, h, sh.N, 1, nullptr, z + l * step, nullptr, nullptr, h->xb, h->r, h->c1, st);
+        if (s != PRIEST_OK) return s;
+        cudaError_t e = launch_select(sh.N, h->r, h->c1, sh.n_proj, sh.n_elite, h->elite, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "select kernel");
+        e = launch_refit(sh.D, h->xb, h->r, h->c1, h->elite, sh.n_elite, ctx->cfg.sigma_lr, ctx->cfg.gamma,
+                         ctx->cfg.chol_eps, h->mu, h->cov, h->mu_new, h->L, h->counter, status,
+                         out ? out : h->out, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "refit kernel");
+    }
+    return PRIEST_OK;
+}
+
+priest_status check_status(priest_ctx *ctx, int *d_status, cudaStream_t st)
+{
+    int hs = 0;
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(&hs, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
+    if (hs) {
+        PRIEST_CUDA(ctx, cudaMemsetAsync(d_status, 0, sizeof(int), st));
+        PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
+        if (hs & kStatusCholesky) return fail(ctx, PRIEST_ERR_NUMERIC, "covariance Cholesky met a non-positive pivot");
+        if (hs & kStatusKkt) return fail(ctx, PRIEST_ERR_NUMERIC, "KKT block met a non-positive pivot");
+        return fail(ctx, PRIEST_ERR_NUMERIC, "numerical failure on the device");
+    }
+    return PRIEST_OK;
+}
+
+uint64_t splitmix64(uint64_t &s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void gaussian_stream(uint64_t seed, int64_t count, double *out)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    uint64_t s = seed;
+    int64_t i = 0;
+    while (i < count) {
+        const double u1 = double(splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
+        const double u2 = double(splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
+        const double rad = std::sqrt(-2.0 * std::log(1.0 - u1));
+        const double th = two_pi * u2;
+        out[i++] = rad * std::cos(th);
+        if (i < count) out[i++] = rad * std::sin(th);
+    }
+}
+
+priest_status fill_result(priest_ctx *ctx, const Shape &sh, const double *host_out, const double *host_mu,
+                          priest_result *res)
+{
+    std::memset(res, 0, sizeof(*res));
+    res->status = PRIEST_OK;
+    res->D = sh.D;
+    for (int d = 0; d < sh.D; ++d) {
+        res->xi_best[d] = host_out[d];
+        res->mu[d] = host_mu[d];
+    }
+    res->resid = host_out[sh.D];
+    res->cost = host_out[sh.D + 1];
+    res->c_aug = host_out[sh.D + 2];
+    res->best_index = int(host_out[sh.D + 3]);
+    (void)ctx;
+    return PRIEST_OK;
+}
+
+priest_status plan_host(priest_ctx *ctx, const priest_problem *pr, const double *mu0, const double *cov0,
+                        const double *z_host, priest_result *out)
+{
+    if (!ctx || !out) return fail(ctx, PRIEST_ERR_INVALID, "NULL argument");
+    Shape sh;
+    priest_status s = resolve(ctx, pr, -1, sh);
+    if (s != PRIEST_OK) return s;
+    const int L = ctx->cfg.cem_iters;
+    priest_loaded *h = nullptr;
+    s = scratch_for(ctx, sh, pr, L, false, &h);
+    if (s != PRIEST_OK) return s;
+    const size_t nz = size_t(L) * sh.N * sh.D;
+    std::vector<double> zbuf;
+    if (!z_host) {
+        zbuf.resize(nz);
+        gaussian_stream(pr->seed, int64_t(nz), zbuf.data());
+        z_host = zbuf.data();
+    }
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(h->z, z_host, nz * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    h->default_mu = mu0 == nullptr;
+    h->default_cov = cov0 == nullptr;
+    if (mu0) PRIEST_CUDA(ctx, cudaMemcpyAsync(h->mu, mu0, sh.D * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    if (cov0)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(h->cov, cov0, size_t(sh.D) * sh.D * sizeof(double), cudaMemcpyHostToDevice,
+                                         ctx->stream));
+    s = enqueue_plan(ctx, h, h->z, h->out, ctx->stream, ctx->d_status);
+    if (s != PRIEST_OK) return s;
+    std::vector<double> ho(sh.D + 4), hm(sh.D);
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(ho.data(), h->out, ho.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(hm.data(), h->mu, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    s = check_status(ctx, ctx->d_status, ctx->stream);
+    if (s != PRIEST_OK) return s;
+    return fill_result(ctx, sh, ho.data(), hm.data(), out);
+}
+
+// ---------------------------------------------------------------------------
+// Serving worker: admits queued requests while their device memory fits the
+// budget, runs them on the serving stream, keeps warm-start state per robot.
+// ---------------------------------------------------------------------------
+void serve_loop(priest_ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    for (;;) {
+        ServeRequest req;
+        {
+            std::unique_lock<std::mutex> lk(ctx->mu_q);
+            ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+            if (ctx->stop && ctx->queue.empty()) return;
+            req = std::move(ctx->queue.front());
+            ctx->queue.pop_front();
+        }
+        priest_result res;
+        std::memset(&res, 0, sizeof(res));
+        priest_loaded *h = nullptr;
+        priest_status st = make_loaded(ctx, req.sh, req.center.data(), req.vel.data(), req.semi.data(),
+                                       ctx->cfg.cem_iters, false, ctx->serve_stream, &h);
+        if (st == PRIEST_OK) {
+            const size_t nz = size_t(ctx->cfg.cem_iters) * req.sh.N * req.sh.D;
+            std::vector<double> z(nz);
+            gaussian_stream(req.seed, int64_t(nz), z.data());
+            cudaMemcpyAsync(h->z, z.data(), nz * sizeof(double), cudaMemcpyHostToDevice, ctx->serve_stream);
+            WarmState ws;
+            bool have_warm = false;
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu_q);
+                auto it = ctx->warm.find(req.robot_id);
+                if (req.robot_id >= 0 && it != ctx->warm.end() && it->second.D == req.sh.D) {
+                    ws = it->second;
+                    have_warm = true;
+                }
+            }
+            h->default_mu = !have_warm;
+            h->default_cov = !have_warm;
+            if (have_warm) {
+                cudaMemcpyAsync(h->mu, ws.mu.data(), req.sh.D * sizeof(double), cudaMemcpyHostToDevice,
+                                ctx->serve_stream);
+                cudaMemcpyAsync(h->cov, ws.cov.data(), size_t(req.sh.D) * req.sh.D * sizeof(double),
+                                cudaMemcpyHostToDevice, ctx->serve_stream);
+            }
+            st = enqueue_plan(ctx, h, h->z, h->out, ctx->serve_stream, ctx->serve_status);
+            std::vector<double> ho(req.sh.D + 4), hm(req.sh.D), hc(size_t(req.sh.D) * req.sh.D);
+            if (st == PRIEST_OK) {
+                cudaMemcpyAsync(ho.data(), h->out, ho.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->serve_stream);
+                cudaMemcpyAsync(hm.data(), h->mu, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->serve_stream);
+                cudaMemcpyAsync(hc.data(), h->cov, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->serve_stream);
+                st = check_status(ctx, ctx->serve_status, ctx->serve_stream);
+            }
+            if (st == PRIEST_OK) {
+                fill_result(ctx, req.sh, ho.data(), hm.data(), &res);
+                if (req.robot_id >= 0) {
+                    std::lock_guard<std::mutex> lk(ctx->mu_q);
+                    WarmState &w = ctx->warm[req.robot_id];
+                    w.D = req.sh.D;
+                    w.mu = hm;
+                    w.cov = hc;
+                }
+            }
+            cudaStreamSynchronize(ctx->serve_stream);
+            free_loaded(h);
+        }
+        res.status = st;
+        res.latency_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - req.t_submit).count();
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu_q);
+            ctx->in_flight_bytes -= req.bytes;
+            ctx->done[req.ticket] = res;
+        }
+        ctx->cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out)
+{
+    if (count < 0 || (count > 0 && !out)) return PRIEST_ERR_INVALID;
+    gaussian_stream(seed, count, out);
+    return PRIEST_OK;
+}
+
+priest_status priest_create(const priest_config *cfg, void *cuda_stream, priest_ctx **out)
+{
+    if (!cfg || !out) return PRIEST_ERR_INVALID;
+    *out = nullptr;
+    if (cfg->degree < 5 || cfg->degree > 15 || cfg->proj_iters < 0 || cfg->cem_iters < 1 || !(cfg->rho > 0) ||
+        !(cfg->gamma > 0) || cfg->sigma_lr < 0 || cfg->sigma_lr > 1 || cfg->chol_eps < 0 ||
+        (cfg->precision != PRIEST_FP64_CHECK && cfg->precision != PRIEST_FP32))
+        return PRIEST_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return PRIEST_ERR_CUDA;
+    }
+    priest_ctx *ctx = new (std::nothrow) priest_ctx();
+    if (!ctx) return PRIEST_ERR_NOMEM;
+    ctx->cfg = *cfg;
+    cudaGetDevice(&ctx->device);
+    cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return PRIEST_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->d_status, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return PRIEST_ERR_CUDA;
+    }
+    ctx->serve_status = ctx->d_status + 1;
+    *out = ctx;
+    return PRIEST_OK;
+}
+
+priest_status priest_destroy(priest_ctx *ctx)
+{
+    if (!ctx) return PRIEST_OK;
+    if (ctx->worker_started) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu_q);
+            ctx->stop = true;
+        }
+        ctx->cv.notify_all();
+        ctx->worker.join();
+        cudaStreamDestroy(ctx->serve_stream);
+    }
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_loaded(ctx->scratch);
+    for (auto &ev : ctx->prof_used) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    for (auto &ev : ctx->prof_free) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    cudaFree(ctx->d_status);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return PRIEST_OK;
+}
+
+const char *priest_last_error(const priest_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int64_t priest_kernel_launches(const priest_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+priest_status priest_profile_enable(priest_ctx *ctx, int enable)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    ctx->profile = enable != 0;
+    return PRIEST_OK;
+}
+
+priest_status priest_profile_read(priest_ctx *ctx, int64_t *launches, double *ms)
+{
+    if (!ctx || !launches || !ms) return PRIEST_ERR_INVALID;
+    double total = 0.0;
+    for (auto &ev : ctx->prof_used) {
+        PRIEST_CUDA(ctx, cudaEventSynchronize(ev.second));
+        float t = 0.f;
+        PRIEST_CUDA(ctx, cudaEventElapsedTime(&t, ev.first, ev.second));
+        total += t;
+    }
+    *launches = int64_t(ctx->prof_used.size());
+    *ms = total;
+    ctx->prof_free.insert(ctx->prof_free.end(), ctx->prof_used.begin(), ctx->prof_used.end());
+    ctx->prof_used.clear();
+    return PRIEST_OK;
+}
+
+priest_status priest_sync(priest_ctx *ctx)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_status(ctx, ctx->d_status, ctx->stream);
+}
+
+priest_status priest_project(priest_ctx *ctx, const priest_problem *pr, int n, const double *xi,
+                             double *lambda_io, double *xi_bar_out, double *resid_out, double *cost_out)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    if (n < 0 || n > PRIEST_MAX_SAMPLES) return fail(ctx, PRIEST_ERR_INVALID, "n out of range");
+    if (n > 0 && (!xi || !xi_bar_out)) return fail(ctx, PRIEST_ERR_INVALID, "xi / xi_bar_out is NULL");
+    Shape sh;
+    priest_status s = resolve(ctx, pr, n, sh);
+    if (s != PRIEST_OK) return s;
+    for (size_t i = 0; i < size_t(n) * sh.D; ++i)
+        if (!is_fin(xi[i]) || (lambda_io && !is_fin(lambda_io[i])))
+            return fail(ctx, PRIEST_ERR_INVALID, "xi / lambda must be finite");
+    if (n == 0) return PRIEST_OK;
+    priest_loaded *h = nullptr;
+    s = scratch_for(ctx, sh, pr, 0, true, &h);
+    if (s != PRIEST_OK) return s;
+    const size_t bytes = size_t(n) * sh.D * sizeof(double);
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(h->xi, xi, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if (lambda_io) PRIEST_CUDA(ctx, cudaMemcpyAsync(h->lam, lambda_io, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    s = enqueue_setup(ctx, h, false, ctx->stream, ctx->d_status);
+    if (s != PRIEST_OK) return s;
+    s = enqueue_project_any(ctx, h, n, 0, h->xi, nullptr, lambda_io ? h->lam : nullptr,
+                            lambda_io ? h->lam : nullptr, h->xb, h->r, h->c1, ctx->stream);
+    if (s != PRIEST_OK) return s;
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(xi_bar_out, h->xb, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (lambda_io) PRIEST_CUDA(ctx, cudaMemcpyAsync(lambda_io, h->lam, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (resid_out)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(resid_out, h->r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (cost_out)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(cost_out, h->c1, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return check_status(ctx, ctx->d_status, ctx->stream);
+}
+
+priest_status priest_plan(priest_ctx *ctx, const priest_problem *pr, const double *mu0, const double *cov0,
+                          priest_result *out)
+{
+    return plan_host(ctx, pr, mu0, cov0, nullptr, out);
+}
+
+priest_status priest_plan_z(priest_ctx *ctx, const priest_problem *pr, const double *mu0, const double *cov0,
+                            const double *z, priest_result *out)
+{
+    if (!z) return fail(ctx, PRIEST_ERR_INVALID, "z is NULL");
+    return plan_host(ctx, pr, mu0, cov0, z, out);
+}
+
+priest_status priest_load(priest_ctx *ctx, const priest_problem *pr, priest_loaded **out)
+{
+    if (!ctx || !out) return PRIEST_ERR_INVALID;
+    Shape sh;
+    priest_status s = resolve(ctx, pr, -1, sh);
+    if (s != PRIEST_OK) return s;
+    return make_loaded(ctx, sh, pr->center, pr->vel, pr->semi, 0, false, ctx->stream, out);
+}
+
+priest_status priest_unload(priest_ctx *ctx, priest_loaded *h)
+{
+    if (ctx && ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_loaded(h);
+    return PRIEST_OK;
+}
+
+priest_status priest_plan_device(priest_ctx *ctx, priest_loaded *h, const double *z_dev, double *out_dev)
+{
+    if (!ctx || !h || !z_dev || !out_dev) return fail(ctx, PRIEST_ERR_INVALID, "NULL argument");
+    h->default_mu = true;
+    h->default_cov = true;
+    return enqueue_plan(ctx, h, z_dev, out_dev, ctx->stream, ctx->d_status);
+}
+
+priest_status priest_project_device(priest_ctx *ctx, priest_loaded *h, int n, const double *xi_dev,
+                                    double *lambda_dev, double *xi_bar_dev, double *resid_dev, double *cost_dev)
+{
+    if (!ctx || !h) return PRIEST_ERR_INVALID;
+    if (n < 0 || n > h->sh.N) return fail(ctx, PRIEST_ERR_INVALID, "n exceeds the loaded sample count");
+    if (n == 0) return PRIEST_OK;
+    if (!xi_dev || !xi_bar_dev || !resid_dev || !cost_dev) return fail(ctx, PRIEST_ERR_INVALID, "NULL pointer");
+    priest_status s = enqueue_setup(ctx, h, false, ctx->stream, ctx->d_status);
+    if (s != PRIEST_OK) return s;
+    return enqueue_project_any(ctx, h, n, 0, xi_dev, nullptr, lambda_dev, lambda_dev, xi_bar_dev, resid_dev,
+                               cost_dev, ctx->stream);
+}
+
+priest_status priest_submit(priest_ctx *ctx, const priest_problem *pr, uint64_t *ticket)
+{
+    if (!ctx || !ticket) return PRIEST_ERR_INVALID;
+    ServeRequest req;
+    priest_status s = resolve(ctx, pr, -1, req.sh);
+    if (s != PRIEST_OK) return s;
+    req.sh.n_static = 0;
+    const bool fp32 = ctx->cfg.precision != PRIEST_FP64_CHECK;
+    req.bytes = carve(req.sh, fp32, ctx->cfg.cem_iters, false).total;
+    if (ctx->cfg.hbm_budget && req.bytes > ctx->cfg.hbm_budget)
+        return fail(ctx, PRIEST_ERR_BUDGET, "request larger than the HBM budget");
+    const int n = pr->n_obs, d = req.sh.dims;
+    req.center.assign(pr->center, pr->center + size_t(n) * d);
+    req.vel.assign(size_t(n) * d, 0.0);
+    if (pr->vel) req.vel.assign(pr->vel, pr->vel + size_t(n) * d);
+    req.semi.assign(pr->semi, pr->semi + size_t(n) * 2);
+    if (n == 0) {
+        req.center.assign(d, 0.0);
+        req.vel.assign(d, 0.0);
+        req.semi.assign(2, 1.0);
+    }
+    req.seed = pr->seed;
+    req.robot_id = pr->robot_id;
+    req.t_submit = std::chrono::steady_clock::now();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu_q);
+        if (!ctx->worker_started) {
+            if (cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(ctx, PRIEST_ERR_CUDA, "cannot create the serving stream");
+            ctx->worker = std::thread(serve_loop, ctx);
+            ctx->worker_started = true;
+        }
+        req.ticket = ctx->next_ticket++;
+        *ticket = req.ticket;
+        ctx->in_flight_bytes += req.bytes;
+        ctx->queue.push_back(std::move(req));
+    }
+    ctx->cv.notify_all();
+    return PRIEST_OK;
+}
+
+priest_status priest_poll(priest_ctx *ctx, uint64_t ticket, priest_result *out)
+{
+    if (!ctx || !out) return PRIEST_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu_q);
+    auto it = ctx->done.find(ticket);
+    if (it == ctx->done.end()) {
+        if (ticket == 0 || ticket >= ctx->next_ticket) return fail(ctx, PRIEST_ERR_INVALID, "unknown ticket");
+        return PRIEST_PENDING;
+    }
+    *out = it->second;
+    ctx->done.erase(it);
+    return PRIEST_OK;
+}
+
+}  // extern "C"

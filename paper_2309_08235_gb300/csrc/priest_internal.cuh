@@ -1,0 +1,138 @@
+// priest_internal.cuh -- shapes, table layouts and launch entry points shared
+// by the library's translation units (setup, projection, CEM stages, C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "priest.h"
+
+namespace priest {
+
+constexpr int kMaxNv = PRIEST_MAX_NV;
+constexpr int kFree0 = 3;  // c_0, c_1, c_2 are fixed by the start position / velocity / acceleration
+
+// Bits of the device status word.
+enum : int {
+    kStatusCholesky = 1,   // non-positive pivot in the covariance Cholesky
+    kStatusKkt = 2,        // non-positive pivot in the shared KKT block
+    kStatusNaN = 4,
+};
+
+// Resolved shape and scalar data of one problem.
+struct Shape {
+    int dims, degree, nv, n_p, n_obs, n_static, nf, bc_mask, use_bounds;
+    double horizon, rho, vmax, amax;
+    double smin[3], smax[3];
+    double b0[3][3], bf[3][3];
+    int N, n_proj, n_elite, D;
+};
+
+// Number of coefficients fixed at the final time by the Bernstein end-point
+// conditions (mask 0, 1, 3, 7 -> 0, 1, 2, 3).
+inline int final_fixed(int mask) { return mask == 7 ? 3 : mask == 3 ? 2 : mask == 1 ? 1 : 0; }
+
+// Obstacle record stride in Real units.
+__host__ __device__ inline int obs_stride(int dims) { return dims == 2 ? 8 : 12; }
+
+__host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
+
+// Per-problem device tables, in units of Real, one contiguous buffer.
+struct TableLayout {
+    size_t basis;  // [3][n_p][nv]   P, Pd, Pdd
+    size_t base;   // [3][n_p][dims] contribution of the fixed coefficients
+    size_t W;      // [nf][nf]       (I + rho Q_FF)^-1
+    size_t obs;    // [n_obs][stride] pre-scaled obstacle records (static first)
+    size_t tval;   // [n_p]          time stamps
+    size_t total;
+};
+
+__host__ __device__ inline TableLayout table_layout(int dims, int nv, int nf, int n_p, int n_obs)
+{
+    TableLayout t;
+    size_t o = 0;
+    t.basis = o;
+    o = align8(o + size_t(3) * n_p * nv);
+    t.base = o;
+    o = align8(o + size_t(3) * n_p * dims);
+    t.W = o;
+    o = align8(o + size_t(nf) * nf);
+    t.obs = o;
+    o = align8(o + size_t(n_obs) * obs_stride(dims));
+    t.tval = o;
+    o = align8(o + size_t(n_p));
+    t.total = o;
+    return t;
+}
+
+// Inputs of the setup kernel (step a0): FP64 basis, fixed coefficients,
+// shared KKT block inverse, obstacle records; optionally the default mean /
+// covariance and the Cholesky factor of the first sampling covariance.
+struct SetupParams {
+    Shape sh;
+    const double *center, *vel, *semi;  // raw obstacles (device), static first
+    double *tab64;                      // FP64 tables (always written)
+    void *tab;                          // working tables: == tab64 for FP64, else float copy
+    int real_is_double;
+    double *cB;                         // [3][nv] fixed coefficient values (FP64)
+    double *mu, *cov, *L;               // D, D x D, D x D (plan mode) or null
+    int default_mu, default_cov;
+    double init_std, chol_eps;
+    int *status;
+};
+
+// Inputs of the fused projection kernel.
+template <typename Real>
+struct ProjParams {
+    int dims, nv, nf, n_p, n_obs, n_static, use_bounds;
+    int N, K, S, C, want_lambda, mode;  // mode 0: xi_in given; 1: xi = mu + L z
+    Real rho, vmax, amax, smin[3], smax[3];
+    const Real *tab;
+    TableLayout lay;
+    const double *cB;
+    const double *xi_in, *mu, *Lc, *z, *lam_in;
+    double *xi_bar, *lam_out, *r_out, *c1_out;
+};
+
+// Tiling chosen for one projection launch.
+struct Tiling {
+    int S;        // samples per CTA
+    int C;        // obstacle chunks per CTA
+    int threads;  // CTA size
+    int R;        // points per obstacle-loop item (template value)
+    size_t smem;  // dynamic shared memory bytes
+};
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` when it is above
+// the 48 KB default; `granted` caches the largest value set so far.
+template <typename Kernel>
+inline cudaError_t reserve_smem(Kernel kernel, size_t bytes, size_t &granted)
+{
+    if (bytes <= 48 * 1024 || bytes <= granted) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e == cudaSuccess) granted = bytes;
+    return e;
+}
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_setup(const SetupParams &p, cudaStream_t st);
+
+template <typename Real>
+size_t project_smem_bytes(const Shape &sh, int S, int C);
+
+template <typename Real>
+cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st);
+
+template <typename Real>
+Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm);
+
+cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, int n_elite,
+                          int *elite_idx, cudaStream_t st);
+
+cudaError_t launch_refit(int D, const double *xb, const double *r, const double *c1,
+                         const int *elite, int n_elite, double sigma, double gamma, double chol_eps,
+                         double *mu, double *cov, double *mu_new, double *L, unsigned *counter,
+                         int *status, double *best_out, cudaStream_t st);
+
+}  // namespace priest

@@ -1,0 +1,208 @@
+// setup.cu -- step a0 of the hot path, once per problem: the Bernstein basis
+// and its derivatives (Sec. II-A.2, eq. parametrized), the coefficients fixed
+// by the boundary conditions (A xi = b_eq), the inverse of the shared KKT block
+// (Sec. III-A, eqs. affine_trans / matrix_vec, reduced to the free
+// coefficients), pre-scaled obstacle records, and for a full solve the first
+// sampling factor chol(Sigma_0 + eps I) (Alg. 1).  All arithmetic in FP64; the
+// FP32 working tables are rounded copies.
+//
+// Design note: with the Bernstein basis every boundary row of A touches only
+// the end coefficients (c_0..c_2 at t_0, c_{n-2}..c_n at t_f), so {A c = b}
+// fixes those coefficients in closed form and leaves the interior ones free.
+// The KKT system of eq. matrix_vec then reduces to
+//   c_F = (I + rho Q_FF)^-1 (rhs_F - rho Q_FB c_B),  Q = F^T F per axis,
+// and the projection only ever needs W = (I + rho Q_FF)^-1.
+#include "block_linalg.cuh"
+#include "priest_internal.cuh"
+
+namespace priest {
+namespace {
+
+constexpr int kSetupThreads = 256;
+
+// Bernstein values of degree n, n-1 and n-2 at tau by the triangular
+// recurrence B_{j,m} = (1 - tau) B_{j,m-1} + tau B_{j-1,m-1}.
+__device__ void bernstein_levels(int n, double tau, double *bn, double *bn1, double *bn2)
+{
+    double b[kMaxNv];
+    for (int j = 0; j <= n; ++j) b[j] = 0.0;
+    b[0] = 1.0;
+    for (int m = 1; m <= n; ++m) {
+        for (int j = m; j >= 1; --j) b[j] = (1.0 - tau) * b[j] + tau * b[j - 1];
+        b[0] = (1.0 - tau) * b[0];
+        if (m == n - 2)
+            for (int j = 0; j <= n; ++j) bn2[j] = (j <= m) ? b[j] : 0.0;
+        if (m == n - 1)
+            for (int j = 0; j <= n; ++j) bn1[j] = (j <= m) ? b[j] : 0.0;
+    }
+    for (int j = 0; j <= n; ++j) bn[j] = b[j];
+}
+
+template <typename Real>
+__device__ void write_tables(const SetupParams &p, const double *src, size_t count)
+{
+    Real *dst = reinterpret_cast<Real *>(p.tab);
+    for (size_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = static_cast<Real>(src[i]);
+}
+
+__global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, double *tab64)
+{
+    const Shape &sh = p.sh;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int n = sh.degree, nv = sh.nv, np_ = sh.n_p, dims = sh.dims, nf = sh.nf;
+    const TableLayout lay = table_layout(dims, nv, nf, np_, sh.n_obs);
+    double *basis = tab64 + lay.basis;
+    double *base = tab64 + lay.base;
+    double *W = tab64 + lay.W;
+    double *obs = tab64 + lay.obs;
+    double *tval = tab64 + lay.tval;
+
+    __shared__ double s_cB[3][kMaxNv];
+    __shared__ double s_G[3][kMaxNv][kMaxNv];
+    __shared__ double s_M[kMaxNv][2 * kMaxNv];
+    __shared__ double s_fcol[kMaxNv];
+    __shared__ int s_flag;
+    extern __shared__ double s_dyn[];  // D x D for the Cholesky
+
+    // (1) basis rows and time stamps
+    for (int t = tid; t < np_; t += T) {
+        const double tau = double(t) / double(np_ - 1);
+        double bn[kMaxNv], bn1[kMaxNv], bn2[kMaxNv];
+        bernstein_levels(n, tau, bn, bn1, bn2);
+        for (int j = 0; j < nv; ++j) {
+            const double d1 = n * ((j >= 1 ? bn1[j - 1] : 0.0) - (j <= n - 1 ? bn1[j] : 0.0));
+            const double d2 = n * (n - 1) *
+                              ((j >= 2 ? bn2[j - 2] : 0.0) - 2.0 * (j >= 1 && j - 1 <= n - 2 ? bn2[j - 1] : 0.0) +
+                               (j <= n - 2 ? bn2[j] : 0.0));
+            basis[(0 * np_ + t) * nv + j] = bn[j];
+            basis[(1 * np_ + t) * nv + j] = d1 / sh.horizon;
+            basis[(2 * np_ + t) * nv + j] = d2 / (sh.horizon * sh.horizon);
+        }
+        tval[t] = sh.horizon * double(t) / double(np_ - 1);
+    }
+    // (2) coefficients fixed by the boundary rows (closed form of A c = b)
+    if (tid < dims) {
+        const int ax = tid;
+        const double Th = sh.horizon, nn = double(n), n2 = double(n) * double(n - 1);
+        for (int j = 0; j < kMaxNv; ++j) s_cB[ax][j] = 0.0;
+        s_cB[ax][0] = sh.b0[ax][0];
+        s_cB[ax][1] = s_cB[ax][0] + Th * sh.b0[ax][1] / nn;
+        s_cB[ax][2] = 2.0 * s_cB[ax][1] - s_cB[ax][0] + Th * Th * sh.b0[ax][2] / n2;
+        if (sh.bc_mask & 1) s_cB[ax][n] = sh.bf[ax][0];
+        if (sh.bc_mask & 2) s_cB[ax][n - 1] = s_cB[ax][n] - Th * sh.bf[ax][1] / nn;
+        if (sh.bc_mask & 4) s_cB[ax][n - 2] = 2.0 * s_cB[ax][n - 1] - s_cB[ax][n] + Th * Th * sh.bf[ax][2] / n2;
+        for (int j = 0; j < nv; ++j) p.cB[ax * kMaxNv + j] = s_cB[ax][j];
+    }
+    __syncthreads();
+    // (3) fixed-coefficient part of position / velocity / acceleration
+    const int f1 = kFree0 + nf;  // first fixed coefficient at the final end
+    for (int e = tid; e < 3 * np_ * dims; e += T) {
+        const int ax = e % dims, qt = e / dims;  // qt = q * np_ + t
+        double s = 0.0;
+        for (int j = 0; j < nv; ++j)
+            if (j < kFree0 || j >= f1) s += basis[qt * nv + j] * s_cB[ax][j];
+        base[qt * dims + ax] = s;
+    }
+    // (4) Gram blocks of the free coefficients: G_q = B_q,F^T B_q,F
+    for (int e = tid; e < 3 * nf * nf; e += T) {
+        const int q = e / (nf * nf), i = (e / nf) % nf, j = e % nf;
+        double s = 0.0;
+        for (int t = 0; t < np_; ++t)
+            s += basis[(q * np_ + t) * nv + kFree0 + i] * basis[(q * np_ + t) * nv + kFree0 + j];
+        s_G[q][i][j] = s;
+    }
+    __syncthreads();
+    // (5) H = I + rho Q_FF with Q = n_obs P^T P + Pd^T Pd + Pdd^T Pdd (+ 2 P^T P with
+    //     the workspace rows -P, +P of eq. bound_con); W = H^-1 by Gauss-Jordan
+    //     (H is symmetric positive definite, so no pivoting is needed).
+    const double wP = double(sh.n_obs) + (sh.use_bounds ? 2.0 : 0.0);
+    for (int e = tid; e < nf * 2 * nf; e += T) {
+        const int i = e / (2 * nf), j = e % (2 * nf);
+        double v;
+        if (j < nf)
+            v = (i == j ? 1.0 : 0.0) + sh.rho * (wP * s_G[0][i][j] + s_G[1][i][j] + s_G[2][i][j]);
+        else
+            v = (j - nf == i) ? 1.0 : 0.0;
+        s_M[i][j] = v;
+    }
+    if (tid == 0) s_flag = 1;
+    __syncthreads();
+    for (int k = 0; k < nf; ++k) {
+        const double piv = s_M[k][k];
+        if (tid < nf) s_fcol[tid] = s_M[tid][k];
+        __syncthreads();
+        if (!(piv > 0.0)) {
+            if (tid == 0) s_flag = 0;
+        } else {
+            for (int j = tid; j < 2 * nf; j += T) s_M[k][j] /= piv;
+        }
+        __syncthreads();
+        for (int e = tid; e < nf * 2 * nf; e += T) {
+            const int i = e / (2 * nf), j = e % (2 * nf);
+            if (i != k) s_M[i][j] -= s_fcol[i] * s_M[k][j];
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && !s_flag) atomicOr(p.status, kStatusKkt);
+    for (int e = tid; e < nf * nf; e += T) W[e] = s_M[e / nf][nf + e % nf];
+    // (6) obstacle records, pre-scaled so one FMA per axis gives the scaled
+    //     offset (x - x_o) / a:  2-D [1/a, -x_o/a, -y_o/a, a, -v_x/a, -v_y/a, 0, 0]
+    //     3-D [1/a, -x_o/a, -y_o/a, -z_o/b, 1/b, a, b, 0, -v_x/a, -v_y/a, -v_z/b, 0]
+    const int st = obs_stride(dims);
+    for (int j = tid; j < sh.n_obs; j += T) {
+        const double a = p.semi[2 * j], b = (dims == 3) ? p.semi[2 * j + 1] : a;
+        const double ia = 1.0 / a, ib = 1.0 / b;
+        double *o = obs + size_t(j) * st;
+        const double *c = p.center + j * dims;
+        const double *v = p.vel + j * dims;
+        if (dims == 2) {
+            o[0] = ia; o[1] = -c[0] * ia; o[2] = -c[1] * ia; o[3] = a;
+            o[4] = -v[0] * ia; o[5] = -v[1] * ia; o[6] = 0.0; o[7] = 0.0;
+        } else {
+            o[0] = ia; o[1] = -c[0] * ia; o[2] = -c[1] * ia; o[3] = -c[2] * ib;
+            o[4] = ib; o[5] = a; o[6] = b; o[7] = 0.0;
+            o[8] = -v[0] * ia; o[9] = -v[1] * ia; o[10] = -v[2] * ib; o[11] = 0.0;
+        }
+    }
+    // (7) full solve: default mean (straight-line coefficients) / covariance
+    //     and the first factor chol(Sigma_0 + chol_eps tr(Sigma_0)/D I)
+    if (p.L) {
+        const int D = sh.D;
+        if (p.default_mu)
+            for (int e = tid; e < D; e += T) {
+                const int ax = e / nv, k = e % nv;
+                p.mu[e] = sh.b0[ax][0] + (sh.bf[ax][0] - sh.b0[ax][0]) * double(k) / double(n);
+            }
+        if (p.default_cov)
+            for (int e = tid; e < D * D; e += T)
+                p.cov[e] = (e / D == e % D) ? p.init_std * p.init_std : 0.0;
+        __syncthreads();
+        __shared__ double s_tr;
+        if (tid == 0) {
+            double tr = 0.0;
+            for (int i = 0; i < D; ++i) tr += p.cov[i * D + i];
+            s_tr = tr;
+        }
+        __syncthreads();
+        const double eps = p.chol_eps * s_tr / double(D);
+        for (int e = tid; e < D * D; e += T) s_dyn[e] = p.cov[e] + ((e / D == e % D) ? eps : 0.0);
+        __syncthreads();
+        const bool ok = block_cholesky(s_dyn, D, &s_flag);
+        for (int e = tid; e < D * D; e += T) p.L[e] = s_dyn[e];
+        if (tid == 0 && !ok) atomicOr(p.status, kStatusCholesky);
+    }
+    __syncthreads();
+    // (8) working-precision copy of the tables
+    if (!p.real_is_double) write_tables<float>(p, tab64, lay.total);
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const SetupParams &p, cudaStream_t st)
+{
+    const size_t dyn = size_t(p.sh.D) * p.sh.D * sizeof(double);
+    setup_kernel<<<1, kSetupThreads, dyn, st>>>(p, p.tab64);
+    return cudaGetLastError();
+}
+
+}  // namespace priest

@@ -1,0 +1,346 @@
+"""Thin ctypes binding of libpriest.so, the C ABI declared in include/priest.h.
+
+Argument marshalling only: every step of the PRIEST path runs in the
+library's CUDA kernels.  The functions below carry the C names; the
+``Context`` class is a convenience wrapper over them that takes the plain
+problem / CEM dicts of ``paper_2309_08235_gb300.workloads``.
+
+If libpriest.so has not been built (``paper_2309_08235_gb300.build.build()``)
+every call raises ``PriestError``: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PRIEST_OK, PRIEST_PENDING = 0, 1
+PRIEST_ERR_INVALID, PRIEST_ERR_NOMEM, PRIEST_ERR_BUDGET = -1, -2, -3
+PRIEST_ERR_CUDA, PRIEST_ERR_TIMEOUT, PRIEST_ERR_NUMERIC = -4, -5, -6
+PRIEST_FP64_CHECK, PRIEST_FP32, PRIEST_MIXED_BF16 = 0, 1, 2
+MAX_D = 48
+
+STATUS_NAMES = {0: "PRIEST_OK", 1: "PRIEST_PENDING", -1: "PRIEST_ERR_INVALID", -2: "PRIEST_ERR_NOMEM",
+                -3: "PRIEST_ERR_BUDGET", -4: "PRIEST_ERR_CUDA", -5: "PRIEST_ERR_TIMEOUT",
+                -6: "PRIEST_ERR_NUMERIC"}
+
+# Every symbol include/priest.h declares.
+EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_project", "priest_plan",
+           "priest_plan_z", "priest_submit", "priest_poll", "priest_rng_normal", "priest_load",
+           "priest_unload", "priest_plan_device", "priest_project_device", "priest_sync",
+           "priest_kernel_launches", "priest_profile_enable", "priest_profile_read"]
+
+
+class PriestError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class priest_config(C.Structure):
+    _fields_ = [
+        ("dims", C.c_int), ("degree", C.c_int), ("n_p", C.c_int), ("horizon", C.c_double),
+        ("rho", C.c_double), ("proj_iters", C.c_int), ("cem_iters", C.c_int), ("n_samples", C.c_int),
+        ("n_proj", C.c_int), ("n_elite", C.c_int), ("sigma_lr", C.c_double), ("gamma", C.c_double),
+        ("chol_eps", C.c_double), ("init_std", C.c_double), ("vmax", C.c_double), ("amax", C.c_double),
+        ("use_bounds", C.c_int), ("smin", C.c_double * 3), ("smax", C.c_double * 3),
+        ("precision", C.c_int), ("hbm_budget", C.c_size_t),
+    ]
+
+
+class priest_problem(C.Structure):
+    _fields_ = [
+        ("n_obs", C.c_int), ("center", C.POINTER(C.c_double)), ("vel", C.POINTER(C.c_double)),
+        ("semi", C.POINTER(C.c_double)), ("b0", (C.c_double * 3) * 3), ("bf", (C.c_double * 3) * 3),
+        ("bc_final_mask", C.c_int), ("seed", C.c_uint64), ("robot_id", C.c_int64),
+        ("dims", C.c_int), ("n_p", C.c_int), ("n_samples", C.c_int), ("n_proj", C.c_int),
+        ("n_elite", C.c_int), ("horizon", C.c_double), ("vmax", C.c_double), ("amax", C.c_double),
+    ]
+
+
+class priest_result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("D", C.c_int), ("best_index", C.c_int), ("xi_best", C.c_double * MAX_D),
+        ("resid", C.c_double), ("cost", C.c_double), ("c_aug", C.c_double), ("mu", C.c_double * MAX_D),
+        ("latency_ms", C.c_double),
+    ]
+
+
+_P = C.POINTER(C.c_double)
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libpriest.so; raises PriestError when it is not built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise PriestError(PRIEST_ERR_CUDA, f"CUDA extension missing: {path} is not built "
+                                               "(run paper_2309_08235_gb300.build.build())")
+        L = C.CDLL(path)
+        vp = C.c_void_p
+        sig = {
+            "priest_create": (C.c_int, [C.POINTER(priest_config), vp, C.POINTER(vp)]),
+            "priest_destroy": (C.c_int, [vp]),
+            "priest_last_error": (C.c_char_p, [vp]),
+            "priest_project": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P, _P, _P]),
+            "priest_plan": (C.c_int, [vp, C.POINTER(priest_problem), _P, _P, C.POINTER(priest_result)]),
+            "priest_plan_z": (C.c_int, [vp, C.POINTER(priest_problem), _P, _P, _P, C.POINTER(priest_result)]),
+            "priest_submit": (C.c_int, [vp, C.POINTER(priest_problem), C.POINTER(C.c_uint64)]),
+            "priest_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(priest_result)]),
+            "priest_rng_normal": (C.c_int, [C.c_uint64, C.c_int64, _P]),
+            "priest_load": (C.c_int, [vp, C.POINTER(priest_problem), C.POINTER(vp)]),
+            "priest_unload": (C.c_int, [vp, vp]),
+            "priest_plan_device": (C.c_int, [vp, vp, vp, vp]),
+            "priest_project_device": (C.c_int, [vp, vp, C.c_int, vp, vp, vp, vp, vp]),
+            "priest_sync": (C.c_int, [vp]),
+            "priest_kernel_launches": (C.c_int64, [vp]),
+            "priest_profile_enable": (C.c_int, [vp, C.c_int]),
+            "priest_profile_read": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _arr(a, n=None):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if n is not None:
+        assert a.size == n, (a.size, n)
+    return a, a.ctypes.data_as(_P)
+
+
+def make_config(problem=None, cem=None, precision=PRIEST_FP32, hbm_budget=0, **over):
+    """priest_config from a workloads problem dict (context-level fields) and
+    a CEM dict; keyword arguments override any field."""
+    p = problem or {}
+    c = cem or {}
+    cfg = priest_config()
+    dims = int(p.get("dims", 2))
+    vals = {
+        "dims": dims, "degree": int(p.get("degree", 10)), "n_p": int(p.get("n_p", 100)),
+        "horizon": float(p.get("horizon", 8.0)), "rho": float(p.get("rho", 1.0)),
+        "proj_iters": int(c.get("proj_iters", 50)), "cem_iters": int(c.get("cem_iters", 4)),
+        "n_samples": int(c.get("n_samples", 200)), "n_proj": int(c.get("n_proj", 0)),
+        "n_elite": int(c.get("n_elite", 0)), "sigma_lr": float(c.get("sigma_lr", 0.5)),
+        "gamma": float(c.get("gamma", 1.0)), "chol_eps": float(c.get("chol_eps", 1e-8)),
+        "init_std": float(c.get("init_std", 2.0)), "vmax": float(p.get("vmax", 1.0)),
+        "amax": float(p.get("amax", 1.0)), "use_bounds": int(bool(p.get("use_bounds", False))),
+        "precision": int(precision), "hbm_budget": int(hbm_budget),
+    }
+    vals.update(over)
+    for k, v in vals.items():
+        setattr(cfg, k, v)
+    smin = np.zeros(3)
+    smax = np.zeros(3)
+    smin[:dims] = np.asarray(p.get("smin", np.zeros(dims)), dtype=float)[:dims]
+    smax[:dims] = np.asarray(p.get("smax", np.zeros(dims)), dtype=float)[:dims]
+    for ax in range(3):
+        cfg.smin[ax] = smin[ax]
+        cfg.smax[ax] = smax[ax]
+    return cfg
+
+
+def make_problem(p, cem=None, robot_id=-1, seed=None, per_problem_shape=False):
+    """priest_problem from a workloads problem dict; returns (struct, keepalive)."""
+    dims = int(p["dims"])
+    n_obs = int(p.get("n_obs", len(p["center"])))
+    keep = []
+    s = priest_problem()
+    s.n_obs = n_obs
+    if n_obs:
+        c, cp = _arr(p["center"], n_obs * dims)
+        v, vp = _arr(p.get("vel", np.zeros((n_obs, dims))), n_obs * dims)
+        m, mp = _arr(p["semi"], n_obs * 2)
+        keep += [c, v, m]
+        s.center, s.vel, s.semi = cp, vp, mp
+    b0 = np.zeros((3, 3))
+    bf = np.zeros((3, 3))
+    b0[:dims] = np.asarray(p["b0"], dtype=float).reshape(dims, 3)
+    bf[:dims] = np.asarray(p["bf"], dtype=float).reshape(dims, 3)
+    for ax in range(3):
+        for q in range(3):
+            s.b0[ax][q] = b0[ax, q]
+            s.bf[ax][q] = bf[ax, q]
+    s.bc_final_mask = int(p.get("bc_final_mask", 7))
+    s.seed = int(p.get("seed", 0) if seed is None else seed) & (2**64 - 1)
+    s.robot_id = int(robot_id)
+    if per_problem_shape:
+        s.dims = dims
+        s.n_p = int(p["n_p"])
+        s.horizon = float(p["horizon"])
+        s.vmax = float(p["vmax"])
+        s.amax = float(p["amax"])
+        if cem:
+            s.n_samples = int(cem["n_samples"])
+            s.n_proj = int(cem.get("n_proj", 0))
+            s.n_elite = int(cem.get("n_elite", 0))
+    return s, keep
+
+
+def _check(ctx, st):
+    if st not in (PRIEST_OK, PRIEST_PENDING):
+        msg = lib().priest_last_error(ctx)
+        raise PriestError(st, msg.decode() if msg else "")
+    return st
+
+
+# ---- the C names --------------------------------------------------------
+
+def priest_create(cfg, stream=None):
+    h = C.c_void_p()
+    st = lib().priest_create(C.byref(cfg), stream, C.byref(h))
+    if st != PRIEST_OK:
+        raise PriestError(st, "priest_create failed")
+    return h
+
+
+def priest_destroy(ctx):
+    return lib().priest_destroy(ctx)
+
+
+def priest_last_error(ctx):
+    m = lib().priest_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def priest_rng_normal(seed, count):
+    out = np.zeros(int(count))
+    st = lib().priest_rng_normal(C.c_uint64(int(seed) & (2**64 - 1)), int(count), out.ctypes.data_as(_P))
+    if st != PRIEST_OK:
+        raise PriestError(st, "priest_rng_normal failed")
+    return out
+
+
+def priest_project(ctx, prob, n, xi, lambda_io, xi_bar_out, resid_out, cost_out):
+    return _check(ctx, lib().priest_project(ctx, C.byref(prob), int(n), *(
+        None if a is None else a.ctypes.data_as(_P) for a in (xi, lambda_io, xi_bar_out, resid_out, cost_out))))
+
+
+def priest_plan(ctx, prob, mu0, cov0, res):
+    return _check(ctx, lib().priest_plan(ctx, C.byref(prob), _arr(mu0)[1], _arr(cov0)[1], C.byref(res)))
+
+
+def priest_plan_z(ctx, prob, mu0, cov0, z, res):
+    return _check(ctx, lib().priest_plan_z(ctx, C.byref(prob), _arr(mu0)[1], _arr(cov0)[1], z.ctypes.data_as(_P),
+                                           C.byref(res)))
+
+
+def priest_submit(ctx, prob):
+    t = C.c_uint64()
+    _check(ctx, lib().priest_submit(ctx, C.byref(prob), C.byref(t)))
+    return t.value
+
+
+def priest_poll(ctx, ticket, res):
+    return _check(ctx, lib().priest_poll(ctx, C.c_uint64(ticket), C.byref(res)))
+
+
+def priest_load(ctx, prob):
+    h = C.c_void_p()
+    _check(ctx, lib().priest_load(ctx, C.byref(prob), C.byref(h)))
+    return h
+
+
+def priest_unload(ctx, h):
+    return lib().priest_unload(ctx, h)
+
+
+def priest_plan_device(ctx, h, z_ptr, out_ptr):
+    return _check(ctx, lib().priest_plan_device(ctx, h, C.c_void_p(z_ptr), C.c_void_p(out_ptr)))
+
+
+def priest_project_device(ctx, h, n, xi_ptr, lam_ptr, xb_ptr, r_ptr, c1_ptr):
+    return _check(ctx, lib().priest_project_device(ctx, h, int(n), C.c_void_p(xi_ptr), C.c_void_p(lam_ptr),
+                                                   C.c_void_p(xb_ptr), C.c_void_p(r_ptr), C.c_void_p(c1_ptr)))
+
+
+def priest_sync(ctx):
+    return _check(ctx, lib().priest_sync(ctx))
+
+
+def priest_kernel_launches(ctx):
+    return int(lib().priest_kernel_launches(ctx))
+
+
+def priest_profile_enable(ctx, enable):
+    return _check(ctx, lib().priest_profile_enable(ctx, int(bool(enable))))
+
+
+def priest_profile_read(ctx):
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(ctx, lib().priest_profile_read(ctx, C.byref(n), C.byref(ms)))
+    return n.value, ms.value
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+def result_dict(res):
+    D = res.D
+    return {"status": res.status, "D": D, "best_index": res.best_index,
+            "best": np.array(res.xi_best[:D]), "r": res.resid, "c1": res.cost, "c_aug": res.c_aug,
+            "mu": np.array(res.mu[:D]), "latency_ms": res.latency_ms}
+
+
+class Context:
+    """A priest_ctx bound to a workloads problem / CEM description."""
+
+    def __init__(self, problem=None, cem=None, precision=PRIEST_FP32, stream=None, hbm_budget=0, **over):
+        self.cfg = make_config(problem, cem, precision, hbm_budget, **over)
+        self.h = priest_create(self.cfg, stream)
+
+    def close(self):
+        if self.h:
+            priest_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def project(self, p, xi, lam=None):
+        D = int(p["dims"]) * (self.cfg.degree + 1)
+        xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64).reshape(-1, D))
+        n = xi.shape[0]
+        lam_io = None if lam is None else np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(n, D)).copy()
+        xb = np.zeros((n, D))
+        r = np.zeros(n)
+        c1 = np.zeros(n)
+        prob, keep = make_problem(p)
+        priest_project(self.h, prob, n, xi, lam_io, xb, r, c1)
+        return xb, lam_io, r, c1
+
+    def plan(self, p, z=None, mu0=None, cov0=None, cem=None):
+        prob, keep = make_problem(p, cem)
+        res = priest_result()
+        if z is None:
+            priest_plan(self.h, prob, mu0, cov0, res)
+        else:
+            z = np.ascontiguousarray(np.asarray(z, dtype=np.float64))
+            priest_plan_z(self.h, prob, mu0, cov0, z, res)
+        return result_dict(res)
+
+    def launches(self):
+        return priest_kernel_launches(self.h)
