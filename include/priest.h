@@ -203,6 +203,31 @@ int64_t priest_kernel_launches(const priest_ctx *ctx);
 priest_status priest_profile_enable(priest_ctx *ctx, int enable);
 priest_status priest_profile_read(priest_ctx *ctx, int64_t *launches, double *ms);
 
+/* Projection that allocates no device memory (the paper has no counterpart;
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * real-time loops with a fixed memory budget or code running inside a
+ * pre-provisioned memory pool).  Same computation as priest_project_device:
+ * cfg->proj_iters alternating-minimisation iterations from Pi_A(xi), then r
+ * and c_1, in cfg->precision (FP32 or FP64 check mode).
+ *   cfg, prob: host structs; prob's obstacle arrays are HOST memory and are
+ *     copied into the library's scratch during the call.
+ *   xi_dev (n x D, read), lambda_dev (n x D, updated in place, or NULL),
+ *   xi_bar_dev (n x D), resid_dev (n), cost_dev (n): caller-owned DEVICE memory.
+ *   cuda_stream: stream to run on (NULL = legacy default stream).
+ * Scratch: one fixed 1 MiB device array inside the library, held by every
+ * device that loads it until the process exits; every call shares it and it
+ * keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * A problem whose tables do not fit returns PRIEST_ERR_BUDGET.  The first
+ * call on a device looks up the scratch's device address (set-up), so make
+ * that first call before any stream capture.  Blocks until the work is done.
+ * Errors are reported by the return code only: PRIEST_ERR_INVALID (bad
+ * arguments), PRIEST_ERR_BUDGET (too large for the scratch),
+ * PRIEST_ERR_NUMERIC (KKT block not positive definite), PRIEST_ERR_CUDA. */
+priest_status priest_project_noalloc(const priest_config *cfg, const priest_problem *prob, int n,
+                                     const double *xi_dev, double *lambda_dev, double *xi_bar_dev,
+                                     double *resid_dev, double *cost_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "PRIEST_OK", 1: "PRIEST_PENDING", -1: "PRIEST_ERR_INVALID", -
 EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_project", "priest_plan",
            "priest_plan_z", "priest_submit", "priest_poll", "priest_rng_normal", "priest_load",
            "priest_unload", "priest_plan_device", "priest_project_device", "priest_sync",
-           "priest_kernel_launches", "priest_profile_enable", "priest_profile_read"]
+           "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
+           "priest_project_noalloc"]
 
 
 class PriestError(RuntimeError):
@@ -105,6 +106,8 @@ def lib():
             "priest_kernel_launches": (C.c_int64, [vp]),
             "priest_profile_enable": (C.c_int, [vp, C.c_int]),
             "priest_profile_read": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
+            "priest_project_noalloc": (C.c_int, [C.POINTER(priest_config), C.POINTER(priest_problem), C.c_int,
+                                                 vp, vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -285,6 +288,14 @@ def priest_profile_read(ctx):
     ms = C.c_double()
     _check(ctx, lib().priest_profile_read(ctx, C.byref(n), C.byref(ms)))
     return n.value, ms.value
+
+
+def priest_project_noalloc(cfg, prob, n, xi_ptr, lam_ptr, xb_ptr, r_ptr, c1_ptr, stream=None):
+    """Projection without device allocation; device pointers as ints.  Returns
+    the status code (no context, so no message)."""
+    return lib().priest_project_noalloc(C.byref(cfg), C.byref(prob), int(n), C.c_void_p(xi_ptr),
+                                        C.c_void_p(lam_ptr), C.c_void_p(xb_ptr), C.c_void_p(r_ptr),
+                                        C.c_void_p(c1_ptr), stream)
 
 
 # ---- convenience wrapper ---------------------------------------------------
