@@ -31,14 +31,13 @@
 namespace priest {
 namespace {
 
-constexpr int kMaxThreads = 512;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Shared-memory layout in Real units: the problem tables first (same layout
 // as in global memory, so they are copied as one block), then the state.
 struct SmemLayout {
     TableLayout tab;
-    size_t xi, lam, c, u, pos, rv, ra, rb, part, total;
+    size_t xi, lam, c, tp, pos, rv, ra, rb, part, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int dims, int nv, int nf, int n_p, int n_obs, int S,
@@ -54,8 +53,8 @@ __host__ __device__ inline SmemLayout smem_layout(int dims, int nv, int nf, int 
     o = align8(o + size_t(S) * dims * nv);
     L.c = o;
     o = align8(o + size_t(S) * dims * nf);
-    L.u = o;
-    o = align8(o + size_t(S) * dims * nf);
+    L.tp = o;
+    o = align8(o + PS);
     L.pos = o;
     o = align8(o + dims * PS);
     L.rv = o;
@@ -119,7 +118,7 @@ __device__ __forceinline__ void obstacle_pairs(const Real *o, const Real (&px)[R
             q[r] = fma(dx[r], dx[r], dy[r] * dy[r]);
             qmin = min(qmin, q[r]);
         }
-        if (qmin < Real(1)) {
+        if (__any_sync(kFull, qmin < Real(1))) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (q[r] < Real(1)) {
@@ -159,7 +158,7 @@ __device__ __forceinline__ void obstacle_pairs(const Real *o, const Real (&px)[R
             q[r] = fma(dx[r], dx[r], fma(dy[r], dy[r], dz[r] * dz[r]));
             qmin = min(qmin, q[r]);
         }
-        if (qmin < Real(1)) {
+        if (__any_sync(kFull, qmin < Real(1))) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (q[r] < Real(1)) {
@@ -182,12 +181,13 @@ __device__ __forceinline__ void obstacle_pairs(const Real *o, const Real (&px)[R
     }
 }
 
-template <typename Real, int DIMS, int R>
-__global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<Real> p)
+template <typename Real, int DIMS, int R, int THREADS>
+__global__ void __launch_bounds__(THREADS) project_kernel(const ProjParams<Real> p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *sm = reinterpret_cast<Real *>(smem_raw);
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = T >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int T = THREADS, NW = THREADS / 32;
     const int nv = p.nv, nf = p.nf, np_ = p.n_p, S = p.S, C = p.C;
     const int D = DIMS * nv;
     const int s0 = blockIdx.x * S;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
     Real *sXi = sm + L.xi;
     Real *sLam = sm + L.lam;
     Real *sC = sm + L.c;
-    Real *sU = sm + L.u;
+    Real *sTp = sm + L.tp;
     Real *sPos = sm + L.pos;
     Real *sRV = sm + L.rv;
     Real *sRA = sm + L.ra;
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(p.tab);
         uint4 *dst = reinterpret_cast<uint4 *>(sm);
-        const size_t n16 = L.tab.total * sizeof(Real) / 16;
-        for (size_t i = tid; i < n16; i += T) dst[i] = src[i];
+        const int n16 = int(L.tab.total * sizeof(Real) / 16);
+        for (int i = tid; i < n16; i += T) dst[i] = src[i];
     }
     // a1/a2: samples (given, or xi = mu + L z in FP64), xi_bar^0 = Pi_A(xi)
     // (free coefficients copied, boundary ones implied), lambda^0
@@ -244,12 +244,25 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
         sLam[(s * DIMS + ax) * nv + col] = p.lam_in ? Real(p.lam_in[gi]) : Real(0);
     }
     __syncthreads();
+    // time stamp of every point (for moving obstacles)
+    for (int pt = tid; pt < P_act; pt += T) sTp[pt] = sT[pt % np_];
 
-    const int n_groups = (P_act + R - 1) / R;
+    // obstacle-loop items: (group of R points, obstacle chunk); the group
+    // count is padded to a warp multiple so each warp works on one chunk
+    const int n_groups = (((P_act + R - 1) / R) + 31) & ~31;
     const int Cs = (p.n_obs + C - 1) / C;
     const int items = n_groups * C;
+    // transposed-basis step: one warp per (sample, axis); lane = (column, segment)
     const int col_lo = p.want_lambda ? 0 : kFree0;
     const int ng = p.want_lambda ? nv : nf;
+    int ngp = 1;
+    while (ngp < ng) ngp <<= 1;
+    const int nseg = 32 / ngp;
+    const int f_lane = lane / nseg, seg = lane - f_lane * nseg;
+    const int col = col_lo + f_lane;
+    const bool col_ok = f_lane < ng;
+    const int fcol = col - kFree0;
+    const bool is_free = col_ok && fcol >= 0 && fcol < nf;
     constexpr int ST = DIMS == 2 ? 8 : 12;
 
     for (int k = 0; k <= p.K; ++k) {
@@ -260,26 +273,30 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
             const Real *b0 = sBasis + size_t(0 * np_ + t) * nv + kFree0;
             const Real *b1 = sBasis + size_t(1 * np_ + t) * nv + kFree0;
             const Real *b2 = sBasis + size_t(2 * np_ + t) * nv + kFree0;
+            const Real *cc = sC + s * DIMS * nf;
             Real pos[DIMS], vel[DIMS], acc[DIMS];
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax) {
+                pos[ax] = sBase[(0 * np_ + t) * DIMS + ax];
+                vel[ax] = sBase[(1 * np_ + t) * DIMS + ax];
+                acc[ax] = sBase[(2 * np_ + t) * DIMS + ax];
+            }
+            for (int f = 0; f < nf; ++f) {
+                const Real p0 = b0[f], p1 = b1[f], p2 = b2[f];
+#pragma unroll
+                for (int ax = 0; ax < DIMS; ++ax) {
+                    const Real cf = cc[ax * nf + f];
+                    pos[ax] = fma(p0, cf, pos[ax]);
+                    vel[ax] = fma(p1, cf, vel[ax]);
+                    acc[ax] = fma(p2, cf, acc[ax]);
+                }
+            }
             Real v2 = Real(0), a2 = Real(0);
 #pragma unroll
             for (int ax = 0; ax < DIMS; ++ax) {
-                Real x = sBase[(0 * np_ + t) * DIMS + ax];
-                Real v = sBase[(1 * np_ + t) * DIMS + ax];
-                Real a = sBase[(2 * np_ + t) * DIMS + ax];
-                const Real *cc = sC + (s * DIMS + ax) * nf;
-                for (int f = 0; f < nf; ++f) {
-                    const Real cf = cc[f];
-                    x = fma(b0[f], cf, x);
-                    v = fma(b1[f], cf, v);
-                    a = fma(b2[f], cf, a);
-                }
-                pos[ax] = x;
-                vel[ax] = v;
-                acc[ax] = a;
-                sPos[ax * PS + pt] = x;
-                v2 = fma(v, v, v2);
-                a2 = fma(a, a, a2);
+                sPos[ax * PS + pt] = pos[ax];
+                v2 = fma(vel[ax], vel[ax], v2);
+                a2 = fma(acc[ax], acc[ax], a2);
             }
             const Real fv = (v2 > vmax2) ? Real(1) - vmax * rsq(v2) : Real(0);
             const Real fa = (a2 > amax2) ? Real(1) - amax * rsq(a2) : Real(0);
@@ -322,15 +339,20 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
                 px[r] = ok ? sPos[pp] : Real(1e15);
                 py[r] = ok ? sPos[PS + pp] : Real(1e15);
                 pz[r] = (DIMS == 3 && ok) ? sPos[2 * PS + pp] : Real(1e15);
-                tt[r] = ok ? sT[pp % np_] : Real(0);
+                tt[r] = Real(0);
                 sx[r] = sy[r] = sz[r] = rq[r] = Real(0);
             }
             const int j0 = c * Cs, j1 = min(j0 + Cs, p.n_obs);
             const int js = min(j1, p.n_static);
             for (int j = j0; j < js; ++j)
                 obstacle_pairs<Real, DIMS, R, false>(sObs + size_t(j) * ST, px, py, pz, tt, sx, sy, sz, rq);
-            for (int j = max(j0, p.n_static); j < j1; ++j)
-                obstacle_pairs<Real, DIMS, R, true>(sObs + size_t(j) * ST, px, py, pz, tt, sx, sy, sz, rq);
+            const int jd = max(j0, p.n_static);
+            if (jd < j1) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) tt[r] = (p0 + r < P_act) ? sTp[p0 + r] : Real(0);
+                for (int j = jd; j < j1; ++j)
+                    obstacle_pairs<Real, DIMS, R, true>(sObs + size_t(j) * ST, px, py, pz, tt, sx, sy, sz, rq);
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int pp = p0 + r;
@@ -347,52 +369,48 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
         }
         __syncthreads();
         if (fin) break;
-        // ---- C/D: g = F^T(F xi_bar - e), multiplier step, shared-inverse step;
-        //      one warp per (sample, axis)
+        // ---- chunk partials -> one P-row residual per point (+ workspace rows)
+        if (C > 1 || p.use_bounds) {
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax)
+                for (int pt = tid; pt < P_act; pt += T) {
+                    Real v = sPart[ax * PS + pt];
+                    for (int c = 1; c < C; ++c) v += sPart[(c * DIMS + ax) * PS + pt];
+                    if (p.use_bounds) v += sRB[ax * PS + pt];
+                    sPart[ax * PS + pt] = v;
+                }
+            __syncthreads();
+        }
+        // ---- C/D: g = F^T(F xi_bar - e) (eq. lag), multiplier step, shared-inverse
+        //      step (eqs. affine_trans / comp_zeta); one warp per (sample, axis)
         for (int task = warp; task < S_act * DIMS; task += NW) {
             const int s = task / DIMS, ax = task - s * DIMS;
-            Real gacc[kMaxNv];
-#pragma unroll
-            for (int i = 0; i < kMaxNv; ++i) gacc[i] = Real(0);
-            for (int t = lane; t < np_; t += 32) {
-                const int pp = s * np_ + t;
-                Real rp = Real(0);
-                for (int c = 0; c < C; ++c) rp += sPart[(c * DIMS + ax) * PS + pp];
-                if (p.use_bounds) rp += sRB[ax * PS + pp];
-                const Real rv = sRV[ax * PS + pp], ra = sRA[ax * PS + pp];
-                const Real *b0 = sBasis + size_t(0 * np_ + t) * nv + col_lo;
-                const Real *b1 = sBasis + size_t(1 * np_ + t) * nv + col_lo;
-                const Real *b2 = sBasis + size_t(2 * np_ + t) * nv + col_lo;
-#pragma unroll
-                for (int i = 0; i < kMaxNv; ++i)
-                    if (i < ng) gacc[i] = fma(b0[i], rp, fma(b1[i], rv, fma(b2[i], ra, gacc[i])));
-            }
-#pragma unroll
-            for (int i = 0; i < kMaxNv; ++i) {
-                if (i < ng) {
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) gacc[i] += __shfl_xor_sync(kFull, gacc[i], off);
+            Real acc = Real(0);
+            if (col_ok) {
+                for (int t = seg; t < np_; t += nseg) {
+                    const int pp = s * np_ + t;
+                    const Real rp = sPart[ax * PS + pp], rv = sRV[ax * PS + pp], ra = sRA[ax * PS + pp];
+                    const Real *b = sBasis + size_t(t) * nv + col;
+                    acc = fma(b[0], rp, fma(b[size_t(np_) * nv], rv, fma(b[size_t(2 * np_) * nv], ra, acc)));
                 }
             }
-            Real g = Real(0);
-#pragma unroll
-            for (int i = 0; i < kMaxNv; ++i)
-                if (lane == i) g = gacc[i];
+            for (int off = nseg >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+            const Real g = acc;
             Real *lam = sLam + (s * DIMS + ax) * nv;
             Real *cc = sC + (s * DIMS + ax) * nf;
             const Real *xi = sXi + (s * DIMS + ax) * nf;
-            Real *u = sU + (s * DIMS + ax) * nf;
-            const int col = col_lo + lane, f = col - kFree0;
-            const bool is_free = lane < ng && f >= 0 && f < nf;
-            if (lane < ng) lam[col] -= rho * g;
-            if (is_free) u[f] = xi[f] + lam[col] - rho * g - cc[f];
-            __syncwarp();
-            if (is_free) {
-                Real du = Real(0);
-                for (int j = 0; j < nf; ++j) du = fma(sW[f * nf + j], u[j], du);
-                cc[f] += du;
+            const Real lam_new = col_ok ? lam[col] - rho * g : Real(0);
+            const Real u = is_free ? xi[fcol] + lam_new - rho * g - cc[fcol] : Real(0);
+            Real du = Real(0);
+            for (int j = 0; j < nf; ++j) {
+                const Real uj = __shfl_sync(kFull, u, (j + kFree0 - col_lo) * nseg);
+                if (is_free) du = fma(sW[fcol * nf + j], uj, du);
             }
             __syncwarp();
+            if (seg == 0) {
+                if (col_ok) lam[col] = lam_new;
+                if (is_free) cc[fcol] += du;
+            }
         }
         __syncthreads();
     }
@@ -420,22 +438,30 @@ __global__ void __launch_bounds__(kMaxThreads) project_kernel(const ProjParams<R
     // ---- outputs: xi_bar (boundary coefficients from the closed form), lambda
     for (int e = tid; e < S_act * D; e += T) {
         const int s = e / D, d = e - s * D;
-        const int ax = d / nv, col = d - ax * nv, f = col - kFree0;
+        const int ax = d / nv, cl = d - ax * nv, f = cl - kFree0;
         const size_t gi = size_t(s0 + s) * D + d;
-        p.xi_bar[gi] = (f >= 0 && f < nf) ? double(sC[(s * DIMS + ax) * nf + f]) : p.cB[ax * kMaxNv + col];
-        if (p.lam_out) p.lam_out[gi] = double(sLam[(s * DIMS + ax) * nv + col]);
+        p.xi_bar[gi] = (f >= 0 && f < nf) ? double(sC[(s * DIMS + ax) * nf + f]) : p.cB[ax * kMaxNv + cl];
+        if (p.lam_out) p.lam_out[gi] = double(sLam[(s * DIMS + ax) * nv + cl]);
     }
 }
 
-template <typename Real, int DIMS, int R>
+template <typename Real, int DIMS, int R, int THREADS>
 cudaError_t launch_one(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st)
 {
     static size_t granted = 0;  // per instantiation
-    cudaError_t e = reserve_smem(project_kernel<Real, DIMS, R>, t.smem, granted);
+    cudaError_t e = reserve_smem(project_kernel<Real, DIMS, R, THREADS>, t.smem, granted);
     if (e != cudaSuccess) return e;
     const int grid = (p.N + t.S - 1) / t.S;
-    project_kernel<Real, DIMS, R><<<grid, t.threads, t.smem, st>>>(p);
+    project_kernel<Real, DIMS, R, THREADS><<<grid, THREADS, t.smem, st>>>(p);
     return cudaGetLastError();
+}
+
+// CTA size per (precision, dims): bounded by the registers the kernel needs.
+template <typename Real>
+int threads_for(int dims)
+{
+    if (sizeof(Real) == 8) return 256;
+    return dims == 2 ? 1024 : 512;
 }
 
 }  // namespace
@@ -446,29 +472,37 @@ size_t project_smem_bytes(const Shape &sh, int S, int C)
     return smem_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, S, C, sh.use_bounds).total * sizeof(Real);
 }
 
+// Tile choice: S samples per CTA so the grid covers the SMs once, then the
+// obstacle chunk count C that minimises the modelled critical path of the
+// pair loop (rounds of items x per-item work) within the shared-memory cap.
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm)
 {
     Tiling t;
     t.R = 4;
-    t.threads = kMaxThreads;
+    t.threads = threads_for<Real>(sh.dims);
     const size_t cap = 227 * 1024;
     int S = std::max(1, (n_samples + n_sm - 1) / n_sm);
-    int C = 1;
-    for (;;) {
-        const int groups = (S * sh.n_p + t.R - 1) / t.R;
-        // about two items per thread, at least ~4 obstacles per chunk
-        C = std::max(1, (2 * t.threads + groups / 2) / std::max(1, groups));
-        C = std::min(C, std::max(1, sh.n_obs / 4));
-        C = std::min(C, 16);
-        while (C > 1 && project_smem_bytes<Real>(sh, S, C) > cap) --C;
-        if (project_smem_bytes<Real>(sh, S, C) <= cap || S == 1) break;
-        S = std::max(1, S * 3 / 4);
+    while (S > 1 && project_smem_bytes<Real>(sh, S, 1) > cap) S = std::max(1, S * 3 / 4);
+    const double pair_cost = sh.dims == 2 ? 5.5 : 7.5, item_cost = 48.0;
+    const int groups = (((S * sh.n_p + t.R - 1) / t.R) + 31) & ~31;
+    int bestC = 1;
+    double best = 1e300;
+    const int cmax = std::max(1, std::min(16, sh.n_obs));
+    for (int C = 1; C <= cmax; ++C) {
+        if (project_smem_bytes<Real>(sh, S, C) > cap) break;
+        const int items = groups * C;
+        const int rounds = (items + t.threads - 1) / t.threads;
+        const int Cs = (sh.n_obs + C - 1) / C;
+        const double cost = rounds * (Cs * t.R * pair_cost + item_cost) + (C - 1) * 4.0;
+        if (cost < best - 1e-9) {
+            best = cost;
+            bestC = C;
+        }
     }
     t.S = S;
-    t.C = C;
-    t.smem = project_smem_bytes<Real>(sh, S, C);
-    if (S * sh.n_p < 2 * t.threads) t.threads = 256;
+    t.C = bestC;
+    t.smem = project_smem_bytes<Real>(sh, S, bestC);
     return t;
 }
 
@@ -476,8 +510,13 @@ template <typename Real>
 cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st)
 {
     if (p.N <= 0) return cudaSuccess;
-    if (p.dims == 2) return launch_one<Real, 2, 4>(p, t, st);
-    return launch_one<Real, 3, 4>(p, t, st);
+    if constexpr (sizeof(Real) == 8) {
+        if (p.dims == 2) return launch_one<Real, 2, 4, 256>(p, t, st);
+        return launch_one<Real, 3, 4, 256>(p, t, st);
+    } else {
+        if (p.dims == 2) return launch_one<Real, 2, 4, 1024>(p, t, st);
+        return launch_one<Real, 3, 4, 512>(p, t, st);
+    }
 }
 
 template size_t project_smem_bytes<float>(const Shape &, int, int);
