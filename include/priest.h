@@ -85,6 +85,9 @@ typedef struct {
     double smin[3], smax[3];
     int precision;         /* priest_precision */
     size_t hbm_budget;     /* bytes the serving loop may hold on the device; 0 = no limit */
+    int autotune;          /* 1: time candidate tilings of the projection kernel on the first
+                              call of each problem shape and keep the fastest (the first call
+                              then blocks for the trials); 0: cost-model tiling */
 } priest_config;
 
 /* One planning problem (Sec. II-A: eqs. acc_cost .. coll_multiagent). */

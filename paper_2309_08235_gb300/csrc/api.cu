@@ -9,8 +9,10 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -43,6 +45,7 @@ struct priest_loaded {
     double *xi = nullptr;   // N x D (host-driven projections)
     double *lam = nullptr;  // N x D
     bool default_mu = true, default_cov = true;
+    bool shape_ready = false;  // basis and Gram blocks computed for this shape
 };
 
 struct ServeRequest {
@@ -81,6 +84,8 @@ struct priest_ctx {
     size_t in_flight_bytes = 0;
     cudaStream_t serve_stream = nullptr;
     int *serve_status = nullptr;
+    // tilings chosen by the autotuner, per problem shape
+    std::map<std::vector<int>, Tiling> tuned;
     // instrumentation
     bool profile = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_used, prof_free;
@@ -233,7 +238,7 @@ Carve carve(const Shape &sh, bool fp32, int z_iters, bool proj_buffers)
     k.semi = take(sizeof(double) * nob * 2);
     k.tab64 = take(sizeof(double) * lay.total);
     k.tab32 = take(fp32 ? sizeof(float) * lay.total : 0);
-    k.cB = take(sizeof(double) * 3 * kMaxNv);
+    k.cB = take(sizeof(double) * kAuxDoubles);
     k.mu = take(sizeof(double) * D);
     k.cov = take(sizeof(double) * D * D);
     k.L = take(sizeof(double) * D * D);
@@ -327,6 +332,7 @@ priest_status scratch_for(priest_ctx *ctx, const Shape &sh, const priest_problem
         std::vector<double> c, v, s;
         order_obstacles(s2, pr->center, pr->vel, pr->semi, c, v, s, s2.n_static);
         h->sh = s2;
+        h->shape_ready = false;
         h->center = reinterpret_cast<double *>(b + k.center);
         h->vel = reinterpret_cast<double *>(b + k.vel);
         h->semi = reinterpret_cast<double *>(b + k.semi);
@@ -385,6 +391,7 @@ ProjParams<Real> proj_params(priest_ctx *ctx, priest_loaded *h, const Tiling &t)
     p.K = ctx->cfg.proj_iters;
     p.S = t.S;
     p.C = t.C;
+    p.WS = t.ws;
     p.rho = Real(sh.rho);
     p.vmax = Real(sh.vmax);
     p.amax = Real(sh.amax);
@@ -421,10 +428,72 @@ priest_status enqueue_setup(priest_ctx *ctx, priest_loaded *h, bool plan_mode, c
     sp.init_std = ctx->cfg.init_std;
     sp.chol_eps = ctx->cfg.chol_eps;
     sp.status = status;
+    sp.shape_ready = h->shape_ready ? 1 : 0;
     cudaError_t e = launch_setup(sp, st);
     ctx->launches++;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "setup kernel");
+    h->shape_ready = true;
     return PRIEST_OK;
+}
+
+// Autotuner: on the first call of a problem shape, time every candidate
+// tiling for a few iterations on the actual inputs (outputs are rewritten by
+// the real launch that follows; multipliers are not written back) and keep
+// the fastest.  Blocks while it runs.
+template <typename Real>
+Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, cudaStream_t st)
+{
+    const Tiling model = choose_tiling<Real>(sh, N, ctx->n_sm);
+    if (!ctx->cfg.autotune) return model;
+    const std::vector<int> key = {int(sizeof(Real)), sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, sh.n_static,
+                                  N, p.want_lambda, sh.use_bounds};
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) return it->second;
+    std::vector<Tiling> cands = tiling_candidates<Real>(sh, N, ctx->n_sm);
+    cands.push_back(model);
+    // marginal cost per iteration: time K = 2 and K = 10 and take the difference
+    const int k_lo = 2, k_hi = 10;
+    p.lam_out = nullptr;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Tiling best = model;
+    float best_ms = 1e30f;
+    for (const Tiling &t : cands) {
+        if (t.smem > size_t(227) * 1024) continue;
+        p.S = t.S;
+        p.C = t.C;
+        p.WS = t.ws;
+        float t_k[2] = {1e30f, 1e30f};
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            p.K = (rep == 0 || rep == 1) ? k_lo : k_hi;  // rep 0 warms up
+            cudaEventRecord(e0, st);
+            cudaError_t e = launch_project<Real>(p, t, st);
+            cudaEventRecord(e1, st);
+            ctx->launches++;
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                ok = false;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_k[rep - 1] = ms;
+        }
+        const float ms = ok ? (t_k[1] - t_k[0]) / float(k_hi - k_lo) : 1e30f;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (getenv("PRIEST_AUTOTUNE_LOG"))
+        fprintf(stderr, "priest autotune: %zu candidates, best S=%d C=%d R=%d threads=%d ws=%d (%.2f us / iteration)\n",
+                cands.size(), best.S, best.C, best.R, best.threads, best.ws, 1e3f * best_ms);
+    ctx->tuned[key] = best;
+    return best;
 }
 
 template <typename Real>
@@ -434,7 +503,7 @@ priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode
 {
     Shape sh = h->sh;
     sh.N = N;
-    const Tiling t = choose_tiling<Real>(sh, N, ctx->n_sm);
+    Tiling t = choose_tiling<Real>(sh, N, ctx->n_sm);
     if (t.smem > size_t(227) * 1024)
         return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory (reduce n_p / n_obs)");
     ProjParams<Real> p = proj_params<Real>(ctx, h, t);
@@ -450,6 +519,10 @@ priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode
     p.xi_bar = xb;
     p.r_out = r;
     p.c1_out = c1;
+    t = pick_tiling<Real>(ctx, sh, N, p, st);
+    p.S = t.S;
+    p.C = t.C;
+    p.WS = t.ws;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->profile && st == ctx->stream) {
         if (!ctx->prof_free.empty()) {

@@ -7,8 +7,11 @@ namespace priest {
 
 // In-place Cholesky of the D x D symmetric matrix A (row-major, shared
 // memory): on return the lower triangle holds L with A = L L^T and the strict
-// upper triangle is zeroed.  Left-looking, column by column.  Returns false
-// (to every thread) on a non-positive pivot.  All threads of the CTA call it.
+// upper triangle is zeroed.  Right-looking: per column one square root, a
+// parallel scaling of the column and a parallel rank-1 update of the trailing
+// lower triangle, so the serial chain is one sqrt and one division per
+// column.  Returns false (to every thread) on a non-positive pivot.  All
+// threads of the CTA call it.
 __device__ inline bool block_cholesky(double *A, int D, int *flag_smem)
 {
     const int tid = threadIdx.x, T = blockDim.x;
@@ -17,7 +20,6 @@ __device__ inline bool block_cholesky(double *A, int D, int *flag_smem)
     for (int j = 0; j < D; ++j) {
         if (tid == 0) {
             double s = A[j * D + j];
-            for (int k = 0; k < j; ++k) s -= A[j * D + k] * A[j * D + k];
             if (!(s > 0.0)) {
                 *flag_smem = 0;
                 s = 1.0;
@@ -25,11 +27,14 @@ __device__ inline bool block_cholesky(double *A, int D, int *flag_smem)
             A[j * D + j] = sqrt(s);
         }
         __syncthreads();
-        const double djj = A[j * D + j];
-        for (int i = j + 1 + tid; i < D; i += T) {
-            double t = A[i * D + j];
-            for (int k = 0; k < j; ++k) t -= A[i * D + k] * A[j * D + k];
-            A[i * D + j] = t / djj;
+        const double inv = 1.0 / A[j * D + j];
+        for (int i = j + 1 + tid; i < D; i += T) A[i * D + j] *= inv;
+        __syncthreads();
+        // trailing update A[i][k] -= L[i][j] L[k][j] for j < k <= i
+        const int m = D - j - 1;
+        for (int e = tid; e < m * m; e += T) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) A[i * D + k] -= A[i * D + j] * A[k * D + j];
         }
         __syncthreads();
     }

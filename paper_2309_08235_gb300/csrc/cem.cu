@@ -6,6 +6,8 @@
 //       weights exp(-(c_aug - delta)/gamma), delta = min c_aug;
 //   a12 the next sampling factor chol(Sigma' + eps I), eps = chol_eps tr(Sigma')/D,
 //       by the last CTA of the refit grid.
+#include <algorithm>
+
 #include "block_linalg.cuh"
 #include "priest_internal.cuh"
 
@@ -14,7 +16,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSelectThreads = 1024;
-constexpr int kRefitThreads = 128;
+constexpr int kRefitThreads = 256;
+constexpr int kMaxEliteSort = PRIEST_MAX_ELITE;  // elites sorted in static shared memory
 
 // Order-preserving map of an FP64 key to uint64 (NaN sorts after +inf).
 __device__ __forceinline__ unsigned long long order_key(double x)
@@ -81,36 +84,145 @@ __device__ void bitonic_sort(unsigned long long *key, int *idx, int n2)
     }
 }
 
+// k-th smallest (1-based) composite key (key, index) among the elements with
+// member[i] != 0, by most-significant-digit radix select: 8 passes over the
+// 64-bit key and 2 over the index (indices are below 2^16), each pass a
+// 256-bin histogram of the surviving candidates (warp-aggregated atomics)
+// and a scan by one warp.  Composite keys are distinct, so the result is the
+// unique element with exactly k - 1 smaller ones.
+__device__ void radix_select(const unsigned long long *key, const unsigned char *member, int N, int k,
+                             unsigned *hist, unsigned long long *out_key, int *out_idx, int *s_k)
+{
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+    unsigned long long pkey = 0ull;  // decided high bits of the key
+    unsigned pidx = 0u;              // decided high bits of the index
+    if (tid == 0) *s_k = k;
+    for (int pass = 0; pass < 10; ++pass) {
+        for (int b = tid; b < 256; b += T) hist[b] = 0u;
+        __syncthreads();
+        const bool on_key = pass < 8;
+        const int shift = on_key ? 56 - 8 * pass : 8 - 8 * (pass - 8);
+        for (int base = 0; base < N; base += T) {
+            const int i = base + tid;
+            int digit = -1;
+            if (i < N && member[i]) {
+                const unsigned long long kk = key[i];
+                bool match;
+                if (on_key) {
+                    match = (pass == 0) || ((kk >> (shift + 8)) == pkey);
+                    if (match) digit = int((kk >> shift) & 0xffull);
+                } else {
+                    match = (kk == pkey) && (pass == 8 || (unsigned(i) >> (shift + 8)) == pidx);
+                    if (match) digit = (i >> shift) & 0xff;
+                }
+            }
+            const unsigned grp = __match_any_sync(kFull, digit);
+            if (digit >= 0 && lane == __ffs(grp) - 1) atomicAdd(&hist[digit], unsigned(__popc(grp)));
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // find the bin holding the k-th candidate: scan 256 bins, 8 per lane
+            unsigned c[8], sum = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = hist[lane * 8 + q];
+                sum += c[q];
+            }
+            unsigned incl = sum;
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned v = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += v;
+            }
+            const unsigned excl = incl - sum;
+            const unsigned kk = unsigned(*s_k);
+            int found = -1;
+            unsigned before = 0u;
+            if (kk > excl && kk <= incl) {
+                unsigned run = excl;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (found < 0 && kk <= run + c[q]) {
+                        found = lane * 8 + q;
+                        before = run;
+                    }
+                    run += c[q];
+                }
+            }
+            const unsigned owner = __ballot_sync(kFull, found >= 0);
+            const int src = __ffs(owner) - 1;
+            const int digit = __shfl_sync(kFull, found, src);
+            const unsigned bef = __shfl_sync(kFull, before, src);
+            if (lane == 0) {
+                *s_k = int(kk - bef);
+                hist[256] = unsigned(digit);
+            }
+        }
+        __syncthreads();
+        const unsigned digit = hist[256];
+        if (on_key)
+            pkey = (pkey << 8) | digit;
+        else
+            pidx = (pidx << 8) | digit;
+        __syncthreads();
+    }
+    *out_key = pkey;
+    *out_idx = int(pidx);
+}
+
+__device__ __forceinline__ bool le_composite(unsigned long long ka, int ia, unsigned long long kb, int ib)
+{
+    return ka < kb || (ka == kb && ia <= ib);
+}
+
+// ConstraintEliteSet: the n_proj least (r, index); EliteSet: the n_elite least
+// (c_aug, index) among them, written in ascending order.
 __global__ void __launch_bounds__(kSelectThreads)
     select_kernel(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int n2 = 32;
-    while (n2 < N) n2 <<= 1;
-    unsigned long long *key = reinterpret_cast<unsigned long long *>(smem_raw);
-    int *idx = reinterpret_cast<int *>(key + n2);
+    unsigned long long *kr = reinterpret_cast<unsigned long long *>(smem_raw);  // N
+    unsigned long long *kc = kr + N;                                             // N
+    unsigned char *member = reinterpret_cast<unsigned char *>(kc + N);           // N
+    __shared__ unsigned hist[257];
+    __shared__ int s_k, s_cnt;
+    __shared__ unsigned long long s_tkey;
+    __shared__ int s_tidx;
+    __shared__ unsigned long long s_ek[kMaxEliteSort];
+    __shared__ int s_ei[kMaxEliteSort];
     const int tid = threadIdx.x, T = blockDim.x;
-    // ConstraintEliteSet: sort by (r, index)
-    for (int e = tid; e < n2; e += T) {
-        key[e] = (e < N) ? order_key(r[e]) : ~0ull;
-        idx[e] = e;
+    for (int i = tid; i < N; i += T) {
+        kr[i] = order_key(r[i]);
+        kc[i] = order_key(c1[i] + r[i]);
+        member[i] = 1;
     }
-    bitonic_sort(key, idx, n2);
-    // EliteSet: the first n_proj re-keyed by c_aug = c_1 + r
-    int m2 = 32;
-    while (m2 < n_proj) m2 <<= 1;
-    for (int e = tid; e < m2; e += T) {
-        if (e < n_proj) {
-            const int i = idx[e];
-            key[e] = order_key(c1[i] + r[i]);
-        } else {
-            key[e] = ~0ull;
-            idx[e] = 0x7fffffff;
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    unsigned long long tk;
+    int ti;
+    radix_select(kr, member, N, n_proj, hist, &tk, &ti, &s_k);
+    for (int i = tid; i < N; i += T) member[i] = le_composite(kr[i], i, tk, ti) ? 1 : 0;
+    __syncthreads();
+    radix_select(kc, member, N, n_elite, hist, &tk, &ti, &s_k);
+    // gather the elites, then order them by (c_aug, index)
+    int n2 = 32;
+    while (n2 < n_elite) n2 <<= 1;
+    for (int i = tid; i < N; i += T)
+        if (member[i] && le_composite(kc[i], i, tk, ti)) {
+            const int slot = atomicAdd(&s_cnt, 1);
+            s_ek[slot] = kc[i];
+            s_ei[slot] = i;
         }
+    __syncthreads();
+    for (int e = n_elite + tid; e < n2; e += T) {
+        s_ek[e] = ~0ull;
+        s_ei[e] = 0x7fffffff;
     }
-    bitonic_sort(key, idx, m2);
-    for (int e = tid; e < n_elite; e += T) elite_idx[e] = idx[e];
+    bitonic_sort(s_ek, s_ei, n2);
+    for (int e = tid; e < n_elite; e += T) elite_idx[e] = s_ei[e];
 }
+
+// Elite rows staged in shared memory per chunk (all of them when they fit).
+constexpr int kRefitChunkBytes = 96 * 1024;
 
 __global__ void __launch_bounds__(kRefitThreads)
     refit_kernel(int D, const double *xb, const double *r, const double *c1, const int *elite, int n_elite,
@@ -118,27 +230,30 @@ __global__ void __launch_bounds__(kRefitThreads)
                  double *Lout, unsigned *counter, int *status, double *best_out)
 {
     extern __shared__ __align__(16) double s_dyn[];
-    double *w = s_dyn;                 // n_elite
-    double *mnew = w + n_elite;        // D
-    double *A = mnew + D;              // D x D (last CTA)
-    __shared__ double s_red[kRefitThreads / 32];
-    __shared__ double s_sw;
-    __shared__ int s_last, s_flag;
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int row = blockIdx.x;
+    const int chunk = max(1, min(n_elite, int(kRefitChunkBytes / (sizeof(double) * D))));
+    double *w = s_dyn;                 // n_elite weights
+    double *mnew = w + n_elite;        // D
+    double *part = mnew + D;           // T partial sums
+    double *xe = part + T;             // chunk x D staged elite rows
+    double *A = xe;                    // D x D (last CTA, reuses the staging area)
+    __shared__ double s_red[kRefitThreads / 32];
+    __shared__ double s_sw, s_tr;
+    __shared__ int s_last, s_flag;
 
     // weights: elites are sorted by c_aug, so delta = c_aug of the first
     const int e0 = elite[0];
     const double delta = c1[e0] + r[e0];
-    double part = 0.0;
+    double psum = 0.0;
     for (int m = tid; m < n_elite; m += T) {
         const int i = elite[m];
         const double wm = exp(-((c1[i] + r[i]) - delta) / gamma);
         w[m] = wm;
-        part += wm;
+        psum += wm;
     }
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(kFull, part, off);
-    if (lane == 0) s_red[warp] = part;
+    for (int off = 16; off > 0; off >>= 1) psum += __shfl_xor_sync(kFull, psum, off);
+    if (lane == 0) s_red[warp] = psum;
     __syncthreads();
     if (tid == 0) {
         double sw = 0.0;
@@ -147,24 +262,52 @@ __global__ void __launch_bounds__(kRefitThreads)
     }
     __syncthreads();
     const double sw = s_sw;
-    // new mean (eq. update_mean); every CTA forms it, CTA 0 publishes it
-    for (int d = tid; d < D; d += T) {
+    // thread (d, slice): column d, elites m = slice, slice + nslice, ...
+    const int nslice = max(1, T / D);
+    const int d = tid % D, slice = tid / D;
+    const bool worker = slice < nslice;
+    // pass 1: new mean (eq. update_mean); every CTA forms it, CTA 0 publishes it
+    double acc = 0.0;
+    for (int m0 = 0; m0 < n_elite; m0 += chunk) {
+        const int mc = min(chunk, n_elite - m0);
+        __syncthreads();
+        for (int e = tid; e < mc * D; e += T) xe[e] = xb[size_t(elite[m0 + e / D]) * D + e % D];
+        __syncthreads();
+        if (worker)
+            for (int m = slice; m < mc; m += nslice) acc = fma(w[m0 + m], xe[m * D + d], acc);
+    }
+    part[tid] = worker ? acc : 0.0;
+    __syncthreads();
+    if (tid < D) {
         double s = 0.0;
-        for (int m = 0; m < n_elite; ++m) s += w[m] * xb[size_t(elite[m]) * D + d];
-        mnew[d] = (1.0 - sigma) * mu[d] + sigma * (s / sw);
+        for (int k = 0; k < nslice; ++k) s += part[k * D + tid];
+        mnew[tid] = (1.0 - sigma) * mu[tid] + sigma * (s / sw);
     }
     __syncthreads();
-    // row `row` of the new covariance (eq. update_covariance, around the new mean)
-    for (int j = tid; j < D; j += T) {
-        double s = 0.0;
-        for (int m = 0; m < n_elite; ++m) {
-            const double *x = xb + size_t(elite[m]) * D;
-            s += w[m] * ((x[row] - mnew[row]) * (x[j] - mnew[j]));
+    // pass 2: row `row` of the new covariance (eq. update_covariance, around the new mean)
+    acc = 0.0;
+    const double mrow = mnew[row], md = mnew[d];
+    for (int m0 = 0; m0 < n_elite; m0 += chunk) {
+        const int mc = min(chunk, n_elite - m0);
+        if (m0 > 0 || chunk < n_elite) {
+            __syncthreads();
+            for (int e = tid; e < mc * D; e += T) xe[e] = xb[size_t(elite[m0 + e / D]) * D + e % D];
+            __syncthreads();
         }
-        cov[row * D + j] = (1.0 - sigma) * cov[row * D + j] + sigma * (s / sw);
+        if (worker)
+            for (int m = slice; m < mc; m += nslice)
+                acc = fma(w[m0 + m], (xe[m * D + row] - mrow) * (xe[m * D + d] - md), acc);
+    }
+    __syncthreads();
+    part[tid] = worker ? acc : 0.0;
+    __syncthreads();
+    if (tid < D) {
+        double s = 0.0;
+        for (int k = 0; k < nslice; ++k) s += part[k * D + tid];
+        cov[row * D + tid] = (1.0 - sigma) * cov[row * D + tid] + sigma * (s / sw);
     }
     if (row == 0)
-        for (int d = tid; d < D; d += T) mu_new[d] = mnew[d];
+        for (int q = tid; q < D; q += T) mu_new[q] = mnew[q];
     // last CTA: publish the mean, factor the new covariance, write the best elite
     __threadfence();
     __syncthreads();
@@ -172,8 +315,7 @@ __global__ void __launch_bounds__(kRefitThreads)
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int d = tid; d < D; d += T) mu[d] = mu_new[d];
-    __shared__ double s_tr;
+    for (int q = tid; q < D; q += T) mu[q] = mu_new[q];
     if (tid == 0) {
         double tr = 0.0;
         for (int i = 0; i < D; ++i) tr += cov[i * D + i];
@@ -189,7 +331,7 @@ __global__ void __launch_bounds__(kRefitThreads)
         if (!ok) atomicOr(status, kStatusCholesky);
         *counter = 0u;
     }
-    for (int d = tid; d < D; d += T) best_out[d] = xb[size_t(e0) * D + d];
+    for (int q = tid; q < D; q += T) best_out[q] = xb[size_t(e0) * D + q];
     if (tid == 0) {
         best_out[D] = r[e0];
         best_out[D + 1] = c1[e0];
@@ -203,9 +345,7 @@ __global__ void __launch_bounds__(kRefitThreads)
 cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx,
                           cudaStream_t st)
 {
-    int n2 = 32;
-    while (n2 < N) n2 <<= 1;
-    const size_t smem = size_t(n2) * (sizeof(unsigned long long) + sizeof(int));
+    const size_t smem = size_t(N) * (2 * sizeof(unsigned long long) + 1) + 16;
     static size_t granted = 0;
     cudaError_t e = reserve_smem(select_kernel, smem, granted);
     if (e != cudaSuccess) return e;
@@ -218,7 +358,9 @@ cudaError_t launch_refit(int D, const double *xb, const double *r, const double 
                          double *mu_new, double *L, unsigned *counter, int *status, double *best_out,
                          cudaStream_t st)
 {
-    const size_t smem = (size_t(n_elite) + D + size_t(D) * D) * sizeof(double);
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>(n_elite, 96 * 1024 / (sizeof(double) * D)));
+    const size_t stage = std::max(chunk * D, size_t(D) * D);
+    const size_t smem = (size_t(n_elite) + D + kRefitThreads + stage) * sizeof(double);
     static size_t granted = 0;
     cudaError_t e = reserve_smem(refit_kernel, smem, granted);
     if (e != cudaSuccess) return e;

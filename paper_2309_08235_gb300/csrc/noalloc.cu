@@ -104,7 +104,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     const size_t off_semi = o;
     o = up256(o + sizeof(double) * nob * 2);
     const size_t off_cB = o;
-    o = up256(o + sizeof(double) * 3 * kMaxNv);
+    o = up256(o + sizeof(double) * kAuxDoubles);
     const size_t off_tab64 = o;
     o = up256(o + sizeof(double) * lay.total);
     const size_t off_tab32 = o;
@@ -168,7 +168,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         std::memset(&p, 0, sizeof(p));
         p.dims = sh.dims; p.nv = sh.nv; p.nf = sh.nf; p.n_p = sh.n_p; p.n_obs = sh.n_obs;
         p.n_static = 0; p.use_bounds = sh.use_bounds; p.N = n; p.K = cfg->proj_iters;
-        p.S = t.S; p.C = t.C; p.mode = 0;
+        p.S = t.S; p.C = t.C; p.WS = t.ws; p.mode = 0;
         p.rho = float(sh.rho); p.vmax = float(sh.vmax); p.amax = float(sh.amax);
         for (int ax = 0; ax < 3; ++ax) { p.smin[ax] = float(sh.smin[ax]); p.smax[ax] = float(sh.smax[ax]); }
         p.tab = reinterpret_cast<const float *>(base + off_tab32);
@@ -184,7 +184,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         std::memset(&p, 0, sizeof(p));
         p.dims = sh.dims; p.nv = sh.nv; p.nf = sh.nf; p.n_p = sh.n_p; p.n_obs = sh.n_obs;
         p.n_static = 0; p.use_bounds = sh.use_bounds; p.N = n; p.K = cfg->proj_iters;
-        p.S = t.S; p.C = t.C; p.mode = 0;
+        p.S = t.S; p.C = t.C; p.WS = t.ws; p.mode = 0;
         p.rho = sh.rho; p.vmax = sh.vmax; p.amax = sh.amax;
         for (int ax = 0; ax < 3; ++ax) { p.smin[ax] = sh.smin[ax]; p.smax[ax] = sh.smax[ax]; }
         p.tab = sp.tab64;

@@ -6,12 +6,17 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "priest.h"
 
 namespace priest {
 
 constexpr int kMaxNv = PRIEST_MAX_NV;
 constexpr int kFree0 = 3;  // c_0, c_1, c_2 are fixed by the start position / velocity / acceleration
+
+// Doubles of the per-problem FP64 side buffer: fixed coefficients + Gram blocks.
+constexpr int kAuxDoubles = 3 * PRIEST_MAX_NV + 3 * PRIEST_MAX_NV * PRIEST_MAX_NV;
 
 // Bits of the device status word.
 enum : int {
@@ -33,18 +38,24 @@ struct Shape {
 // conditions (mask 0, 1, 3, 7 -> 0, 1, 2, 3).
 inline int final_fixed(int mask) { return mask == 7 ? 3 : mask == 3 ? 2 : mask == 1 ? 1 : 0; }
 
-// Obstacle record stride in Real units.
-__host__ __device__ inline int obs_stride(int dims) { return dims == 2 ? 8 : 12; }
+// Obstacle record stride in Real units (see the setup kernel for the fields).
+__host__ __device__ inline int obs_stride(int dims) { return dims == 2 ? 12 : 16; }
 
 __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7); }
+
+// Free-coefficient count rounded up to a multiple of 4 (row stride of the
+// packed per-time-stamp basis and of the per-sample coefficient rows).
+__host__ __device__ inline int nf_padded(int nf) { return (nf + 3) & ~3; }
 
 // Per-problem device tables, in units of Real, one contiguous buffer.
 struct TableLayout {
     size_t basis;  // [3][n_p][nv]   P, Pd, Pdd
+    size_t fb;     // [n_p][3][nfp]  free columns of P, Pd, Pdd per time stamp (padded to nfp)
     size_t base;   // [3][n_p][dims] contribution of the fixed coefficients
     size_t W;      // [nf][nf]       (I + rho Q_FF)^-1
     size_t obs;    // [n_obs][stride] pre-scaled obstacle records (static first)
     size_t tval;   // [n_p]          time stamps
+    size_t origin; // [3]            shift applied to positions and obstacle centres
     size_t total;
 };
 
@@ -54,6 +65,8 @@ __host__ __device__ inline TableLayout table_layout(int dims, int nv, int nf, in
     size_t o = 0;
     t.basis = o;
     o = align8(o + size_t(3) * n_p * nv);
+    t.fb = o;
+    o = align8(o + size_t(3) * n_p * nf_padded(nf));
     t.base = o;
     o = align8(o + size_t(3) * n_p * dims);
     t.W = o;
@@ -62,6 +75,8 @@ __host__ __device__ inline TableLayout table_layout(int dims, int nv, int nf, in
     o = align8(o + size_t(n_obs) * obs_stride(dims));
     t.tval = o;
     o = align8(o + size_t(n_p));
+    t.origin = o;
+    o = align8(o + 3);
     t.total = o;
     return t;
 }
@@ -75,7 +90,9 @@ struct SetupParams {
     double *tab64;                      // FP64 tables (always written)
     void *tab;                          // working tables: == tab64 for FP64, else float copy
     int real_is_double;
-    double *cB;                         // [3][nv] fixed coefficient values (FP64)
+    double *cB;                         // [3][kMaxNv] fixed coefficient values (FP64), followed by
+                                        // [3][kMaxNv][kMaxNv] Gram blocks of the free coefficients
+    int shape_ready;                    // 1: basis, time stamps and Gram blocks are already in place
     double *mu, *cov, *L;               // D, D x D, D x D (plan mode) or null
     int default_mu, default_cov;
     double init_std, chol_eps;
@@ -86,7 +103,7 @@ struct SetupParams {
 template <typename Real>
 struct ProjParams {
     int dims, nv, nf, n_p, n_obs, n_static, use_bounds;
-    int N, K, S, C, want_lambda, mode;  // mode 0: xi_in given; 1: xi = mu + L z
+    int N, K, S, C, WS, want_lambda, mode;  // mode 0: xi_in given; 1: xi = mu + L z; WS warps per sample
     Real rho, vmax, amax, smin[3], smax[3];
     const Real *tab;
     TableLayout lay;
@@ -101,6 +118,7 @@ struct Tiling {
     int C;        // obstacle chunks per CTA
     int threads;  // CTA size
     int R;        // points per obstacle-loop item (template value)
+    int ws;       // warps per sample
     size_t smem;  // dynamic shared memory bytes
 };
 
@@ -126,6 +144,14 @@ cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStrea
 
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm);
+
+template <typename Real>
+std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm);
+
+// One compiled kernel variant (explicitly instantiated in project_f32_*.cu /
+// project_f64.cu).
+template <typename Real, int DIMS, int R, int THREADS>
+cudaError_t launch_variant(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st);
 
 cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, int n_elite,
                           int *elite_idx, cudaStream_t st);

@@ -1,0 +1,13 @@
+// project_f32_2d.cu -- explicit instantiations of the fused projection kernel (FP32, 2-D).
+#include "project_kernel.cuh"
+
+namespace priest {
+
+template cudaError_t launch_variant<float, 2, 4, 512>(const ProjParams<float> &, const Tiling &,
+                                                         cudaStream_t);
+template cudaError_t launch_variant<float, 2, 8, 512>(const ProjParams<float> &, const Tiling &,
+                                                         cudaStream_t);
+template cudaError_t launch_variant<float, 2, 4, 1024>(const ProjParams<float> &, const Tiling &,
+                                                         cudaStream_t);
+
+}  // namespace priest

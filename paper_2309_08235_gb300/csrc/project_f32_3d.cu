@@ -1,0 +1,11 @@
+// project_f32_3d.cu -- explicit instantiations of the fused projection kernel (FP32, 3-D).
+#include "project_kernel.cuh"
+
+namespace priest {
+
+template cudaError_t launch_variant<float, 3, 4, 256>(const ProjParams<float> &, const Tiling &,
+                                                         cudaStream_t);
+template cudaError_t launch_variant<float, 3, 4, 512>(const ProjParams<float> &, const Tiling &,
+                                                         cudaStream_t);
+
+}  // namespace priest

@@ -18,7 +18,9 @@
 namespace priest {
 namespace {
 
-constexpr int kSetupThreads = 256;
+constexpr int kSetupThreads = 512;
+// The FP64 basis is staged in shared memory when it fits.
+constexpr size_t kSetupBasisSmem = 160 * 1024;
 
 // Bernstein values of degree n, n-1 and n-2 at tau by the triangular
 // recurrence B_{j,m} = (1 - tau) B_{j,m-1} + tau B_{j-1,m-1}.
@@ -62,9 +64,18 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     __shared__ double s_M[kMaxNv][2 * kMaxNv];
     __shared__ double s_fcol[kMaxNv];
     __shared__ int s_flag;
-    extern __shared__ double s_dyn[];  // D x D for the Cholesky
+    extern __shared__ double s_dyn[];  // D x D for the Cholesky, then the staged basis
+    const size_t nbasis = size_t(3) * np_ * nv;
+    const bool staged = nbasis * sizeof(double) <= kSetupBasisSmem;
+    double *bsrc = staged ? s_dyn + size_t(sh.D) * sh.D : basis;  // where the sums read the basis
 
-    // (1) basis rows and time stamps
+    double *gram = p.cB + 3 * kMaxNv;  // [3][kMaxNv][kMaxNv]
+    // (1) basis rows and time stamps (once per problem shape; afterwards only
+    //     staged back into shared memory)
+    if (p.shape_ready) {
+        if (staged)
+            for (size_t e = tid; e < nbasis; e += T) bsrc[e] = basis[e];
+    } else
     for (int t = tid; t < np_; t += T) {
         const double tau = double(t) / double(np_ - 1);
         double bn[kMaxNv], bn1[kMaxNv], bn2[kMaxNv];
@@ -77,8 +88,23 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
             basis[(0 * np_ + t) * nv + j] = bn[j];
             basis[(1 * np_ + t) * nv + j] = d1 / sh.horizon;
             basis[(2 * np_ + t) * nv + j] = d2 / (sh.horizon * sh.horizon);
+            if (staged) {
+                bsrc[(0 * np_ + t) * nv + j] = bn[j];
+                bsrc[(1 * np_ + t) * nv + j] = d1 / sh.horizon;
+                bsrc[(2 * np_ + t) * nv + j] = d2 / (sh.horizon * sh.horizon);
+            }
         }
         tval[t] = sh.horizon * double(t) / double(np_ - 1);
+    }
+    __syncthreads();
+    // (1b) packed free columns per time stamp: fb[t][q][f] = B_q[t][3 + f]
+    if (!p.shape_ready) {
+        const int nfp = nf_padded(nf);
+        double *fb = tab64 + lay.fb;
+        for (int e = tid; e < np_ * 3 * nfp; e += T) {
+            const int f = e % nfp, q = (e / nfp) % 3, t = e / (3 * nfp);
+            fb[e] = (f < nf) ? basis[(q * np_ + t) * nv + kFree0 + f] : 0.0;
+        }
     }
     // (2) coefficients fixed by the boundary rows (closed form of A c = b)
     if (tid < dims) {
@@ -94,21 +120,32 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
         for (int j = 0; j < nv; ++j) p.cB[ax * kMaxNv + j] = s_cB[ax][j];
     }
     __syncthreads();
-    // (3) fixed-coefficient part of position / velocity / acceleration
+    // (3) fixed-coefficient part of position / velocity / acceleration; positions
+    //     are expressed relative to the start-goal midpoint (the origin)
+    __shared__ double s_org[3];
+    if (tid < 3) s_org[tid] = (tid < dims) ? 0.5 * (sh.b0[tid][0] + sh.bf[tid][0]) : 0.0;
+    __syncthreads();
+    if (tid < 3) tab64[lay.origin + tid] = s_org[tid];
     const int f1 = kFree0 + nf;  // first fixed coefficient at the final end
     for (int e = tid; e < 3 * np_ * dims; e += T) {
         const int ax = e % dims, qt = e / dims;  // qt = q * np_ + t
         double s = 0.0;
         for (int j = 0; j < nv; ++j)
-            if (j < kFree0 || j >= f1) s += basis[qt * nv + j] * s_cB[ax][j];
-        base[qt * dims + ax] = s;
+            if (j < kFree0 || j >= f1) s += bsrc[qt * nv + j] * s_cB[ax][j];
+        base[qt * dims + ax] = (qt < np_) ? s - s_org[ax] : s;
     }
-    // (4) Gram blocks of the free coefficients: G_q = B_q,F^T B_q,F
+    // (4) Gram blocks of the free coefficients: G_q = B_q,F^T B_q,F (once per shape)
     for (int e = tid; e < 3 * nf * nf; e += T) {
         const int q = e / (nf * nf), i = (e / nf) % nf, j = e % nf;
-        double s = 0.0;
-        for (int t = 0; t < np_; ++t)
-            s += basis[(q * np_ + t) * nv + kFree0 + i] * basis[(q * np_ + t) * nv + kFree0 + j];
+        double s;
+        if (p.shape_ready) {
+            s = gram[(q * kMaxNv + i) * kMaxNv + j];
+        } else {
+            s = 0.0;
+            for (int t = 0; t < np_; ++t)
+                s += bsrc[(q * np_ + t) * nv + kFree0 + i] * bsrc[(q * np_ + t) * nv + kFree0 + j];
+            gram[(q * kMaxNv + i) * kMaxNv + j] = s;
+        }
         s_G[q][i][j] = s;
     }
     __syncthreads();
@@ -145,23 +182,37 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     }
     if (tid == 0 && !s_flag) atomicOr(p.status, kStatusKkt);
     for (int e = tid; e < nf * nf; e += T) W[e] = s_M[e / nf][nf + e % nf];
-    // (6) obstacle records, pre-scaled so one FMA per axis gives the scaled
-    //     offset (x - x_o) / a:  2-D [1/a, -x_o/a, -y_o/a, a, -v_x/a, -v_y/a, 0, 0]
-    //     3-D [1/a, -x_o/a, -y_o/a, -z_o/b, 1/b, a, b, 0, -v_x/a, -v_y/a, -v_z/b, 0]
+    // (6) obstacle records, centres relative to the origin.  The first four
+    //     values feed a conservative pre-filter: with p the point and o the
+    //     centre, |p|^2 - 2 p.o < a^2 - |o|^2 (+ margin) whenever the scaled
+    //     distance is below one; the exact test follows only for candidates.
+    //     2-D: [-2 o_x, -2 o_y, thr, a | 1/a, -o_x/a, -o_y/a, 0 | -v_x/a, -v_y/a, 0, 0]
+    //     3-D (kappa = a^2/b^2): [-2 o_x, -2 o_y, -2 kappa o_z, thr | kappa, a, b, 0 |
+    //          1/a, -o_x/a, -o_y/a, -o_z/b | 1/b, -v_x/a, -v_y/a, -v_z/b]
+    //     thr = a^2 - (o_x^2 + o_y^2 + kappa o_z^2) + margin, the margin covering
+    //     the rounding of the expanded form in the working precision.
     const int st = obs_stride(dims);
+    const double eps = p.real_is_double ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     for (int j = tid; j < sh.n_obs; j += T) {
         const double a = p.semi[2 * j], b = (dims == 3) ? p.semi[2 * j + 1] : a;
-        const double ia = 1.0 / a, ib = 1.0 / b;
+        const double ia = 1.0 / a, ib = 1.0 / b, kap = (a * a) / (b * b);
         double *o = obs + size_t(j) * st;
-        const double *c = p.center + j * dims;
         const double *v = p.vel + j * dims;
+        double c[3];
+        for (int ax = 0; ax < 3; ++ax) c[ax] = (ax < dims) ? p.center[j * dims + ax] - s_org[ax] : 0.0;
+        const double oo = c[0] * c[0] + c[1] * c[1] + (dims == 3 ? kap * c[2] * c[2] : 0.0);
+        const double on = sqrt(oo) + a + 1.0;
+        const double margin = 64.0 * eps * (4.0 * on * on) * (dims == 3 ? 1.0 + kap : 1.0);
+        const double thr = a * a - oo + margin;
         if (dims == 2) {
-            o[0] = ia; o[1] = -c[0] * ia; o[2] = -c[1] * ia; o[3] = a;
-            o[4] = -v[0] * ia; o[5] = -v[1] * ia; o[6] = 0.0; o[7] = 0.0;
+            o[0] = -2.0 * c[0]; o[1] = -2.0 * c[1]; o[2] = thr; o[3] = a;
+            o[4] = ia; o[5] = -c[0] * ia; o[6] = -c[1] * ia; o[7] = 0.0;
+            o[8] = -v[0] * ia; o[9] = -v[1] * ia; o[10] = 0.0; o[11] = 0.0;
         } else {
-            o[0] = ia; o[1] = -c[0] * ia; o[2] = -c[1] * ia; o[3] = -c[2] * ib;
-            o[4] = ib; o[5] = a; o[6] = b; o[7] = 0.0;
-            o[8] = -v[0] * ia; o[9] = -v[1] * ia; o[10] = -v[2] * ib; o[11] = 0.0;
+            o[0] = -2.0 * c[0]; o[1] = -2.0 * c[1]; o[2] = -2.0 * kap * c[2]; o[3] = thr;
+            o[4] = kap; o[5] = a; o[6] = b; o[7] = 0.0;
+            o[8] = ia; o[9] = -c[0] * ia; o[10] = -c[1] * ia; o[11] = -c[2] * ib;
+            o[12] = ib; o[13] = -v[0] * ia; o[14] = -v[1] * ia; o[15] = -v[2] * ib;
         }
     }
     // (7) full solve: default mean (straight-line coefficients) / covariance
@@ -200,7 +251,11 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
 
 cudaError_t launch_setup(const SetupParams &p, cudaStream_t st)
 {
-    const size_t dyn = size_t(p.sh.D) * p.sh.D * sizeof(double);
+    const size_t nbasis = size_t(3) * p.sh.n_p * p.sh.nv * sizeof(double);
+    const size_t dyn = size_t(p.sh.D) * p.sh.D * sizeof(double) + (nbasis <= kSetupBasisSmem ? nbasis : 0);
+    static size_t granted = 0;
+    cudaError_t e = reserve_smem(setup_kernel, dyn, granted);
+    if (e != cudaSuccess) return e;
     setup_kernel<<<1, kSetupThreads, dyn, st>>>(p, p.tab64);
     return cudaGetLastError();
 }

@@ -48,7 +48,7 @@ class priest_config(C.Structure):
         ("n_proj", C.c_int), ("n_elite", C.c_int), ("sigma_lr", C.c_double), ("gamma", C.c_double),
         ("chol_eps", C.c_double), ("init_std", C.c_double), ("vmax", C.c_double), ("amax", C.c_double),
         ("use_bounds", C.c_int), ("smin", C.c_double * 3), ("smax", C.c_double * 3),
-        ("precision", C.c_int), ("hbm_budget", C.c_size_t),
+        ("precision", C.c_int), ("hbm_budget", C.c_size_t), ("autotune", C.c_int),
     ]
 
 
@@ -142,7 +142,7 @@ def make_config(problem=None, cem=None, precision=PRIEST_FP32, hbm_budget=0, **o
         "gamma": float(c.get("gamma", 1.0)), "chol_eps": float(c.get("chol_eps", 1e-8)),
         "init_std": float(c.get("init_std", 2.0)), "vmax": float(p.get("vmax", 1.0)),
         "amax": float(p.get("amax", 1.0)), "use_bounds": int(bool(p.get("use_bounds", False))),
-        "precision": int(precision), "hbm_budget": int(hbm_budget),
+        "precision": int(precision), "hbm_budget": int(hbm_budget), "autotune": 1,
     }
     vals.update(over)
     for k, v in vals.items():
