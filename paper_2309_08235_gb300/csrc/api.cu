@@ -86,6 +86,7 @@ struct priest_ctx {
     int *serve_status = nullptr;
     // tilings chosen by the autotuner, per problem shape
     std::map<std::vector<int>, Tiling> tuned;
+    bool tune_cache_loaded = false;
     // instrumentation
     bool profile = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_used, prof_free;
@@ -436,6 +437,45 @@ priest_status enqueue_setup(priest_ctx *ctx, priest_loaded *h, bool plan_mode, c
     return PRIEST_OK;
 }
 
+// Optional persistent record of tuned tilings: the file named by the
+// environment variable PRIEST_TUNE_CACHE holds one line per shape,
+// "<10 key integers> S C R threads ws".  Read once per context, appended to
+// after each new tuning.
+void load_tune_cache(priest_ctx *ctx)
+{
+    const char *path = getenv("PRIEST_TUNE_CACHE");
+    if (!path || ctx->tune_cache_loaded) return;
+    ctx->tune_cache_loaded = true;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    std::vector<int> v(15);
+    for (;;) {
+        int got = 0;
+        for (int i = 0; i < 15; ++i) got += fscanf(f, "%d", &v[i]);
+        if (got != 15) break;
+        Tiling t;
+        t.S = v[10];
+        t.C = v[11];
+        t.R = v[12];
+        t.threads = v[13];
+        t.ws = v[14];
+        t.smem = 0;
+        ctx->tuned[std::vector<int>(v.begin(), v.begin() + 10)] = t;
+    }
+    fclose(f);
+}
+
+void save_tune_entry(const std::vector<int> &key, const Tiling &t)
+{
+    const char *path = getenv("PRIEST_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    for (int k : key) fprintf(f, "%d ", k);
+    fprintf(f, "%d %d %d %d %d\n", t.S, t.C, t.R, t.threads, t.ws);
+    fclose(f);
+}
+
 // Autotuner: on the first call of a problem shape, time every candidate
 // tiling for a few iterations on the actual inputs (outputs are rewritten by
 // the real launch that follows; multipliers are not written back) and keep
@@ -447,8 +487,13 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
     if (!ctx->cfg.autotune) return model;
     const std::vector<int> key = {int(sizeof(Real)), sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, sh.n_static,
                                   N, p.want_lambda, sh.use_bounds};
+    load_tune_cache(ctx);
     auto it = ctx->tuned.find(key);
-    if (it != ctx->tuned.end()) return it->second;
+    if (it != ctx->tuned.end()) {
+        Tiling t = it->second;
+        if (t.smem == 0) t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
+        return t;
+    }
     std::vector<Tiling> cands = tiling_candidates<Real>(sh, N, ctx->n_sm);
     cands.push_back(model);
     // marginal cost per iteration: time K = 2 and K = 10 and take the difference
@@ -493,6 +538,7 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
         fprintf(stderr, "priest autotune: %zu candidates, best S=%d C=%d R=%d threads=%d ws=%d (%.2f us / iteration)\n",
                 cands.size(), best.S, best.C, best.R, best.threads, best.ws, 1e3f * best_ms);
     ctx->tuned[key] = best;
+    save_tune_entry(key, best);
     return best;
 }
 

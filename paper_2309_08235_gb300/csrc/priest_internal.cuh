@@ -47,11 +47,20 @@ __host__ __device__ inline size_t align8(size_t x) { return (x + 7) & ~size_t(7)
 // packed per-time-stamp basis and of the per-sample coefficient rows).
 __host__ __device__ inline int nf_padded(int nf) { return (nf + 3) & ~3; }
 
+// Stride of one time stamp in the packed basis: 3 rows of nf_padded(nf),
+// plus 4 when needed so the stride is an odd multiple of 4 Real (16-byte
+// loads by consecutive lanes then hit distinct bank groups).
+__host__ __device__ inline int fb_stride(int nf)
+{
+    const int s = 3 * nf_padded(nf);
+    return ((s / 4) % 2 == 0) ? s + 4 : s;
+}
+
 // Per-problem device tables, in units of Real, one contiguous buffer.
 struct TableLayout {
     size_t basis;  // [3][n_p][nv]   P, Pd, Pdd
-    size_t fb;     // [n_p][3][nfp]  free columns of P, Pd, Pdd per time stamp (padded to nfp)
-    size_t base;   // [3][n_p][dims] contribution of the fixed coefficients
+    size_t fb;     // [n_p][fb_stride] free columns of P, Pd, Pdd per time stamp (rows of nfp)
+    size_t base;   // [3][dims][n_p] contribution of the fixed coefficients
     size_t W;      // [nf][nf]       (I + rho Q_FF)^-1
     size_t obs;    // [n_obs][stride] pre-scaled obstacle records (static first)
     size_t tval;   // [n_p]          time stamps
@@ -66,7 +75,7 @@ __host__ __device__ inline TableLayout table_layout(int dims, int nv, int nf, in
     t.basis = o;
     o = align8(o + size_t(3) * n_p * nv);
     t.fb = o;
-    o = align8(o + size_t(3) * n_p * nf_padded(nf));
+    o = align8(o + size_t(n_p) * fb_stride(nf));
     t.base = o;
     o = align8(o + size_t(3) * n_p * dims);
     t.W = o;

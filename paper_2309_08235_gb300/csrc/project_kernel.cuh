@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Re
     constexpr int NGM = NG > 0 ? NG : kMaxNv;
     constexpr int NFV = (NF + 3) / 4;  // float4 rows of the packed basis (NF > 0)
     const int nv = p.nv, nf = NF > 0 ? NF : p.nf, np_ = p.n_p, S = p.S, C = p.C;
-    const int nfp = nf_padded(nf);
+    const int nfp = nf_padded(nf), fbs = fb_stride(nf);
     const int D = DIMS * nv;
     const int s0 = blockIdx.x * S;
     const int S_act = min(S, p.N - s0);
@@ -347,13 +347,13 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Re
             Real pos[DIMS], vel[DIMS], acc[DIMS];
 #pragma unroll
             for (int ax = 0; ax < DIMS; ++ax) {
-                pos[ax] = sBase[(0 * np_ + t) * DIMS + ax];
-                vel[ax] = sBase[(1 * np_ + t) * DIMS + ax];
-                acc[ax] = sBase[(2 * np_ + t) * DIMS + ax];
+                pos[ax] = sBase[(0 * DIMS + ax) * np_ + t];
+                vel[ax] = sBase[(1 * DIMS + ax) * np_ + t];
+                acc[ax] = sBase[(2 * DIMS + ax) * np_ + t];
             }
             if constexpr (NF > 0) {
                 Real b[3][4 * NFV], cf[DIMS][4 * NFV];
-                const Real *fbt = sFb + size_t(t) * 3 * nfp;
+                const Real *fbt = sFb + size_t(t) * fbs;
 #pragma unroll
                 for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Re
                 if (p.use_bounds) rp += sRB[ax * PS + pp];
                 const Real rv = sRV[ax * PS + pp], ra = sRA[ax * PS + pp];
                 if constexpr (NF > 0 && NG == NF) {
-                    const Real *fbt = sFb + size_t(t) * 3 * nfp;
+                    const Real *fbt = sFb + size_t(t) * fbs;
                     Real b[3][4 * NFV];
 #pragma unroll
                     for (int q = 0; q < 3; ++q)

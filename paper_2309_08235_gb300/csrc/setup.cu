@@ -99,11 +99,11 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     __syncthreads();
     // (1b) packed free columns per time stamp: fb[t][q][f] = B_q[t][3 + f]
     if (!p.shape_ready) {
-        const int nfp = nf_padded(nf);
+        const int nfp = nf_padded(nf), fbs = fb_stride(nf);
         double *fb = tab64 + lay.fb;
-        for (int e = tid; e < np_ * 3 * nfp; e += T) {
-            const int f = e % nfp, q = (e / nfp) % 3, t = e / (3 * nfp);
-            fb[e] = (f < nf) ? basis[(q * np_ + t) * nv + kFree0 + f] : 0.0;
+        for (int e = tid; e < np_ * fbs; e += T) {
+            const int t = e / fbs, w = e - t * fbs, q = w / nfp, f = w - q * nfp;
+            fb[e] = (q < 3 && f < nf) ? basis[(q * np_ + t) * nv + kFree0 + f] : 0.0;
         }
     }
     // (2) coefficients fixed by the boundary rows (closed form of A c = b)
@@ -128,11 +128,11 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     if (tid < 3) tab64[lay.origin + tid] = s_org[tid];
     const int f1 = kFree0 + nf;  // first fixed coefficient at the final end
     for (int e = tid; e < 3 * np_ * dims; e += T) {
-        const int ax = e % dims, qt = e / dims;  // qt = q * np_ + t
+        const int t = e % np_, qa = e / np_, q = qa / dims, ax = qa - q * dims;  // e = (q * dims + ax) * np_ + t
         double s = 0.0;
         for (int j = 0; j < nv; ++j)
-            if (j < kFree0 || j >= f1) s += bsrc[qt * nv + j] * s_cB[ax][j];
-        base[qt * dims + ax] = (qt < np_) ? s - s_org[ax] : s;
+            if (j < kFree0 || j >= f1) s += bsrc[(q * np_ + t) * nv + j] * s_cB[ax][j];
+        base[e] = (q == 0) ? s - s_org[ax] : s;
     }
     // (4) Gram blocks of the free coefficients: G_q = B_q,F^T B_q,F (once per shape)
     for (int e = tid; e < 3 * nf * nf; e += T) {
