@@ -250,14 +250,13 @@ def run_ours(args):
     achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
     traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "traffic.json")
+    prof_path = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(prof_path):
-        try:
-            traffic = json.load(open(prof_path)).get("project_kernel_bytes_per_launch")
-        except Exception:
-            traffic = None
+        for ln in open(prof_path):
+            if ln.startswith("project_kernel_bytes_per_launch:"):
+                traffic = int(ln.split(":", 1)[1])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "project_kernel<float,2,4>",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "project_kernel (FP32, 2-D)",
                 "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
                 "flops_per_launch": flops_launch,
                 "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}

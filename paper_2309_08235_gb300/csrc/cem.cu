@@ -245,10 +245,14 @@ __global__ void __launch_bounds__(kRefitThreads)
     // weights: elites are sorted by c_aug, so delta = c_aug of the first
     const int e0 = elite[0];
     const double delta = c1[e0] + r[e0];
+    __shared__ double s_ig;
+    if (tid == 0) s_ig = 1.0 / gamma;
+    __syncthreads();
+    const double ig = s_ig;
     double psum = 0.0;
     for (int m = tid; m < n_elite; m += T) {
         const int i = elite[m];
-        const double wm = exp(-((c1[i] + r[i]) - delta) / gamma);
+        const double wm = exp(-((c1[i] + r[i]) - delta) * ig);
         w[m] = wm;
         psum += wm;
     }
@@ -278,10 +282,14 @@ __global__ void __launch_bounds__(kRefitThreads)
     }
     part[tid] = worker ? acc : 0.0;
     __syncthreads();
+    __shared__ double s_isw;
+    if (tid == 0) s_isw = 1.0 / sw;
+    __syncthreads();
+    const double isw = s_isw;
     if (tid < D) {
         double s = 0.0;
         for (int k = 0; k < nslice; ++k) s += part[k * D + tid];
-        mnew[tid] = (1.0 - sigma) * mu[tid] + sigma * (s / sw);
+        mnew[tid] = (1.0 - sigma) * mu[tid] + sigma * (s * isw);
     }
     __syncthreads();
     // pass 2: row `row` of the new covariance (eq. update_covariance, around the new mean)
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(kRefitThreads)
     if (tid < D) {
         double s = 0.0;
         for (int k = 0; k < nslice; ++k) s += part[k * D + tid];
-        cov[row * D + tid] = (1.0 - sigma) * cov[row * D + tid] + sigma * (s / sw);
+        cov[row * D + tid] = (1.0 - sigma) * cov[row * D + tid] + sigma * (s * isw);
     }
     if (row == 0)
         for (int q = tid; q < D; q += T) mu_new[q] = mnew[q];
@@ -319,10 +327,10 @@ __global__ void __launch_bounds__(kRefitThreads)
     if (tid == 0) {
         double tr = 0.0;
         for (int i = 0; i < D; ++i) tr += cov[i * D + i];
-        s_tr = tr;
+        s_tr = chol_eps * tr / double(D);
     }
     __syncthreads();
-    const double eps = chol_eps * s_tr / double(D);
+    const double eps = s_tr;
     for (int e = tid; e < D * D; e += T) A[e] = cov[e] + ((e / D == e % D) ? eps : 0.0);
     __syncthreads();
     const bool ok = block_cholesky(A, D, &s_flag);

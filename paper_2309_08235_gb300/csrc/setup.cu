@@ -41,10 +41,10 @@ __device__ void bernstein_levels(int n, double tau, double *bn, double *bn1, dou
 }
 
 template <typename Real>
-__device__ void write_tables(const SetupParams &p, const double *src, size_t count)
+__device__ void write_tables(const SetupParams &p, const double *src, size_t from, size_t to)
 {
     Real *dst = reinterpret_cast<Real *>(p.tab);
-    for (size_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = static_cast<Real>(src[i]);
+    for (size_t i = from + threadIdx.x; i < to; i += blockDim.x) dst[i] = static_cast<Real>(src[i]);
 }
 
 __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, double *tab64)
@@ -164,15 +164,16 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     }
     if (tid == 0) s_flag = 1;
     __syncthreads();
+    __shared__ double s_ipiv;
     for (int k = 0; k < nf; ++k) {
-        const double piv = s_M[k][k];
         if (tid < nf) s_fcol[tid] = s_M[tid][k];
-        __syncthreads();
-        if (!(piv > 0.0)) {
-            if (tid == 0) s_flag = 0;
-        } else {
-            for (int j = tid; j < 2 * nf; j += T) s_M[k][j] /= piv;
+        if (tid == 0) {
+            const double piv = s_M[k][k];
+            if (!(piv > 0.0)) s_flag = 0;
+            s_ipiv = (piv > 0.0) ? 1.0 / piv : 1.0;
         }
+        __syncthreads();
+        for (int j = tid; j < 2 * nf; j += T) s_M[k][j] *= s_ipiv;
         __syncthreads();
         for (int e = tid; e < nf * 2 * nf; e += T) {
             const int i = e / (2 * nf), j = e % (2 * nf);
@@ -195,13 +196,13 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     const double eps = p.real_is_double ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     for (int j = tid; j < sh.n_obs; j += T) {
         const double a = p.semi[2 * j], b = (dims == 3) ? p.semi[2 * j + 1] : a;
-        const double ia = 1.0 / a, ib = 1.0 / b, kap = (a * a) / (b * b);
+        const double ia = rcp_nr(a), ib = rcp_nr(b), kap = (a * a) * (ib * ib);
         double *o = obs + size_t(j) * st;
         const double *v = p.vel + j * dims;
         double c[3];
         for (int ax = 0; ax < 3; ++ax) c[ax] = (ax < dims) ? p.center[j * dims + ax] - s_org[ax] : 0.0;
         const double oo = c[0] * c[0] + c[1] * c[1] + (dims == 3 ? kap * c[2] * c[2] : 0.0);
-        const double on = sqrt(oo) + a + 1.0;
+        const double on = double(sqrtf(float(oo)) * 1.001f) + a + 1.0;  // bound only
         const double margin = 64.0 * eps * (4.0 * on * on) * (dims == 3 ? 1.0 + kap : 1.0);
         const double thr = a * a - oo + margin;
         if (dims == 2) {
@@ -232,10 +233,10 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
         if (tid == 0) {
             double tr = 0.0;
             for (int i = 0; i < D; ++i) tr += p.cov[i * D + i];
-            s_tr = tr;
+            s_tr = p.chol_eps * tr / double(D);
         }
         __syncthreads();
-        const double eps = p.chol_eps * s_tr / double(D);
+        const double eps = s_tr;
         for (int e = tid; e < D * D; e += T) s_dyn[e] = p.cov[e] + ((e / D == e % D) ? eps : 0.0);
         __syncthreads();
         const bool ok = block_cholesky(s_dyn, D, &s_flag);
@@ -244,7 +245,12 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     }
     __syncthreads();
     // (8) working-precision copy of the tables
-    if (!p.real_is_double) write_tables<float>(p, tab64, lay.total);
+    if (!p.real_is_double) {
+        if (p.shape_ready)
+            write_tables<float>(p, tab64, lay.base, lay.total);  // basis and packed basis unchanged
+        else
+            write_tables<float>(p, tab64, 0, lay.total);
+    }
 }
 
 }  // namespace
