@@ -192,6 +192,21 @@ priest_status priest_project_device(priest_ctx *ctx, priest_loaded *h, int n, co
                                     double *lambda_dev, double *xi_bar_dev, double *resid_dev,
                                     double *cost_dev);
 
+/* Batched solve (Alg. 1 for every problem) in shared launches: one setup
+ * launch for all problems, then per CEM iteration one persistent projection
+ * launch over the samples of every problem (CTAs pull (problem, sample range)
+ * items, most expensive first), one selection launch and one refit launch.
+ * Problems may differ in sample count, time stamps, horizon, bounds and
+ * obstacles; they must share dims, degree and bc_final_mask.
+ * probs: n handles from priest_load; z_dev[i]: L x N_i x D draws (device);
+ * out_dev[i]: D + 4 doubles (device), laid out as in priest_plan_device.
+ * The first call for a given (probs, z_dev, out_dev) list runs the launches
+ * directly and records them in a CUDA graph; later calls with the same list
+ * replay the graph.  Asynchronous on the context stream.  Errors:
+ * PRIEST_ERR_INVALID (mixed dims / degree / mask, n < 1), PRIEST_ERR_CUDA. */
+priest_status priest_plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs,
+                                const double *const *z_dev, double *const *out_dev);
+
 /* Waits for the context stream and reports any kernel-side error status. */
 priest_status priest_sync(priest_ctx *ctx);
 

@@ -48,6 +48,21 @@ struct priest_loaded {
     bool shape_ready = false;  // basis and Gram blocks computed for this shape
 };
 
+// Descriptors and recorded launch sequence of one batched solve.
+struct BatchPlan {
+    void *dev = nullptr;            // one allocation: params, setup params, CEM args, items, counters
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n = 0, n_items = 0, L = 0, D_max = 0;
+    size_t smem_proj = 0, smem_setup = 0, smem_select = 0, smem_refit = 0;
+    SetupParams *setup_dev = nullptr, *setup_dev_ready = nullptr;
+    void *params_dev = nullptr;     // L x n ProjParams<Real>
+    CemArgs *cem_dev = nullptr;
+    int2 *items_dev = nullptr;
+    int *counters_dev = nullptr;    // L
+    int dims = 0, nf = 0, nv = 0, dbl = 0;
+};
+
 struct ServeRequest {
     uint64_t ticket;
     Shape sh;
@@ -84,6 +99,8 @@ struct priest_ctx {
     size_t in_flight_bytes = 0;
     cudaStream_t serve_stream = nullptr;
     int *serve_status = nullptr;
+    // batched solves: recorded launch sequences, keyed by the handle / buffer lists
+    std::map<std::vector<uintptr_t>, BatchPlan *> batches;
     // tilings chosen by the autotuner, per problem shape
     std::map<std::vector<int>, Tiling> tuned;
     bool tune_cache_loaded = false;
@@ -791,9 +808,253 @@ void serve_loop(priest_ctx *ctx)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched solves.
+// ---------------------------------------------------------------------------
+void free_batch(BatchPlan *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->dev) cudaFree(b->dev);
+    delete b;
+}
+
+template <typename Real>
+priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
+                          double *const *out, BatchPlan *b)
+{
+    const int L = ctx->cfg.cem_iters;
+    const int threads = sizeof(Real) == 8 ? 256 : 512;
+    const int R = 4;
+    const Shape &s0 = probs[0]->sh;
+    b->n = n;
+    b->L = L;
+    b->dims = s0.dims;
+    b->nf = s0.nf;
+    b->nv = s0.nv;
+    b->dbl = sizeof(Real) == 8;
+    std::vector<ProjParams<Real>> params(size_t(L) * n);
+    std::vector<SetupParams> setups(n), setups_ready(n);
+    std::vector<CemArgs> cem(n);
+    std::vector<std::pair<double, int2>> items;
+    for (int i = 0; i < n; ++i) {
+        priest_loaded *h = probs[i];
+        const Shape &sh = h->sh;
+        if (sh.dims != s0.dims || sh.nv != s0.nv || sh.bc_mask != s0.bc_mask)
+            return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
+        // tiling: warp groups of 2 (2-D) or 1 (3-D) in a fixed CTA, chunks from the cost model
+        Tiling t;
+        t.R = R;
+        t.threads = threads;
+        t.ws = (sh.dims == 2 && sizeof(Real) == 4) ? 2 : 1;
+        t.S = std::max(1, std::min(sh.N, threads / (32 * t.ws)));
+        if (t.ws > 1) t.S = std::min(t.S, 15);
+        const int nblk32 = ((sh.n_p + 32 * R - 1) / (32 * R)) * 32;
+        t.C = std::max(1, std::min(std::min(16, std::max(1, sh.n_obs)), (32 * t.ws) / nblk32));
+        while (t.S > 1 && project_smem_bytes<Real>(sh, t.S, t.C) > size_t(227) * 1024) t.S = std::max(1, t.S / 2);
+        t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
+        if (t.smem > size_t(227) * 1024)
+            return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
+        b->smem_proj = std::max(b->smem_proj, t.smem);
+        ProjParams<Real> p = proj_params<Real>(ctx, h, t);
+        p.N = sh.N;
+        p.mode = 1;
+        p.mu = h->mu;
+        p.Lc = h->L;
+        p.want_lambda = 0;
+        p.xi_bar = h->xb;
+        p.r_out = h->r;
+        p.c1_out = h->c1;
+        for (int l = 0; l < L; ++l) {
+            p.z = z[i] + size_t(l) * sh.N * sh.D;
+            params[size_t(l) * n + i] = p;
+        }
+        const double cost = double(sh.n_p) * (double(sh.n_obs) + 12.0);
+        for (int s = 0; s < sh.N; s += t.S) items.push_back({cost * std::min(t.S, sh.N - s), make_int2(i, s)});
+        SetupParams sp;
+        std::memset(&sp, 0, sizeof(sp));
+        sp.sh = sh;
+        sp.center = h->center;
+        sp.vel = h->vel;
+        sp.semi = h->semi;
+        sp.tab64 = h->tab64;
+        sp.tab = h->tab32 ? static_cast<void *>(h->tab32) : static_cast<void *>(h->tab64);
+        sp.real_is_double = h->tab32 ? 0 : 1;
+        sp.cB = h->cB;
+        sp.mu = h->mu;
+        sp.cov = h->cov;
+        sp.L = h->L;
+        sp.default_mu = 1;
+        sp.default_cov = 1;
+        sp.init_std = ctx->cfg.init_std;
+        sp.chol_eps = ctx->cfg.chol_eps;
+        sp.status = ctx->d_status;
+        sp.shape_ready = h->shape_ready ? 1 : 0;
+        setups[i] = sp;
+        sp.shape_ready = 1;
+        setups_ready[i] = sp;
+        b->smem_setup = std::max(b->smem_setup, setup_smem_bytes(sh));
+        CemArgs a;
+        a.N = sh.N;
+        a.n_proj = sh.n_proj;
+        a.n_elite = sh.n_elite;
+        a.D = sh.D;
+        a.r = h->r;
+        a.c1 = h->c1;
+        a.xb = h->xb;
+        a.elite = h->elite;
+        a.sigma = ctx->cfg.sigma_lr;
+        a.gamma = ctx->cfg.gamma;
+        a.chol_eps = ctx->cfg.chol_eps;
+        a.mu = h->mu;
+        a.cov = h->cov;
+        a.mu_new = h->mu_new;
+        a.L = h->L;
+        a.counter = h->counter;
+        a.status = ctx->d_status;
+        a.best_out = out[i];
+        cem[i] = a;
+        b->smem_select = std::max(b->smem_select, select_smem_bytes(sh.N));
+        b->smem_refit = std::max(b->smem_refit, refit_smem_bytes(sh.D, sh.n_elite));
+        b->D_max = std::max(b->D_max, sh.D);
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) { return x.first > y.first; });
+    std::vector<int2> it(items.size());
+    for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
+    b->n_items = int(it.size());
+    // one device allocation for all descriptors
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = round_up(o + bytes);
+        return at;
+    };
+    const size_t o_params = take(sizeof(ProjParams<Real>) * params.size());
+    const size_t o_setup = take(sizeof(SetupParams) * n);
+    const size_t o_setup_r = take(sizeof(SetupParams) * n);
+    const size_t o_cem = take(sizeof(CemArgs) * n);
+    const size_t o_items = take(sizeof(int2) * it.size());
+    const size_t o_cnt = take(sizeof(int) * L);
+    cudaError_t e = cudaMalloc(&b->dev, o);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, PRIEST_ERR_NOMEM, "batch descriptors");
+    }
+    char *d = static_cast<char *>(b->dev);
+    b->params_dev = d + o_params;
+    b->setup_dev = reinterpret_cast<SetupParams *>(d + o_setup);
+    b->setup_dev_ready = reinterpret_cast<SetupParams *>(d + o_setup_r);
+    b->cem_dev = reinterpret_cast<CemArgs *>(d + o_cem);
+    b->items_dev = reinterpret_cast<int2 *>(d + o_items);
+    b->counters_dev = reinterpret_cast<int *>(d + o_cnt);
+    cudaStream_t st = ctx->stream;
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->params_dev, params.data(), sizeof(ProjParams<Real>) * params.size(),
+                                     cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev, setups.data(), sizeof(SetupParams) * n, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev_ready, setups_ready.data(), sizeof(SetupParams) * n,
+                                     cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->cem_dev, cem.data(), sizeof(CemArgs) * n, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->items_dev, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
+    return PRIEST_OK;
+}
+
+// The launch sequence of one batched solve.
+template <typename Real>
+priest_status batch_enqueue(priest_ctx *ctx, BatchPlan *b, bool shape_ready, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(b->counters_dev, 0, sizeof(int) * b->L, st);
+    if (e == cudaSuccess)
+        e = launch_setup_batch(shape_ready ? b->setup_dev_ready : b->setup_dev, b->n, b->smem_setup, st);
+    ctx->launches++;
+    const ProjParams<Real> *params = static_cast<const ProjParams<Real> *>(b->params_dev);
+    for (int l = 0; l < b->L && e == cudaSuccess; ++l) {
+        e = launch_project_batch<Real>(params + size_t(l) * b->n, b->items_dev, b->n_items, b->counters_dev + l,
+                                       b->dims, 4, 0, b->nf, b->nv, 0, b->smem_proj, 0, st);
+        if (e == cudaSuccess) e = launch_select_batch(b->cem_dev, b->n, b->smem_select, st);
+        if (e == cudaSuccess) e = launch_refit_batch(b->cem_dev, b->n, b->D_max, b->smem_refit, st);
+        ctx->launches += 3;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched launch");
+    return PRIEST_OK;
+}
+
+template <typename Real>
+priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
+                         double *const *out)
+{
+    std::vector<uintptr_t> key;
+    key.reserve(3 * size_t(n) + 1);
+    key.push_back(uintptr_t(n));
+    for (int i = 0; i < n; ++i) {
+        key.push_back(reinterpret_cast<uintptr_t>(probs[i]));
+        key.push_back(reinterpret_cast<uintptr_t>(z[i]));
+        key.push_back(reinterpret_cast<uintptr_t>(out[i]));
+    }
+    auto it = ctx->batches.find(key);
+    if (it != ctx->batches.end() && it->second->exec) {
+        cudaError_t e = cudaGraphLaunch(it->second->exec, ctx->stream);
+        ctx->launches += 1 + 3 * it->second->L;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+        return PRIEST_OK;
+    }
+    BatchPlan *b = new BatchPlan();
+    priest_status s = batch_build<Real>(ctx, n, probs, z, out, b);
+    if (s != PRIEST_OK) {
+        free_batch(b);
+        return s;
+    }
+    bool ready = true;
+    for (int i = 0; i < n; ++i) ready = ready && probs[i]->shape_ready;
+    s = batch_enqueue<Real>(ctx, b, ready, ctx->stream);  // direct run (also sets kernel attributes)
+    if (s != PRIEST_OK) {
+        free_batch(b);
+        return s;
+    }
+    for (int i = 0; i < n; ++i) probs[i]->shape_ready = true;
+    // record the sequence for replay
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess) {
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int64_t before = ctx->launches.load();
+            const priest_status ok = batch_enqueue<Real>(ctx, b, true, cap);
+            ctx->launches = before;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamEndCapture(cap, &g) == cudaSuccess && ok == PRIEST_OK && g) {
+                b->graph = g;
+                if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) b->exec = nullptr;
+            } else if (g) {
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();
+        cudaStreamDestroy(cap);
+    }
+    if (it != ctx->batches.end()) {
+        free_batch(it->second);
+        ctx->batches.erase(it);
+    }
+    ctx->batches[key] = b;
+    return PRIEST_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+priest_status priest_plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z_dev,
+                                double *const *out_dev)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    if (n < 1 || !probs || !z_dev || !out_dev) return fail(ctx, PRIEST_ERR_INVALID, "empty batch or NULL lists");
+    for (int i = 0; i < n; ++i)
+        if (!probs[i] || !z_dev[i] || !out_dev[i]) return fail(ctx, PRIEST_ERR_INVALID, "NULL entry in the batch");
+    if (ctx->cfg.precision == PRIEST_FP64_CHECK) return plan_batch<double>(ctx, n, probs, z_dev, out_dev);
+    return plan_batch<float>(ctx, n, probs, z_dev, out_dev);
+}
+
 
 priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out)
 {
@@ -854,6 +1115,7 @@ priest_status priest_destroy(priest_ctx *ctx)
     }
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_loaded(ctx->scratch);
+    for (auto &kv : ctx->batches) free_batch(kv.second);
     for (auto &ev : ctx->prof_used) {
         cudaEventDestroy(ev.first);
         cudaEventDestroy(ev.second);

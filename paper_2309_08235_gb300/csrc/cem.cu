@@ -176,8 +176,7 @@ __device__ __forceinline__ bool le_composite(unsigned long long ka, int ia, unsi
 
 // ConstraintEliteSet: the n_proj least (r, index); EliteSet: the n_elite least
 // (c_aug, index) among them, written in ascending order.
-__global__ void __launch_bounds__(kSelectThreads)
-    select_kernel(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx)
+__device__ void select_body(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *kr = reinterpret_cast<unsigned long long *>(smem_raw);  // N
@@ -221,17 +220,29 @@ __global__ void __launch_bounds__(kSelectThreads)
     for (int e = tid; e < n_elite; e += T) elite_idx[e] = s_ei[e];
 }
 
+__global__ void __launch_bounds__(kSelectThreads)
+    select_kernel(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx)
+{
+    select_body(N, r, c1, n_proj, n_elite, elite_idx);
+}
+
+__global__ void __launch_bounds__(kSelectThreads) select_batch_kernel(const CemArgs *args)
+{
+    const CemArgs a = args[blockIdx.x];
+    select_body(a.N, a.r, a.c1, a.n_proj, a.n_elite, a.elite);
+}
+
 // Elite rows staged in shared memory per chunk (all of them when they fit).
 constexpr int kRefitChunkBytes = 96 * 1024;
 
-__global__ void __launch_bounds__(kRefitThreads)
-    refit_kernel(int D, const double *xb, const double *r, const double *c1, const int *elite, int n_elite,
-                 double sigma, double gamma, double chol_eps, double *mu, double *cov, double *mu_new,
-                 double *Lout, unsigned *counter, int *status, double *best_out)
+// Row `row` of the refit of one problem; the last of its D CTAs (counted on
+// *counter) publishes the mean, factors the covariance and writes the best elite.
+__device__ void refit_body(int D, int row, const double *xb, const double *r, const double *c1, const int *elite,
+                           int n_elite, double sigma, double gamma, double chol_eps, double *mu, double *cov,
+                           double *mu_new, double *Lout, unsigned *counter, int *status, double *best_out)
 {
     extern __shared__ __align__(16) double s_dyn[];
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const int row = blockIdx.x;
     const int chunk = max(1, min(n_elite, int(kRefitChunkBytes / (sizeof(double) * D))));
     double *w = s_dyn;                 // n_elite weights
     double *mnew = w + n_elite;        // D
@@ -319,7 +330,7 @@ __global__ void __launch_bounds__(kRefitThreads)
     // last CTA: publish the mean, factor the new covariance, write the best elite
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (tid == 0) s_last = (atomicAdd(counter, 1u) == unsigned(D) - 1u);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -348,7 +359,53 @@ __global__ void __launch_bounds__(kRefitThreads)
     }
 }
 
+__global__ void __launch_bounds__(kRefitThreads)
+    refit_kernel(int D, const double *xb, const double *r, const double *c1, const int *elite, int n_elite,
+                 double sigma, double gamma, double chol_eps, double *mu, double *cov, double *mu_new,
+                 double *Lout, unsigned *counter, int *status, double *best_out)
+{
+    refit_body(D, blockIdx.x, xb, r, c1, elite, n_elite, sigma, gamma, chol_eps, mu, cov, mu_new, Lout, counter,
+               status, best_out);
+}
+
+// grid (max D, problems): CTAs past their problem's D return at once.
+__global__ void __launch_bounds__(kRefitThreads) refit_batch_kernel(const CemArgs *args)
+{
+    const CemArgs a = args[blockIdx.y];
+    if (int(blockIdx.x) >= a.D) return;
+    refit_body(a.D, blockIdx.x, a.xb, a.r, a.c1, a.elite, a.n_elite, a.sigma, a.gamma, a.chol_eps, a.mu, a.cov,
+               a.mu_new, a.L, a.counter, a.status, a.best_out);
+}
+
+size_t refit_smem(int D, int n_elite)
+{
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>(n_elite, 96 * 1024 / (sizeof(double) * D)));
+    const size_t stage = std::max(chunk * D, size_t(D) * D);
+    return (size_t(n_elite) + D + kRefitThreads + stage) * sizeof(double);
+}
+
 }  // namespace
+
+size_t select_smem_bytes(int N) { return size_t(N) * (2 * sizeof(unsigned long long) + 1) + 16; }
+size_t refit_smem_bytes(int D, int n_elite) { return refit_smem(D, n_elite); }
+
+cudaError_t launch_select_batch(const CemArgs *args_dev, int n, size_t smem, cudaStream_t st)
+{
+    static size_t granted = 0;
+    cudaError_t e = reserve_smem(select_batch_kernel, smem, granted);
+    if (e != cudaSuccess) return e;
+    select_batch_kernel<<<n, kSelectThreads, smem, st>>>(args_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refit_batch(const CemArgs *args_dev, int n, int D_max, size_t smem, cudaStream_t st)
+{
+    static size_t granted = 0;
+    cudaError_t e = reserve_smem(refit_batch_kernel, smem, granted);
+    if (e != cudaSuccess) return e;
+    refit_batch_kernel<<<dim3(D_max, n), kRefitThreads, smem, st>>>(args_dev);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx,
                           cudaStream_t st)

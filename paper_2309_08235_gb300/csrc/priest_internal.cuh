@@ -142,8 +142,33 @@ inline cudaError_t reserve_smem(Kernel kernel, size_t bytes, size_t &granted)
     return e;
 }
 
+// Arguments of the selection and refit stages of one problem (batched launches).
+struct CemArgs {
+    int N, n_proj, n_elite, D;
+    const double *r, *c1, *xb;
+    int *elite;
+    double sigma, gamma, chol_eps;
+    double *mu, *cov, *mu_new, *L;
+    unsigned *counter;
+    int *status;
+    double *best_out;
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
 cudaError_t launch_setup(const SetupParams &p, cudaStream_t st);
+cudaError_t launch_setup_batch(const SetupParams *ps_dev, int n, size_t smem, cudaStream_t st);
+size_t setup_smem_bytes(const Shape &sh);
+cudaError_t launch_select_batch(const CemArgs *args_dev, int n, size_t smem, cudaStream_t st);
+cudaError_t launch_refit_batch(const CemArgs *args_dev, int n, int D_max, size_t smem, cudaStream_t st);
+size_t select_smem_bytes(int N);
+size_t refit_smem_bytes(int D, int n_elite);
+
+// Persistent batched projection over the (problem, first sample) items.
+template <typename Real>
+cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 *items_dev, int n_items,
+                                 int *counter_dev, int dims, int R, int threads, int nf, int nv, int want_lambda,
+                                 size_t smem, int grid, cudaStream_t st);
+
 
 template <typename Real>
 size_t project_smem_bytes(const Shape &sh, int S, int C);
@@ -161,6 +186,9 @@ std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm);
 // project_f64.cu).
 template <typename Real, int DIMS, int R, int THREADS>
 cudaError_t launch_variant(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st);
+template <typename Real, int DIMS, int R, int THREADS>
+cudaError_t launch_variant_batch(const ProjParams<Real> *params, const int2 *items, int n_items, int *counter,
+                                 int nf, int nv, int want_lambda, size_t smem, int grid, cudaStream_t st);
 
 cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, int n_elite,
                           int *elite_idx, cudaStream_t st);

@@ -119,6 +119,35 @@ cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStrea
     }
 }
 
+// Batched launches use one variant per precision and dimension: 2-D
+// (R = 4, 512 threads), 3-D (R = 4, 512 threads), FP64 (R = 4, 256 threads).
+template <typename Real>
+cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 *items_dev, int n_items,
+                                 int *counter_dev, int dims, int R, int threads, int nf, int nv, int want_lambda,
+                                 size_t smem, int grid, cudaStream_t st)
+{
+    (void)R;
+    (void)threads;
+    if (n_items <= 0) return cudaSuccess;
+    if constexpr (sizeof(Real) == 8) {
+        if (dims == 2)
+            return launch_variant_batch<Real, 2, 4, 256>(params_dev, items_dev, n_items, counter_dev, nf, nv,
+                                                         want_lambda, smem, grid, st);
+        return launch_variant_batch<Real, 3, 4, 256>(params_dev, items_dev, n_items, counter_dev, nf, nv,
+                                                     want_lambda, smem, grid, st);
+    } else {
+        if (dims == 2)
+            return launch_variant_batch<Real, 2, 4, 512>(params_dev, items_dev, n_items, counter_dev, nf, nv,
+                                                         want_lambda, smem, grid, st);
+        return launch_variant_batch<Real, 3, 4, 512>(params_dev, items_dev, n_items, counter_dev, nf, nv,
+                                                     want_lambda, smem, grid, st);
+    }
+}
+
+template cudaError_t launch_project_batch<float>(const ProjParams<float> *, const int2 *, int, int *, int, int, int,
+                                                 int, int, int, size_t, int, cudaStream_t);
+template cudaError_t launch_project_batch<double>(const ProjParams<double> *, const int2 *, int, int *, int, int,
+                                                  int, int, int, int, size_t, int, cudaStream_t);
 template size_t project_smem_bytes<float>(const Shape &, int, int);
 template size_t project_smem_bytes<double>(const Shape &, int, int);
 template Tiling choose_tiling<float>(const Shape &, int, int);

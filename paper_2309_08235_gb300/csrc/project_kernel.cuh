@@ -26,6 +26,8 @@
 // and c_1 = sum ||acc||^2 (Alg. 1 residual and cost).
 #pragma once
 
+#include <algorithm>
+
 #include "priest_internal.cuh"
 
 namespace priest {
@@ -241,8 +243,10 @@ __device__ __forceinline__ void moving_obstacle(const Real *o, const Real (&px)[
 // NF: free coefficients (0 = runtime); NG: columns of the transposed basis
 // product (0 = runtime, <= 16).  Each sample of the CTA is owned by its own
 // group of p.WS warps, which runs all K iterations with group barriers only.
+// The projection of samples [s0, s0 + S) of one problem by the calling CTA
+// (all threads call it; it returns with the CTA converged).
 template <typename Real, int DIMS, int R, int THREADS, int NF, int NG>
-__global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Real> p)
+__device__ void project_body(const ProjParams<Real> &p, int s0)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *sm = reinterpret_cast<Real *>(smem_raw);
@@ -253,7 +257,6 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Re
     const int nv = p.nv, nf = NF > 0 ? NF : p.nf, np_ = p.n_p, S = p.S, C = p.C;
     const int nfp = nf_padded(nf), fbs = fb_stride(nf);
     const int D = DIMS * nv;
-    const int s0 = blockIdx.x * S;
     const int S_act = min(S, p.N - s0);
     if (S_act <= 0) return;
     const int PS = S * np_;
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Re
     // ---- from here on each sample's warp group works on its own
     const int WS = p.WS, GT = 32 * WS;
     const int s = warp / WS;
-    if (s >= S_act) return;
+    if (s < S_act) {
     const int lt = tid - s * GT, wl = warp - s * WS, bar = 1 + s;
     const int ps0 = s * np_;
     Real smin[DIMS], smax[DIMS];
@@ -560,6 +563,34 @@ __global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Re
         p.xi_bar[gi] = (f >= 0 && f < nf) ? double(sC[(s * DIMS + ax) * nfp + f]) : p.cB[ax * kMaxNv + cl];
         if (p.lam_out) p.lam_out[gi] = double(sLam[(s * DIMS + ax) * nv + cl]);
     }
+    }  // this sample's warp group
+    __syncthreads();
+}
+
+template <typename Real, int DIMS, int R, int THREADS, int NF, int NG>
+__global__ void __launch_bounds__(THREADS, 1) project_kernel(const ProjParams<Real> p)
+{
+    project_body<Real, DIMS, R, THREADS, NF, NG>(p, blockIdx.x * p.S);
+}
+
+// Persistent projection over many problems: CTAs take (problem, first sample)
+// items from `items` through an atomic counter until none is left.  Items are
+// listed most expensive first.  *next must be zero at launch.
+template <typename Real, int DIMS, int R, int THREADS, int NF, int NG>
+__global__ void __launch_bounds__(THREADS, 1)
+    project_batch_kernel(const ProjParams<Real> *params, const int2 *items, int n_items, int *next)
+{
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int2 w = items[it];
+        const ProjParams<Real> p = params[w.x];
+        project_body<Real, DIMS, R, THREADS, NF, NG>(p, w.y);
+        __syncthreads();
+    }
 }
 
 }  // namespace detail
@@ -584,6 +615,37 @@ cudaError_t launch_variant(const ProjParams<Real> &p, const Tiling &t, cudaStrea
     if (p.nf == 5 && !p.want_lambda) return launch_one<Real, DIMS, R, THREADS, 5, 5>(p, t, st);
     if (p.nf == 5 && p.nv == 11) return launch_one<Real, DIMS, R, THREADS, 5, 11>(p, t, st);
     return launch_one<Real, DIMS, R, THREADS, 0, 0>(p, t, st);
+}
+
+template <typename Real, int DIMS, int R, int THREADS, int NF, int NG>
+cudaError_t launch_batch_one(const ProjParams<Real> *params, const int2 *items, int n_items, int *counter,
+                             size_t smem, int grid, cudaStream_t st)
+{
+    static size_t granted = 0;
+    cudaError_t e = reserve_smem(detail::project_batch_kernel<Real, DIMS, R, THREADS, NF, NG>, smem, granted);
+    if (e != cudaSuccess) return e;
+    if (grid <= 0) {
+        int per_sm = 0, dev = 0, n_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, detail::project_batch_kernel<Real, DIMS, R, THREADS, NF, NG>, THREADS, smem);
+        grid = std::max(1, per_sm) * n_sm;
+    }
+    detail::project_batch_kernel<Real, DIMS, R, THREADS, NF, NG><<<grid, THREADS, smem, st>>>(params, items, n_items,
+                                                                                             counter);
+    return cudaGetLastError();
+}
+
+template <typename Real, int DIMS, int R, int THREADS>
+cudaError_t launch_variant_batch(const ProjParams<Real> *params, const int2 *items, int n_items, int *counter,
+                                 int nf, int nv, int want_lambda, size_t smem, int grid, cudaStream_t st)
+{
+    if (nf == 5 && !want_lambda)
+        return launch_batch_one<Real, DIMS, R, THREADS, 5, 5>(params, items, n_items, counter, smem, grid, st);
+    if (nf == 5 && nv == 11)
+        return launch_batch_one<Real, DIMS, R, THREADS, 5, 11>(params, items, n_items, counter, smem, grid, st);
+    return launch_batch_one<Real, DIMS, R, THREADS, 0, 0>(params, items, n_items, counter, smem, grid, st);
 }
 
 }  // namespace priest

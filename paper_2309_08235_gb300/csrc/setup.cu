@@ -47,7 +47,7 @@ __device__ void write_tables(const SetupParams &p, const double *src, size_t fro
     for (size_t i = from + threadIdx.x; i < to; i += blockDim.x) dst[i] = static_cast<Real>(src[i]);
 }
 
-__global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, double *tab64)
+__device__ void setup_body(const SetupParams &p, double *tab64)
 {
     const Shape &sh = p.sh;
     const int tid = threadIdx.x, T = blockDim.x;
@@ -253,7 +253,33 @@ __global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, dou
     }
 }
 
+__global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, double *tab64) { setup_body(p, tab64); }
+
+// One CTA per problem.
+__global__ void __launch_bounds__(kSetupThreads) setup_batch_kernel(const SetupParams *ps)
+{
+    const SetupParams p = ps[blockIdx.x];
+    setup_body(p, p.tab64);
+}
+
+size_t setup_smem(const Shape &sh)
+{
+    const size_t nbasis = size_t(3) * sh.n_p * sh.nv * sizeof(double);
+    return size_t(sh.D) * sh.D * sizeof(double) + (nbasis <= kSetupBasisSmem ? nbasis : 0);
+}
+
 }  // namespace
+
+cudaError_t launch_setup_batch(const SetupParams *ps_dev, int n, size_t smem, cudaStream_t st)
+{
+    static size_t granted = 0;
+    cudaError_t e = reserve_smem(setup_batch_kernel, smem, granted);
+    if (e != cudaSuccess) return e;
+    setup_batch_kernel<<<n, kSetupThreads, smem, st>>>(ps_dev);
+    return cudaGetLastError();
+}
+
+size_t setup_smem_bytes(const Shape &sh) { return setup_smem(sh); }
 
 cudaError_t launch_setup(const SetupParams &p, cudaStream_t st)
 {

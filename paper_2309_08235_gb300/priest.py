@@ -32,7 +32,7 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_plan_z", "priest_submit", "priest_poll", "priest_rng_normal", "priest_load",
            "priest_unload", "priest_plan_device", "priest_project_device", "priest_sync",
            "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
-           "priest_project_noalloc"]
+           "priest_project_noalloc", "priest_plan_batch"]
 
 
 class PriestError(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
             "priest_profile_read": (C.c_int, [vp, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
             "priest_project_noalloc": (C.c_int, [C.POINTER(priest_config), C.POINTER(priest_problem), C.c_int,
                                                  vp, vp, vp, vp, vp, vp]),
+            "priest_plan_batch": (C.c_int, [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -264,6 +265,16 @@ def priest_unload(ctx, h):
 
 def priest_plan_device(ctx, h, z_ptr, out_ptr):
     return _check(ctx, lib().priest_plan_device(ctx, h, C.c_void_p(z_ptr), C.c_void_p(out_ptr)))
+
+
+def priest_plan_batch(ctx, handles, z_ptrs, out_ptrs):
+    """Batched solve; handles from priest_load, device pointers as ints."""
+    n = len(handles)
+    arr = C.c_void_p * n
+    hs = arr(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    zs = arr(*[int(z) for z in z_ptrs])
+    os_ = arr(*[int(o) for o in out_ptrs])
+    return _check(ctx, lib().priest_plan_batch(ctx, n, hs, zs, os_))
 
 
 def priest_project_device(ctx, h, n, xi_ptr, lam_ptr, xb_ptr, r_ptr, c1_ptr):
