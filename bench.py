@@ -306,6 +306,66 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Batched workload: 256 uneven 2-D problems (obstacles log-uniform 10-400,
+    N in {256, 512, 1024, 2048}, n_p in {60, 100, 150}, K = 60, L = 3) solved
+    by priest_plan_batch (one persistent projection launch per CEM iteration,
+    CUDA graph replay).  Not the default bench line."""
+    import torch
+
+    from paper_2309_08235_gb300 import build as B
+    from paper_2309_08235_gb300 import priest as P
+    from paper_2309_08235_gb300 import workloads as W
+
+    B.build()
+    dev = torch.device("cuda", 0)
+    probs = W.batched_problems(args.batch_problems)
+    K, L = 60, 3
+    stream = torch.cuda.Stream(device=dev)
+    p0 = probs[0][0]
+    ctx = P.Context(p0, W.cem_settings(probs[0][1], K, L), precision=P.PRIEST_FP32, stream=stream.cuda_stream)
+    handles, zs, outs, keep = [], [], [], []
+    units = 0
+    pairs = 0
+    for i, (p, N) in enumerate(probs):
+        cem = W.cem_settings(N, K, L)
+        prob, kp = P.make_problem(p, cem, per_problem_shape=True)
+        keep.append(kp)
+        handles.append(P.priest_load(ctx.h, prob))
+        zs.append(torch.from_numpy(W.normals(2000 + i, (L, N, 22))).to(dev))
+        outs.append(torch.zeros(26, dtype=torch.float64, device=dev))
+        units += N * K * L
+        pairs += N * K * L * p["n_p"] * p["n_obs"]
+    zp = [z.data_ptr() for z in zs]
+    op = [o.data_ptr() for o in outs]
+    with torch.cuda.stream(stream):
+        for _ in range(max(2, args.warmup)):
+            P.priest_plan_batch(ctx.h, handles, zp, op)
+    P.priest_sync(ctx.h)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            e0.record(stream)
+            P.priest_plan_batch(ctx.h, handles, zp, op)
+            e1.record(stream)
+    P.priest_sync(ctx.h)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    tot = sum(ms) / 1e3
+    line = {"metric": METRIC, "value": units * args.steps / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched: {len(probs)} uneven 2-D problems (n_obs 10-400, N 256-2048, "
+                                   f"n_p 60/100/150), K={K}, L={L}, one persistent launch per CEM iteration, "
+                                   "CUDA graph replay", "units_per_step": units, "pairs_per_step": pairs},
+            "solves_per_s": len(probs) * args.steps / tot,
+            "pair_tests_per_s": pairs * args.steps / tot}
+    for h in handles:
+        P.priest_unload(ctx.h, h)
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -314,9 +374,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["clutter2d", "batched"], default="clutter2d",
+                    help="clutter2d: the default bench line; batched: 256 uneven problems (report only)")
+    ap.add_argument("--batch-problems", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

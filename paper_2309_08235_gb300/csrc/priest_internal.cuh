@@ -131,12 +131,13 @@ struct Tiling {
     size_t smem;  // dynamic shared memory bytes
 };
 
-// Raises a kernel's dynamic shared-memory limit to `bytes` when it is above
-// the 48 KB default; `granted` caches the largest value set so far.
+// Raises a kernel's dynamic shared-memory limit to `bytes` (the default limit
+// counts static shared memory too, so it is raised whenever more is asked
+// than granted so far); `granted` caches the largest value set.
 template <typename Kernel>
 inline cudaError_t reserve_smem(Kernel kernel, size_t bytes, size_t &granted)
 {
-    if (bytes <= 48 * 1024 || bytes <= granted) return cudaSuccess;
+    if (bytes <= granted) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (e == cudaSuccess) granted = bytes;
     return e;
