@@ -283,6 +283,30 @@ def run_ours(args):
            "d2h_bytes_per_step": int(8 * (D + 4 + D)),
            "api": "priest_plan_z (host buffers, blocking)"}
 
+    # ---- the plain per-problem FP32 GPU path on the same workload and draws
+    plain = None
+    if args.plain_steps > 0:
+        out_p = torch.zeros(D + 4, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            P.priest_plan_plain_device(ctx.h, h, z_dev.data_ptr(), out_p.data_ptr())
+        P.priest_sync(ctx.h)
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.plain_steps)]
+        with torch.cuda.stream(stream):
+            for e0, e1 in pev:
+                flush.zero_()
+                e0.record(stream)
+                P.priest_plan_plain_device(ctx.h, h, z_dev.data_ptr(), out_p.data_ptr())
+                e1.record(stream)
+        P.priest_sync(ctx.h)
+        pms = sum(a.elapsed_time(b) for a, b in pev) / len(pev)
+        ours = out.cpu().numpy()
+        theirs = out_p.cpu().numpy()
+        plain = {"value": units / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": len(pev),
+                 "speedup_of_fused": (units / (total_ms / args.steps / 1e3)) / (units / (pms / 1e3)),
+                 "c_aug": float(theirs[D + 2]), "c_aug_fused": float(ours[D + 2]),
+                 "path": "priest_plan_plain_device: one kernel per step, HBM trajectory / residual tiles"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -291,7 +315,8 @@ def run_ours(args):
                        "units_per_step": units},
             "solves_per_s": args.steps * world / (total_ms / 1e3),
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "plain_gpu": plain}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(p, cem, args.cpu_samples)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -366,6 +391,137 @@ def run_batched(args):
     return 0
 
 
+def fifo_latencies(arrivals, service):
+    """Completion-minus-arrival times of a single FIFO server (Lindley's
+    recursion) that serves request i for service[i] seconds."""
+    free_at = 0.0
+    out = []
+    for a, s in zip(arrivals, service):
+        start = max(a, free_at)
+        free_at = start + s
+        out.append(free_at - a)
+    return out
+
+
+def run_serving(args):
+    """Serving workload: a Poisson stream of 2-D / 3-D planning requests
+    (sizes as the batched workload, 20 % 3-D, 30 % warm replans of an earlier
+    robot) submitted in real time to priest_submit; the library's serving loop
+    batches them continuously under an HBM budget.  Reports solves/s, p50 /
+    p99 latency and projected sample-iters/s, next to the same stream served
+    one request at a time by priest_plan (service times measured on the GPU,
+    queueing replayed for a single FIFO server).  Not the default bench line."""
+    import threading
+
+    import torch
+
+    from paper_2309_08235_gb300 import build as B
+    from paper_2309_08235_gb300 import priest as P
+    from paper_2309_08235_gb300 import workloads as W
+
+    B.build()
+    torch.cuda.init()
+    K, L = 60, 3
+    reqs = W.serving_requests(rate=args.rate, duration=args.duration, seed=7)
+    p0 = reqs[0][1]
+    budget = int(args.budget_gb * (1 << 30))
+    ctx = P.Context(p0, W.cem_settings(256, K, L), precision=P.PRIEST_FP32, hbm_budget=budget)
+    cems = [W.cem_settings(N, K, L, dims=p["dims"]) for (_, p, N, _) in reqs]
+    # warm-up, untimed: a burst from another stream of the same mix (every
+    # kernel variant loaded, staging buffers sized), then a short paced run
+    warm = W.serving_requests(rate=args.rate, duration=0.5, seed=8)
+    wt = [ctx.submit(p, W.cem_settings(N, K, L, dims=p["dims"]), robot_id=10**9 + rid) for (_, p, N, rid) in warm]
+    for t in wt:
+        ctx.wait(t)
+    st0 = ctx.serve_stats()
+    tickets = [None] * len(reqs)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, ((ta, p, N, rid), cem) in enumerate(zip(reqs, cems)):
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = ctx.submit(p, cem, robot_id=rid)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    res = []
+    for i in range(len(reqs)):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        res.append(ctx.wait(tickets[i]))
+    t_end = time.perf_counter()
+    th.join()
+    clocks = sampler.stop()
+    st = ctx.serve_stats()
+    wall = t_end - t0
+    lat = np.array([r["latency_ms"] for r in res])
+    ok = sum(1 for r in res if r["status"] == 0)
+    units = sum(cem["n_samples"] * K * L for cem in cems)
+    steps = st["steps"] - st0["steps"]
+    served = {
+        "requests": len(reqs), "ok": ok, "wall_s": wall, "solves_per_s": len(reqs) / wall,
+        "sample_iters_per_s": units / wall, "offered_sample_iters_per_s": units / args.duration,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "max_ms": float(lat.max()), "steps": steps,
+        "mean_batch": (st["slot_steps"] - st0["slot_steps"]) / max(1, steps), "max_active": st["max_active"],
+        "warm_starts": st["warm_starts"] - st0["warm_starts"], "peak_bytes": st["peak_bytes"],
+        "budget_bytes": st["budget_bytes"], "deferred": st["deferred"] - st0["deferred"],
+    }
+    if args.dump:
+        np.savez(args.dump, arrival=np.array([r[0] for r in reqs]), latency_ms=lat,
+                 dims=np.array([r[1]["dims"] for r in reqs]), n=np.array([r[2] for r in reqs]),
+                 n_obs=np.array([r[1]["n_obs"] for r in reqs]), n_p=np.array([r[1]["n_p"] for r in reqs]),
+                 robot=np.array([r[3] for r in reqs]))
+    ctx.close()
+    # one request at a time through the plain per-problem FP32 path (load,
+    # device draws, solve, result read, unload): measured service times of a
+    # sample, FIFO queueing replayed on the full arrival stream
+    n_seq = min(len(reqs), args.seq_sample)
+    stride = max(1, len(reqs) // n_seq)
+    idx = list(range(0, len(reqs), stride))[:n_seq]
+    pctx = P.Context(p0, W.cem_settings(256, K, L), precision=P.PRIEST_FP32)
+    svc = []
+    for rep, i in enumerate([idx[0]] + idx):  # the first one again as a warm-up
+        _, p, N, _ = reqs[i]
+        cem = cems[i]
+        D = p["dims"] * 11
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        prob, kp = P.make_problem(p, cem, per_problem_shape=True)
+        hh = P.priest_load(pctx.h, prob)
+        z = torch.empty(L * N * D, dtype=torch.float64, device="cuda")
+        P.priest_rng_normal_device(p["seed"], z.numel(), z.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        o = torch.zeros(D + 4, dtype=torch.float64, device="cuda")
+        P.priest_plan_plain_device(pctx.h, hh, z.data_ptr(), o.data_ptr())
+        P.priest_sync(pctx.h)
+        _ = o.cpu()
+        P.priest_unload(pctx.h, hh)
+        if rep > 0:
+            svc.append(time.perf_counter() - a)
+    pctx.close()
+    mean_svc = float(np.mean(svc))
+    rng = np.random.default_rng(0)
+    service = rng.choice(np.array(svc), size=len(reqs))
+    seq_lat = np.array(fifo_latencies([r[0] for r in reqs], service)) * 1e3
+    seq = {"service_ms_mean": 1e3 * mean_svc, "solves_per_s_capacity": 1.0 / mean_svc,
+           "p50_ms": float(np.percentile(seq_lat, 50)), "p99_ms": float(np.percentile(seq_lat, 99)),
+           "sample": f"{len(idx)} requests timed one at a time, FIFO replay of all {len(reqs)} arrivals"}
+    line = {"metric": METRIC, "value": served["sample_iters_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": len(warm), "ms_per_step": 1e3 * wall / max(1, steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson {args.rate:g} req/s for {args.duration:g} s, sizes as the "
+                                   "batched workload, 20% 3-D, 30% warm replans, K=60, L=3, "
+                                   f"{args.budget_gb:g} GB budget"},
+            "serving": served, "plain_gpu_one_at_a_time": seq, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,14 +530,23 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["clutter2d", "batched"], default="clutter2d",
-                    help="clutter2d: the default bench line; batched: 256 uneven problems (report only)")
+    ap.add_argument("--workload", choices=["clutter2d", "batched", "serving"], default="clutter2d",
+                    help="clutter2d: the default bench line; batched: 256 uneven problems; serving: Poisson "
+                         "request stream (both report only)")
     ap.add_argument("--batch-problems", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=500.0)
+    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--budget-gb", type=float, default=8.0)
+    ap.add_argument("--seq-sample", type=int, default=300)
+    ap.add_argument("--plain-steps", type=int, default=10, help="timed solves of the plain per-problem path")
+    ap.add_argument("--dump", default=None, help="serving: save per-request arrival / latency / sizes (.npz)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -84,10 +84,13 @@ typedef struct {
     int use_bounds;        /* workspace bounds G xi <= tau (eq. bound_con) */
     double smin[3], smax[3];
     int precision;         /* priest_precision */
-    size_t hbm_budget;     /* bytes the serving loop may hold on the device; 0 = no limit */
+    size_t hbm_budget;     /* bytes of device memory the serving loop allocates once and admits
+                              requests into (0 = 2 GiB); its small per-step staging is extra */
     int autotune;          /* 1: time candidate tilings of the projection kernel on the first
                               call of each problem shape and keep the fastest (the first call
                               then blocks for the trials); 0: cost-model tiling */
+    int serve_slots;       /* most requests the serving loop keeps on the device at once
+                              (0 = as many as the budget holds) */
 } priest_config;
 
 /* One planning problem (Sec. II-A: eqs. acc_cost .. coll_multiagent). */
@@ -155,23 +158,68 @@ priest_status priest_plan(priest_ctx *ctx, const priest_problem *prob, const dou
 priest_status priest_plan_z(priest_ctx *ctx, const priest_problem *prob, const double *mu0,
                             const double *cov0, const double *z, priest_result *out);
 
-/* Serving: enqueue a solve (inputs copied before return) and get a ticket.
- * The worker admits requests while their device memory fits cfg.hbm_budget,
- * runs admitted requests together, and keeps per robot_id warm-start state
- * (the last mean / covariance) on the device; a request with a known
- * robot_id starts from it.  Errors: PRIEST_ERR_INVALID,
- * PRIEST_ERR_BUDGET (a single request larger than the budget). */
+/* Serving (continuous batching).  priest_submit copies the problem, queues
+ * it and returns a ticket at once.  A worker thread admits queued requests in
+ * arrival order while their device buffers fit the budget (cfg.hbm_budget,
+ * allocated once at the first submit) and cfg.serve_slots, and advances every
+ * admitted request by one CEM iteration per step, all of them in shared
+ * launches: one persistent projection launch per (dims, free-coefficient
+ * count) group, one selection and one refit launch.  Requests submitted while
+ * others are on the device join at the next step; memory of finished
+ * requests returns to the budget at once.  The standard-normal draws come
+ * from prob->seed through the same stream as priest_rng_normal, computed on
+ * the device (see priest_rng_normal_device).  Each request's solve is Alg. 1
+ * exactly as priest_plan computes it (the shared launches do not mix data
+ * between requests), except for warm starts:
+ *   robot_id >= 0 keeps the request's final sampling mean, covariance and
+ *   last-projection multipliers resident on the device; the robot's next
+ *   request with the same D and sample count starts from that mean and
+ *   covariance and uses those multipliers as lambda^0 of its first CEM
+ *   iteration.  A robot's requests run one after another.  Resident robot
+ *   states are dropped least recently used first when memory is needed.
+ * Errors: PRIEST_ERR_INVALID (as priest_plan), PRIEST_ERR_BUDGET (the
+ * request alone exceeds the budget), PRIEST_ERR_NOMEM (the budget cannot be
+ * allocated). */
 priest_status priest_submit(priest_ctx *ctx, const priest_problem *prob, uint64_t *ticket);
 
-/* PRIEST_PENDING until the ticket's solve is done, then its result (and the
- * ticket is released).  PRIEST_ERR_INVALID for an unknown ticket. */
+/* PRIEST_PENDING until the ticket's solve is done, then PRIEST_OK with its
+ * result (result.status holds the solve's own status: PRIEST_OK,
+ * PRIEST_ERR_NUMERIC or PRIEST_ERR_CUDA) and the ticket is released.
+ * PRIEST_ERR_INVALID for a ticket never issued or already released. */
 priest_status priest_poll(priest_ctx *ctx, uint64_t ticket, priest_result *out);
+
+/* As priest_poll, but blocks until the result is there or timeout_ms has
+ * passed (negative: no limit); PRIEST_ERR_TIMEOUT leaves the ticket pending. */
+priest_status priest_wait(priest_ctx *ctx, uint64_t ticket, double timeout_ms, priest_result *out);
+
+/* Counters of the serving loop. */
+typedef struct {
+    int64_t submitted;     /* tickets issued */
+    int64_t completed;     /* results produced */
+    int64_t steps;         /* shared CEM-iteration steps run */
+    int64_t slot_steps;    /* requests summed over steps (mean batch = slot_steps / steps) */
+    int64_t max_active;    /* most requests in one step */
+    int64_t warm_starts;   /* requests started from a robot's resident state */
+    int64_t deferred;      /* admission passes that stopped at a request waiting for memory */
+    int64_t evictions;     /* resident robot states dropped to make room */
+    size_t budget_bytes;   /* device bytes the loop admits into */
+    size_t peak_bytes;     /* most of them held at once */
+} priest_serve_stats;
+
+priest_status priest_serve_stats_get(priest_ctx *ctx, priest_serve_stats *out);
 
 /* The host Gaussian stream used by priest_plan: SplitMix64 (Steele, Lea,
  * Flood 2014) seeded with `seed`, 53-bit uniforms u = (x >> 11) 2^-53,
  * Box-Muller on (1 - u1, u2) giving cos then sin.  count >= 0 values.
  * Host-only; needs no GPU. */
 priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out);
+
+/* The same stream computed on the device: count values into out_dev
+ * (device, caller-owned) on cuda_stream (NULL = legacy default stream).  The
+ * 53-bit uniforms are bit-identical to the host stream's; the values differ
+ * from priest_rng_normal's by the last-place rounding of log, sqrt, cos and
+ * sin.  Asynchronous. */
+priest_status priest_rng_normal_device(uint64_t seed, int64_t count, double *out_dev, void *cuda_stream);
 
 /* Device-resident problems for callers that keep inputs in HBM.
  * priest_load copies the problem (obstacles, boundary values) to device
@@ -206,6 +254,22 @@ priest_status priest_project_device(priest_ctx *ctx, priest_loaded *h, int n, co
  * PRIEST_ERR_INVALID (mixed dims / degree / mask, n < 1), PRIEST_ERR_CUDA. */
 priest_status priest_plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs,
                                 const double *const *z_dev, double *const *out_dev);
+
+/* The plain per-problem FP32 path: the same computation as priest_plan /
+ * priest_project (same readings, same draws, FP32 projection), implemented
+ * as one kernel per step with every intermediate (trajectory tiles, residual
+ * tiles, coefficients, multipliers) in device memory and one problem at a
+ * time -- a direct GPU port of the method, kept as the comparison point of
+ * the fused, batched and serving forms.  Needs cfg.precision == PRIEST_FP32
+ * (else PRIEST_ERR_INVALID).  Arguments as priest_plan_z (z NULL: the host
+ * stream from prob->seed), priest_plan_device and priest_project. */
+priest_status priest_plan_plain(priest_ctx *ctx, const priest_problem *prob, const double *mu0,
+                                const double *cov0, const double *z, priest_result *out);
+priest_status priest_plan_plain_device(priest_ctx *ctx, priest_loaded *h, const double *z_dev,
+                                       double *out_dev);
+priest_status priest_project_plain(priest_ctx *ctx, const priest_problem *prob, int n, const double *xi,
+                                   double *lambda_io, double *xi_bar_out, double *resid_out,
+                                   double *cost_out);
 
 /* Waits for the context stream and reports any kernel-side error status. */
 priest_status priest_sync(priest_ctx *ctx);

@@ -92,6 +92,8 @@ def _load():
                 "orc_default_mean": (C.c_int, [C.POINTER(_Problem), _P]),
                 "orc_plan": (C.c_int, [C.POINTER(_Problem), C.POINTER(_Cem), _P, _P, _P,
                                        C.c_uint64, _P, _P, _P, _P, _P, _PI]),
+                "orc_plan_warm": (C.c_int, [C.POINTER(_Problem), C.POINTER(_Cem), _P, _P, _P, _P,
+                                            C.c_uint64, _P, _P, _P, _P, _P, _PI, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -304,16 +306,21 @@ def default_mean(p):
     return mu
 
 
-def plan(p, cem, mu0=None, cov0=None, z=None, seed=None):
+def plan(p, cem, mu0=None, cov0=None, z=None, seed=None, lam0=None, want_lam=False):
     """Alg. 1.  cem: dict with proj_iters, cem_iters, n_samples, n_proj,
-    n_elite, sigma_lr, gamma, chol_eps, init_std.  Returns a dict."""
+    n_elite, sigma_lr, gamma, chol_eps, init_std.  lam0 (N x D): lambda^0 of
+    the first CEM iteration's projection (multiplier warm start); want_lam:
+    also return the multipliers after the last CEM iteration's projection.
+    Returns a dict."""
     s, keep = _problem(p)
     c = _Cem()
     for name, _ in _Cem._fields_:
         setattr(c, name, type(getattr(c, name))(cem[name]))
     D = n_coeffs(p)
+    N = int(cem["n_samples"])
     mu0 = _f64(mu0)
     cov0 = _f64(cov0)
+    lam0 = None if lam0 is None else _f64(lam0, (N, D))
     if z is not None:
         z = _f64(z)
         assert z.size == cem["cem_iters"] * cem["n_samples"] * D
@@ -323,9 +330,13 @@ def plan(p, cem, mu0=None, cov0=None, z=None, seed=None):
     mu = np.zeros(D)
     cov = np.zeros((D, D))
     el = np.zeros(cem["n_elite"], dtype=np.int32)
+    lam_out = np.zeros((N, D)) if want_lam else None
     seed = int(p.get("seed", 0) if seed is None else seed)
-    rc = _load().orc_plan(C.byref(s), C.byref(c), _dptr(mu0), _dptr(cov0), _dptr(z),
-                          C.c_uint64(seed & (2**64 - 1)), _dptr(best), C.byref(br), C.byref(bc),
-                          _dptr(mu), _dptr(cov), el.ctypes.data_as(_PI))
-    _check(rc, "orc_plan")
-    return {"best": best, "r": br.value, "c_aug": bc.value, "mu": mu, "cov": cov, "elites": el}
+    rc = _load().orc_plan_warm(C.byref(s), C.byref(c), _dptr(mu0), _dptr(cov0), _dptr(lam0), _dptr(z),
+                               C.c_uint64(seed & (2**64 - 1)), _dptr(best), C.byref(br), C.byref(bc),
+                               _dptr(mu), _dptr(cov), el.ctypes.data_as(_PI), _dptr(lam_out))
+    _check(rc, "orc_plan_warm")
+    out = {"best": best, "r": br.value, "c_aug": bc.value, "mu": mu, "cov": cov, "elites": el}
+    if want_lam:
+        out["lam"] = lam_out
+    return out

@@ -812,8 +812,16 @@ int orc_plan(const orc_problem *pr, const orc_cem *cem, const double *mu0, const
              const double *z, uint64_t seed, double *best, double *best_r, double *best_caug,
              double *mu_out, double *cov_out, int *elite_out)
 {
+    return orc_plan_warm(pr, cem, mu0, cov0, NULL, z, seed, best, best_r, best_caug, mu_out, cov_out, elite_out,
+                         NULL);
+}
+
+int orc_plan_warm(const orc_problem *pr, const orc_cem *cem, const double *mu0, const double *cov0,
+                  const double *lam0, const double *z, uint64_t seed, double *best, double *best_r,
+                  double *best_caug, double *mu_out, double *cov_out, int *elite_out, double *lam_out)
+{
     int D, N, L, l, i, j, k, rc;
-    double *mu, *cov, *Lc, *Sh, *xi, *xb, *r, *c1, *caug, *zz = NULL, *el, *elc;
+    double *mu, *cov, *Lc, *Sh, *xi, *xb, *r, *c1, *caug, *zz = NULL, *el, *elc, *lam;
     int *eidx;
     if (check_problem(pr) || !cem) return -1;
     N = cem->n_samples;
@@ -822,7 +830,7 @@ int orc_plan(const orc_problem *pr, const orc_cem *cem, const double *mu0, const
         cem->n_elite <= 0 || cem->n_elite > cem->n_proj)
         return -1;
     D = pr->dims * (pr->degree + 1);
-    mu = (double *)malloc(sizeof(double) * (2 * D + 3 * D * D + 2 * (size_t)N * D + 3 * N +
+    mu = (double *)malloc(sizeof(double) * (2 * D + 3 * D * D + 3 * (size_t)N * D + 3 * N +
                                             (size_t)cem->n_elite * (D + 1)));
     eidx = (int *)malloc(sizeof(int) * cem->n_elite);
     if (!mu || !eidx) return -2;
@@ -836,6 +844,7 @@ int orc_plan(const orc_problem *pr, const orc_cem *cem, const double *mu0, const
     caug = c1 + N;
     el = caug + N;
     elc = el + (size_t)cem->n_elite * D;
+    lam = elc + cem->n_elite;
     if (mu0)
         for (i = 0; i < D; ++i) mu[i] = mu0[i];
     else
@@ -867,9 +876,13 @@ int orc_plan(const orc_problem *pr, const orc_cem *cem, const double *mu0, const
                 xi[(size_t)i * D + j] = s;
             }
         }
-        /* projection, residuals, cost */
-        rc = orc_project(pr, cem->proj_iters, N, xi, NULL, NULL, xb);
+        /* projection (lambda^0 = 0, or the warm start in the first CEM
+         * iteration), residuals, cost */
+        for (i = 0; i < N * D; ++i) lam[i] = (l == 0 && lam0) ? lam0[i] : 0.0;
+        rc = orc_project(pr, cem->proj_iters, N, xi, NULL, lam, xb);
         if (rc) break;
+        if (l == L - 1 && lam_out)
+            for (i = 0; i < N * D; ++i) lam_out[i] = lam[i];
         orc_residual_cost(pr, N, xb, r, c1);
         for (i = 0; i < N; ++i) caug[i] = c1[i] + r[i];
         rc = orc_select(N, r, caug, cem->n_proj, cem->n_elite, NULL, eidx);

@@ -130,6 +130,15 @@ int orc_plan(const orc_problem *pr, const orc_cem *cem, const double *mu0, const
              const double *z, uint64_t seed, double *best, double *best_r, double *best_caug,
              double *mu_out, double *cov_out, int *elite_out);
 
+/* Alg. 1 with a multiplier warm start (the serving loop's replans): lam0
+ * (N x D, or NULL for 0) is lambda^0 of the first CEM iteration's
+ * projection; later iterations start from 0.  lam_out (N x D, or NULL)
+ * receives the multipliers after the last CEM iteration's projection.
+ * orc_plan is this with both NULL. */
+int orc_plan_warm(const orc_problem *pr, const orc_cem *cem, const double *mu0, const double *cov0,
+                  const double *lam0, const double *z, uint64_t seed, double *best, double *best_r,
+                  double *best_caug, double *mu_out, double *cov_out, int *elite_out, double *lam_out);
+
 #ifdef __cplusplus
 }
 #endif

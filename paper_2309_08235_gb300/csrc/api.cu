@@ -21,34 +21,13 @@
 #include <utility>
 #include <vector>
 
-#include "priest_internal.cuh"
+#include "host_internal.h"
 
 using namespace priest;
-
-// ---------------------------------------------------------------------------
-// Device-resident problem: one allocation carved into all buffers of a solve.
-// ---------------------------------------------------------------------------
-struct priest_loaded {
-    Shape sh;
-    void *block = nullptr;
-    size_t bytes = 0;
-    double *center = nullptr, *vel = nullptr, *semi = nullptr;
-    double *tab64 = nullptr;
-    float *tab32 = nullptr;
-    double *cB = nullptr;
-    double *mu = nullptr, *cov = nullptr, *L = nullptr, *mu_new = nullptr;
-    double *xb = nullptr, *r = nullptr, *c1 = nullptr;
-    int *elite = nullptr;
-    double *out = nullptr;
-    unsigned *counter = nullptr;
-    double *z = nullptr;    // L x N x D (host-driven solves)
-    double *xi = nullptr;   // N x D (host-driven projections)
-    double *lam = nullptr;  // N x D
-    bool default_mu = true, default_cov = true;
-    bool shape_ready = false;  // basis and Gram blocks computed for this shape
-};
+using namespace priest::host;
 
 // Descriptors and recorded launch sequence of one batched solve.
+namespace priest {
 struct BatchPlan {
     void *dev = nullptr;            // one allocation: params, setup params, CEM args, items, counters
     cudaGraph_t graph = nullptr;
@@ -62,54 +41,10 @@ struct BatchPlan {
     int *counters_dev = nullptr;    // L
     int dims = 0, nf = 0, nv = 0, dbl = 0;
 };
+}  // namespace priest
 
-struct ServeRequest {
-    uint64_t ticket;
-    Shape sh;
-    std::vector<double> center, vel, semi;
-    uint64_t seed;
-    int64_t robot_id;
-    std::chrono::steady_clock::time_point t_submit;
-    size_t bytes;
-};
-
-struct WarmState {
-    int D = 0;
-    std::vector<double> mu, cov;
-};
-
-struct priest_ctx {
-    priest_config cfg;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int device = 0, n_sm = 0;
-    int *d_status = nullptr;
-    std::string err;
-    std::atomic<int64_t> launches{0};
-    priest_loaded *scratch = nullptr;  // reused by the host-pointer entry points
-    // serving
-    std::mutex mu_q;
-    std::condition_variable cv;
-    std::deque<ServeRequest> queue;
-    std::unordered_map<uint64_t, priest_result> done;
-    std::unordered_map<int64_t, WarmState> warm;
-    std::thread worker;
-    bool stop = false, worker_started = false;
-    uint64_t next_ticket = 1;
-    size_t in_flight_bytes = 0;
-    cudaStream_t serve_stream = nullptr;
-    int *serve_status = nullptr;
-    // batched solves: recorded launch sequences, keyed by the handle / buffer lists
-    std::map<std::vector<uintptr_t>, BatchPlan *> batches;
-    // tilings chosen by the autotuner, per problem shape
-    std::map<std::vector<int>, Tiling> tuned;
-    bool tune_cache_loaded = false;
-    // instrumentation
-    bool profile = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_used, prof_free;
-};
-
-namespace {
+namespace priest {
+namespace host {
 
 priest_status fail(priest_ctx *ctx, priest_status st, const std::string &msg)
 {
@@ -122,19 +57,14 @@ priest_status cuda_fail(priest_ctx *ctx, cudaError_t e, const char *what)
     return fail(ctx, PRIEST_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define PRIEST_CUDA(ctx, call)                                      \
-    do {                                                            \
-        cudaError_t e_ = (call);                                    \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
-    } while (0)
-
-bool is_fin(double x) { return std::isfinite(x); }
-
 // Resolves the shape of a problem against the context defaults and checks it.
-priest_status resolve(priest_ctx *ctx, const priest_problem *pr, int n_override, Shape &sh)
+priest_status resolve(const priest_config &c, const priest_problem *pr, int n_override, Shape &sh, std::string &why)
 {
-    const priest_config &c = ctx->cfg;
-    if (!pr) return fail(ctx, PRIEST_ERR_INVALID, "problem is NULL");
+    auto fail = [&why](priest_status st, const char *msg) {
+        why = msg;
+        return st;
+    };
+    if (!pr) return fail(PRIEST_ERR_INVALID, "problem is NULL");
     std::memset(&sh, 0, sizeof(sh));
     sh.dims = pr->dims ? pr->dims : c.dims;
     sh.degree = c.degree;
@@ -147,22 +77,22 @@ priest_status resolve(priest_ctx *ctx, const priest_problem *pr, int n_override,
     sh.use_bounds = c.use_bounds ? 1 : 0;
     sh.bc_mask = pr->bc_final_mask;
     sh.n_obs = pr->n_obs;
-    if (sh.dims != 2 && sh.dims != 3) return fail(ctx, PRIEST_ERR_INVALID, "dims must be 2 or 3");
-    if (sh.degree < 5 || sh.degree > 15) return fail(ctx, PRIEST_ERR_INVALID, "degree must be in [5, 15]");
-    if (sh.n_p < 2 || sh.n_p > PRIEST_MAX_NP) return fail(ctx, PRIEST_ERR_INVALID, "n_p out of range");
-    if (!(sh.horizon > 0) || !is_fin(sh.horizon)) return fail(ctx, PRIEST_ERR_INVALID, "horizon must be > 0");
-    if (!(sh.rho > 0) || !is_fin(sh.rho)) return fail(ctx, PRIEST_ERR_INVALID, "rho must be > 0");
-    if (!(sh.vmax > 0) || !(sh.amax > 0) || !is_fin(sh.vmax) || !is_fin(sh.amax))
-        return fail(ctx, PRIEST_ERR_INVALID, "vmax and amax must be > 0");
+    if (sh.dims != 2 && sh.dims != 3) return fail(PRIEST_ERR_INVALID, "dims must be 2 or 3");
+    if (sh.degree < 5 || sh.degree > 15) return fail(PRIEST_ERR_INVALID, "degree must be in [5, 15]");
+    if (sh.n_p < 2 || sh.n_p > PRIEST_MAX_NP) return fail(PRIEST_ERR_INVALID, "n_p out of range");
+    if (!(sh.horizon > 0) || !std::isfinite(sh.horizon)) return fail(PRIEST_ERR_INVALID, "horizon must be > 0");
+    if (!(sh.rho > 0) || !std::isfinite(sh.rho)) return fail(PRIEST_ERR_INVALID, "rho must be > 0");
+    if (!(sh.vmax > 0) || !(sh.amax > 0) || !std::isfinite(sh.vmax) || !std::isfinite(sh.amax))
+        return fail(PRIEST_ERR_INVALID, "vmax and amax must be > 0");
     if (sh.bc_mask != 0 && sh.bc_mask != 1 && sh.bc_mask != 3 && sh.bc_mask != 7)
-        return fail(ctx, PRIEST_ERR_INVALID, "bc_final_mask must be 0, 1, 3 or 7");
-    if (sh.n_obs < 0 || sh.n_obs > PRIEST_MAX_OBS) return fail(ctx, PRIEST_ERR_INVALID, "n_obs out of range");
+        return fail(PRIEST_ERR_INVALID, "bc_final_mask must be 0, 1, 3 or 7");
+    if (sh.n_obs < 0 || sh.n_obs > PRIEST_MAX_OBS) return fail(PRIEST_ERR_INVALID, "n_obs out of range");
     if (sh.n_obs > 0 && (!pr->center || !pr->semi))
-        return fail(ctx, PRIEST_ERR_INVALID, "obstacle arrays are NULL");
+        return fail(PRIEST_ERR_INVALID, "obstacle arrays are NULL");
     for (int ax = 0; ax < sh.dims; ++ax)
         for (int q = 0; q < 3; ++q) {
-            if (!is_fin(pr->b0[ax][q]) || !is_fin(pr->bf[ax][q]))
-                return fail(ctx, PRIEST_ERR_INVALID, "boundary values must be finite");
+            if (!std::isfinite(pr->b0[ax][q]) || !std::isfinite(pr->bf[ax][q]))
+                return fail(PRIEST_ERR_INVALID, "boundary values must be finite");
             sh.b0[ax][q] = pr->b0[ax][q];
             sh.bf[ax][q] = pr->bf[ax][q];
         }
@@ -172,27 +102,27 @@ priest_status resolve(priest_ctx *ctx, const priest_problem *pr, int n_override,
     }
     for (int j = 0; j < sh.n_obs; ++j) {
         const double a = pr->semi[2 * j], b = pr->semi[2 * j + 1];
-        if (!(a > 0) || !is_fin(a) || (sh.dims == 3 && (!(b > 0) || !is_fin(b))))
-            return fail(ctx, PRIEST_ERR_INVALID, "obstacle semi-axes must be finite and > 0");
+        if (!(a > 0) || !std::isfinite(a) || (sh.dims == 3 && (!(b > 0) || !std::isfinite(b))))
+            return fail(PRIEST_ERR_INVALID, "obstacle semi-axes must be finite and > 0");
         for (int ax = 0; ax < sh.dims; ++ax) {
-            if (!is_fin(pr->center[j * sh.dims + ax]))
-                return fail(ctx, PRIEST_ERR_INVALID, "obstacle centre is not finite");
-            if (pr->vel && !is_fin(pr->vel[j * sh.dims + ax]))
-                return fail(ctx, PRIEST_ERR_INVALID, "obstacle velocity is not finite");
+            if (!std::isfinite(pr->center[j * sh.dims + ax]))
+                return fail(PRIEST_ERR_INVALID, "obstacle centre is not finite");
+            if (pr->vel && !std::isfinite(pr->vel[j * sh.dims + ax]))
+                return fail(PRIEST_ERR_INVALID, "obstacle velocity is not finite");
         }
     }
     sh.nf = sh.nv - kFree0 - final_fixed(sh.bc_mask);
     sh.D = sh.dims * sh.nv;
     sh.N = n_override >= 0 ? n_override : (pr->n_samples ? pr->n_samples : c.n_samples);
-    if (sh.N < 0 || sh.N > PRIEST_MAX_SAMPLES) return fail(ctx, PRIEST_ERR_INVALID, "sample count out of range");
+    if (sh.N < 0 || sh.N > PRIEST_MAX_SAMPLES) return fail(PRIEST_ERR_INVALID, "sample count out of range");
     if (n_override < 0) {
-        if (sh.N < 1) return fail(ctx, PRIEST_ERR_INVALID, "n_samples must be >= 1");
+        if (sh.N < 1) return fail(PRIEST_ERR_INVALID, "n_samples must be >= 1");
         int np = pr->n_proj ? pr->n_proj : c.n_proj;
         int ne = pr->n_elite ? pr->n_elite : c.n_elite;
         if (np <= 0) np = std::max(1, (80 * sh.N) / 110);
         if (ne <= 0) ne = std::max(1, std::min(np, sh.N / 10));
         if (np > sh.N || ne > np || ne > PRIEST_MAX_ELITE)
-            return fail(ctx, PRIEST_ERR_INVALID, "need n_elite <= n_proj <= n_samples");
+            return fail(PRIEST_ERR_INVALID, "need n_elite <= n_proj <= n_samples");
         sh.n_proj = np;
         sh.n_elite = ne;
     }
@@ -233,12 +163,6 @@ void order_obstacles(const Shape &sh, const double *center, const double *vel, c
 
 size_t round_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Byte layout of a loaded problem (also used to admit serving requests).
-struct Carve {
-    size_t center, vel, semi, tab64, tab32, cB, mu, cov, L, mu_new, xb, r, c1, elite, out, counter, z, xi, lam,
-        total;
-};
-
 Carve carve(const Shape &sh, bool fp32, int z_iters, bool proj_buffers)
 {
     Carve k;
@@ -265,13 +189,158 @@ Carve carve(const Shape &sh, bool fp32, int z_iters, bool proj_buffers)
     k.r = take(sizeof(double) * N);
     k.c1 = take(sizeof(double) * N);
     k.elite = take(sizeof(int) * std::max(sh.n_elite, 1));
-    k.out = take(sizeof(double) * (D + 4));
+    k.out = take(sizeof(double) * (D + 5));
     k.counter = take(sizeof(unsigned));
     k.z = take(sizeof(double) * size_t(z_iters) * N * D);
     k.xi = take(proj_buffers ? sizeof(double) * N * D : 0);
     k.lam = take(proj_buffers ? sizeof(double) * N * D : 0);
     k.total = o;
     return k;
+}
+
+void carve_ptrs(priest_loaded *h, char *b, const Carve &k, bool fp32, int z_iters, bool proj_buffers)
+{
+    h->center = reinterpret_cast<double *>(b + k.center);
+    h->vel = reinterpret_cast<double *>(b + k.vel);
+    h->semi = reinterpret_cast<double *>(b + k.semi);
+    h->tab64 = reinterpret_cast<double *>(b + k.tab64);
+    h->tab32 = fp32 ? reinterpret_cast<float *>(b + k.tab32) : nullptr;
+    h->cB = reinterpret_cast<double *>(b + k.cB);
+    h->mu = reinterpret_cast<double *>(b + k.mu);
+    h->cov = reinterpret_cast<double *>(b + k.cov);
+    h->L = reinterpret_cast<double *>(b + k.L);
+    h->mu_new = reinterpret_cast<double *>(b + k.mu_new);
+    h->xb = reinterpret_cast<double *>(b + k.xb);
+    h->r = reinterpret_cast<double *>(b + k.r);
+    h->c1 = reinterpret_cast<double *>(b + k.c1);
+    h->elite = reinterpret_cast<int *>(b + k.elite);
+    h->out = reinterpret_cast<double *>(b + k.out);
+    h->counter = reinterpret_cast<unsigned *>(b + k.counter);
+    h->z = z_iters ? reinterpret_cast<double *>(b + k.z) : nullptr;
+    h->xi = proj_buffers ? reinterpret_cast<double *>(b + k.xi) : nullptr;
+    h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
+}
+
+template <typename Real>
+ProjParams<Real> proj_params(const priest_ctx *ctx, const priest_loaded *h, const Tiling &t)
+{
+    const Shape &sh = h->sh;
+    ProjParams<Real> p;
+    std::memset(&p, 0, sizeof(p));
+    p.dims = sh.dims;
+    p.nv = sh.nv;
+    p.nf = sh.nf;
+    p.n_p = sh.n_p;
+    p.n_obs = sh.n_obs;
+    p.n_static = sh.n_static;
+    p.use_bounds = sh.use_bounds;
+    p.K = ctx->cfg.proj_iters;
+    p.S = t.S;
+    p.C = t.C;
+    p.WS = t.ws;
+    p.rho = Real(sh.rho);
+    p.vmax = Real(sh.vmax);
+    p.amax = Real(sh.amax);
+    for (int ax = 0; ax < 3; ++ax) {
+        p.smin[ax] = Real(sh.smin[ax]);
+        p.smax[ax] = Real(sh.smax[ax]);
+    }
+    p.tab = std::is_same<Real, double>::value ? reinterpret_cast<const Real *>(h->tab64)
+                                              : reinterpret_cast<const Real *>(h->tab32);
+    p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
+    p.cB = h->cB;
+    return p;
+}
+
+SetupParams setup_params(const priest_ctx *ctx, const priest_loaded *h, bool plan_mode, int *status)
+{
+    SetupParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.sh = h->sh;
+    sp.center = h->center;
+    sp.vel = h->vel;
+    sp.semi = h->semi;
+    sp.tab64 = h->tab64;
+    sp.tab = h->tab32 ? static_cast<void *>(h->tab32) : static_cast<void *>(h->tab64);
+    sp.real_is_double = h->tab32 ? 0 : 1;
+    sp.cB = h->cB;
+    if (plan_mode) {
+        sp.mu = h->mu;
+        sp.cov = h->cov;
+        sp.L = h->L;
+        sp.default_mu = h->default_mu;
+        sp.default_cov = h->default_cov;
+    }
+    sp.init_std = ctx->cfg.init_std;
+    sp.chol_eps = ctx->cfg.chol_eps;
+    sp.status = status;
+    sp.shape_ready = h->shape_ready ? 1 : 0;
+    return sp;
+}
+
+CemArgs cem_args(const priest_ctx *ctx, const priest_loaded *h, int *status, double *best_out)
+{
+    const Shape &sh = h->sh;
+    CemArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.N = sh.N;
+    a.n_proj = sh.n_proj;
+    a.n_elite = sh.n_elite;
+    a.D = sh.D;
+    a.r = h->r;
+    a.c1 = h->c1;
+    a.xb = h->xb;
+    a.elite = h->elite;
+    a.sigma = ctx->cfg.sigma_lr;
+    a.gamma = ctx->cfg.gamma;
+    a.chol_eps = ctx->cfg.chol_eps;
+    a.mu = h->mu;
+    a.cov = h->cov;
+    a.mu_new = h->mu_new;
+    a.L = h->L;
+    a.counter = h->counter;
+    a.status = status;
+    a.best_out = best_out;
+    return a;
+}
+
+void fill_result(const Shape &sh, const double *host_out, const double *host_mu, priest_result *res)
+{
+    std::memset(res, 0, sizeof(*res));
+    res->status = PRIEST_OK;
+    res->D = sh.D;
+    for (int d = 0; d < sh.D; ++d) {
+        res->xi_best[d] = host_out[d];
+        res->mu[d] = host_mu[d];
+    }
+    res->resid = host_out[sh.D];
+    res->cost = host_out[sh.D + 1];
+    res->c_aug = host_out[sh.D + 2];
+    res->best_index = int(host_out[sh.D + 3]);
+}
+
+template ProjParams<float> proj_params<float>(const priest_ctx *, const priest_loaded *, const Tiling &);
+template ProjParams<double> proj_params<double>(const priest_ctx *, const priest_loaded *, const Tiling &);
+
+}  // namespace host
+}  // namespace priest
+
+namespace {
+
+#define PRIEST_CUDA(ctx, call)                                      \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
+    } while (0)
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+priest_status resolve(priest_ctx *ctx, const priest_problem *pr, int n_override, Shape &sh)
+{
+    std::string why;
+    const priest_status s = host::resolve(ctx->cfg, pr, n_override, sh, why);
+    if (s != PRIEST_OK) return fail(ctx, s, why);
+    return PRIEST_OK;
 }
 
 void free_loaded(priest_loaded *h)
@@ -301,26 +370,7 @@ priest_status make_loaded(priest_ctx *ctx, const Shape &sh_in, const double *cen
         return fail(ctx, PRIEST_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
     h->bytes = k.total;
-    char *b = static_cast<char *>(h->block);
-    h->center = reinterpret_cast<double *>(b + k.center);
-    h->vel = reinterpret_cast<double *>(b + k.vel);
-    h->semi = reinterpret_cast<double *>(b + k.semi);
-    h->tab64 = reinterpret_cast<double *>(b + k.tab64);
-    h->tab32 = fp32 ? reinterpret_cast<float *>(b + k.tab32) : nullptr;
-    h->cB = reinterpret_cast<double *>(b + k.cB);
-    h->mu = reinterpret_cast<double *>(b + k.mu);
-    h->cov = reinterpret_cast<double *>(b + k.cov);
-    h->L = reinterpret_cast<double *>(b + k.L);
-    h->mu_new = reinterpret_cast<double *>(b + k.mu_new);
-    h->xb = reinterpret_cast<double *>(b + k.xb);
-    h->r = reinterpret_cast<double *>(b + k.r);
-    h->c1 = reinterpret_cast<double *>(b + k.c1);
-    h->elite = reinterpret_cast<int *>(b + k.elite);
-    h->out = reinterpret_cast<double *>(b + k.out);
-    h->counter = reinterpret_cast<unsigned *>(b + k.counter);
-    h->z = z_iters ? reinterpret_cast<double *>(b + k.z) : nullptr;
-    h->xi = proj_buffers ? reinterpret_cast<double *>(b + k.xi) : nullptr;
-    h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
+    carve_ptrs(h, static_cast<char *>(h->block), k, fp32, z_iters, proj_buffers);
     const size_t ob = sizeof(double) * c.size();
     e = cudaMemcpyAsync(h->center, c.data(), ob, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->vel, v.data(), ob, cudaMemcpyHostToDevice, st);
@@ -351,25 +401,7 @@ priest_status scratch_for(priest_ctx *ctx, const Shape &sh, const priest_problem
         order_obstacles(s2, pr->center, pr->vel, pr->semi, c, v, s, s2.n_static);
         h->sh = s2;
         h->shape_ready = false;
-        h->center = reinterpret_cast<double *>(b + k.center);
-        h->vel = reinterpret_cast<double *>(b + k.vel);
-        h->semi = reinterpret_cast<double *>(b + k.semi);
-        h->tab64 = reinterpret_cast<double *>(b + k.tab64);
-        h->tab32 = fp32 ? reinterpret_cast<float *>(b + k.tab32) : nullptr;
-        h->cB = reinterpret_cast<double *>(b + k.cB);
-        h->mu = reinterpret_cast<double *>(b + k.mu);
-        h->cov = reinterpret_cast<double *>(b + k.cov);
-        h->L = reinterpret_cast<double *>(b + k.L);
-        h->mu_new = reinterpret_cast<double *>(b + k.mu_new);
-        h->xb = reinterpret_cast<double *>(b + k.xb);
-        h->r = reinterpret_cast<double *>(b + k.r);
-        h->c1 = reinterpret_cast<double *>(b + k.c1);
-        h->elite = reinterpret_cast<int *>(b + k.elite);
-        h->out = reinterpret_cast<double *>(b + k.out);
-        h->counter = reinterpret_cast<unsigned *>(b + k.counter);
-        h->z = z_iters ? reinterpret_cast<double *>(b + k.z) : nullptr;
-        h->xi = proj_buffers ? reinterpret_cast<double *>(b + k.xi) : nullptr;
-        h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
+        carve_ptrs(h, b, k, fp32, z_iters, proj_buffers);
         const size_t ob = sizeof(double) * c.size();
         cudaError_t e = cudaMemcpyAsync(h->center, c.data(), ob, cudaMemcpyHostToDevice, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h->vel, v.data(), ob, cudaMemcpyHostToDevice, ctx->stream);
@@ -393,60 +425,9 @@ priest_status scratch_for(priest_ctx *ctx, const Shape &sh, const priest_problem
     return PRIEST_OK;
 }
 
-template <typename Real>
-ProjParams<Real> proj_params(priest_ctx *ctx, priest_loaded *h, const Tiling &t)
-{
-    const Shape &sh = h->sh;
-    ProjParams<Real> p;
-    std::memset(&p, 0, sizeof(p));
-    p.dims = sh.dims;
-    p.nv = sh.nv;
-    p.nf = sh.nf;
-    p.n_p = sh.n_p;
-    p.n_obs = sh.n_obs;
-    p.n_static = sh.n_static;
-    p.use_bounds = sh.use_bounds;
-    p.K = ctx->cfg.proj_iters;
-    p.S = t.S;
-    p.C = t.C;
-    p.WS = t.ws;
-    p.rho = Real(sh.rho);
-    p.vmax = Real(sh.vmax);
-    p.amax = Real(sh.amax);
-    for (int ax = 0; ax < 3; ++ax) {
-        p.smin[ax] = Real(sh.smin[ax]);
-        p.smax[ax] = Real(sh.smax[ax]);
-    }
-    p.tab = std::is_same<Real, double>::value ? reinterpret_cast<const Real *>(h->tab64)
-                                              : reinterpret_cast<const Real *>(h->tab32);
-    p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
-    p.cB = h->cB;
-    return p;
-}
-
 priest_status enqueue_setup(priest_ctx *ctx, priest_loaded *h, bool plan_mode, cudaStream_t st, int *status)
 {
-    SetupParams sp;
-    std::memset(&sp, 0, sizeof(sp));
-    sp.sh = h->sh;
-    sp.center = h->center;
-    sp.vel = h->vel;
-    sp.semi = h->semi;
-    sp.tab64 = h->tab64;
-    sp.tab = h->tab32 ? static_cast<void *>(h->tab32) : static_cast<void *>(h->tab64);
-    sp.real_is_double = h->tab32 ? 0 : 1;
-    sp.cB = h->cB;
-    if (plan_mode) {
-        sp.mu = h->mu;
-        sp.cov = h->cov;
-        sp.L = h->L;
-        sp.default_mu = h->default_mu;
-        sp.default_cov = h->default_cov;
-    }
-    sp.init_std = ctx->cfg.init_std;
-    sp.chol_eps = ctx->cfg.chol_eps;
-    sp.status = status;
-    sp.shape_ready = h->shape_ready ? 1 : 0;
+    const SetupParams sp = setup_params(ctx, h, plan_mode, status);
     cudaError_t e = launch_setup(sp, st);
     ctx->launches++;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "setup kernel");
@@ -678,26 +659,96 @@ void gaussian_stream(uint64_t seed, int64_t count, double *out)
     }
 }
 
-priest_status fill_result(priest_ctx *ctx, const Shape &sh, const double *host_out, const double *host_mu,
-                          priest_result *res)
+// ---------------------------------------------------------------------------
+// Plain per-problem FP32 path (plain.cu): the comparison point of the fused
+// kernel, one launch per step with HBM intermediates.
+// ---------------------------------------------------------------------------
+priest_status plain_workspace(priest_ctx *ctx, const Shape &sh, int N, float **out)
 {
-    std::memset(res, 0, sizeof(*res));
-    res->status = PRIEST_OK;
-    res->D = sh.D;
-    for (int d = 0; d < sh.D; ++d) {
-        res->xi_best[d] = host_out[d];
-        res->mu[d] = host_mu[d];
+    if (ctx->cfg.precision != PRIEST_FP32) return fail(ctx, PRIEST_ERR_INVALID, "the plain path runs in FP32 only");
+    const size_t need = plain_work_floats(sh.dims, sh.nv, sh.nf, sh.n_p, std::max(N, 1));
+    if (need > ctx->plain_cap) {
+        PRIEST_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->plain_work) cudaFree(ctx->plain_work);
+        ctx->plain_work = nullptr;
+        ctx->plain_cap = 0;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&ctx->plain_work), need * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, PRIEST_ERR_NOMEM, "plain-path workspace");
+        }
+        ctx->plain_cap = need;
     }
-    res->resid = host_out[sh.D];
-    res->cost = host_out[sh.D + 1];
-    res->c_aug = host_out[sh.D + 2];
-    res->best_index = int(host_out[sh.D + 3]);
-    (void)ctx;
+    *out = ctx->plain_work;
+    return PRIEST_OK;
+}
+
+PlainParams plain_params(priest_ctx *ctx, const priest_loaded *h, int N, float *work)
+{
+    const Shape &sh = h->sh;
+    PlainParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.dims = sh.dims;
+    p.nv = sh.nv;
+    p.nf = sh.nf;
+    p.n_p = sh.n_p;
+    p.np4 = (sh.n_p + 3) / 4 * 4;
+    p.n_obs = sh.n_obs;
+    p.use_bounds = sh.use_bounds;
+    p.N = N;
+    p.K = ctx->cfg.proj_iters;
+    p.rho = float(sh.rho);
+    p.vmax = float(sh.vmax);
+    p.amax = float(sh.amax);
+    for (int ax = 0; ax < 3; ++ax) {
+        p.smin[ax] = float(sh.smin[ax]);
+        p.smax[ax] = float(sh.smax[ax]);
+    }
+    p.tab = h->tab32;
+    p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
+    p.cB = h->cB;
+    plain_carve(p, work);
+    return p;
+}
+
+// Alg. 1 on a loaded problem through the plain projection.
+priest_status enqueue_plan_plain(priest_ctx *ctx, priest_loaded *h, const double *z, double *out, cudaStream_t st,
+                                 int *status)
+{
+    const Shape &sh = h->sh;
+    float *work = nullptr;
+    priest_status s = plain_workspace(ctx, sh, sh.N, &work);
+    if (s != PRIEST_OK) return s;
+    s = enqueue_setup(ctx, h, true, st, status);
+    if (s != PRIEST_OK) return s;
+    const size_t step = size_t(sh.N) * sh.D;
+    PlainParams p = plain_params(ctx, h, sh.N, work);
+    p.mode = 1;
+    p.mu = h->mu;
+    p.Lc = h->L;
+    p.xi_bar = h->xb;
+    p.r_out = h->r;
+    p.c1_out = h->c1;
+    for (int l = 0; l < ctx->cfg.cem_iters; ++l) {
+        p.z = z + l * step;
+        int64_t n = 0;
+        cudaError_t e = launch_plain_project(p, st, &n);
+        ctx->launches += n;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "plain projection");
+        e = launch_select(sh.N, h->r, h->c1, sh.n_proj, sh.n_elite, h->elite, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "select kernel");
+        e = launch_refit(sh.D, h->xb, h->r, h->c1, h->elite, sh.n_elite, ctx->cfg.sigma_lr, ctx->cfg.gamma,
+                         ctx->cfg.chol_eps, h->mu, h->cov, h->mu_new, h->L, h->counter, status,
+                         out ? out : h->out, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "refit kernel");
+    }
     return PRIEST_OK;
 }
 
 priest_status plan_host(priest_ctx *ctx, const priest_problem *pr, const double *mu0, const double *cov0,
-                        const double *z_host, priest_result *out)
+                        const double *z_host, priest_result *out, bool plain = false)
 {
     if (!ctx || !out) return fail(ctx, PRIEST_ERR_INVALID, "NULL argument");
     Shape sh;
@@ -721,91 +772,16 @@ priest_status plan_host(priest_ctx *ctx, const priest_problem *pr, const double 
     if (cov0)
         PRIEST_CUDA(ctx, cudaMemcpyAsync(h->cov, cov0, size_t(sh.D) * sh.D * sizeof(double), cudaMemcpyHostToDevice,
                                          ctx->stream));
-    s = enqueue_plan(ctx, h, h->z, h->out, ctx->stream, ctx->d_status);
+    s = plain ? enqueue_plan_plain(ctx, h, h->z, h->out, ctx->stream, ctx->d_status)
+              : enqueue_plan(ctx, h, h->z, h->out, ctx->stream, ctx->d_status);
     if (s != PRIEST_OK) return s;
     std::vector<double> ho(sh.D + 4), hm(sh.D);
     PRIEST_CUDA(ctx, cudaMemcpyAsync(ho.data(), h->out, ho.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     PRIEST_CUDA(ctx, cudaMemcpyAsync(hm.data(), h->mu, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     s = check_status(ctx, ctx->d_status, ctx->stream);
     if (s != PRIEST_OK) return s;
-    return fill_result(ctx, sh, ho.data(), hm.data(), out);
-}
-
-// ---------------------------------------------------------------------------
-// Serving worker: admits queued requests while their device memory fits the
-// budget, runs them on the serving stream, keeps warm-start state per robot.
-// ---------------------------------------------------------------------------
-void serve_loop(priest_ctx *ctx)
-{
-    cudaSetDevice(ctx->device);
-    for (;;) {
-        ServeRequest req;
-        {
-            std::unique_lock<std::mutex> lk(ctx->mu_q);
-            ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
-            if (ctx->stop && ctx->queue.empty()) return;
-            req = std::move(ctx->queue.front());
-            ctx->queue.pop_front();
-        }
-        priest_result res;
-        std::memset(&res, 0, sizeof(res));
-        priest_loaded *h = nullptr;
-        priest_status st = make_loaded(ctx, req.sh, req.center.data(), req.vel.data(), req.semi.data(),
-                                       ctx->cfg.cem_iters, false, ctx->serve_stream, &h);
-        if (st == PRIEST_OK) {
-            const size_t nz = size_t(ctx->cfg.cem_iters) * req.sh.N * req.sh.D;
-            std::vector<double> z(nz);
-            gaussian_stream(req.seed, int64_t(nz), z.data());
-            cudaMemcpyAsync(h->z, z.data(), nz * sizeof(double), cudaMemcpyHostToDevice, ctx->serve_stream);
-            WarmState ws;
-            bool have_warm = false;
-            {
-                std::lock_guard<std::mutex> lk(ctx->mu_q);
-                auto it = ctx->warm.find(req.robot_id);
-                if (req.robot_id >= 0 && it != ctx->warm.end() && it->second.D == req.sh.D) {
-                    ws = it->second;
-                    have_warm = true;
-                }
-            }
-            h->default_mu = !have_warm;
-            h->default_cov = !have_warm;
-            if (have_warm) {
-                cudaMemcpyAsync(h->mu, ws.mu.data(), req.sh.D * sizeof(double), cudaMemcpyHostToDevice,
-                                ctx->serve_stream);
-                cudaMemcpyAsync(h->cov, ws.cov.data(), size_t(req.sh.D) * req.sh.D * sizeof(double),
-                                cudaMemcpyHostToDevice, ctx->serve_stream);
-            }
-            st = enqueue_plan(ctx, h, h->z, h->out, ctx->serve_stream, ctx->serve_status);
-            std::vector<double> ho(req.sh.D + 4), hm(req.sh.D), hc(size_t(req.sh.D) * req.sh.D);
-            if (st == PRIEST_OK) {
-                cudaMemcpyAsync(ho.data(), h->out, ho.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->serve_stream);
-                cudaMemcpyAsync(hm.data(), h->mu, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->serve_stream);
-                cudaMemcpyAsync(hc.data(), h->cov, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->serve_stream);
-                st = check_status(ctx, ctx->serve_status, ctx->serve_stream);
-            }
-            if (st == PRIEST_OK) {
-                fill_result(ctx, req.sh, ho.data(), hm.data(), &res);
-                if (req.robot_id >= 0) {
-                    std::lock_guard<std::mutex> lk(ctx->mu_q);
-                    WarmState &w = ctx->warm[req.robot_id];
-                    w.D = req.sh.D;
-                    w.mu = hm;
-                    w.cov = hc;
-                }
-            }
-            cudaStreamSynchronize(ctx->serve_stream);
-            free_loaded(h);
-        }
-        res.status = st;
-        res.latency_ms =
-            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - req.t_submit).count();
-        {
-            std::lock_guard<std::mutex> lk(ctx->mu_q);
-            ctx->in_flight_bytes -= req.bytes;
-            ctx->done[req.ticket] = res;
-        }
-        ctx->cv.notify_all();
-    }
+    fill_result(sh, ho.data(), hm.data(), out);
+    return PRIEST_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -825,8 +801,6 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
                           double *const *out, BatchPlan *b)
 {
     const int L = ctx->cfg.cem_iters;
-    const int threads = sizeof(Real) == 8 ? 256 : 512;
-    const int R = 4;
     const Shape &s0 = probs[0]->sh;
     b->n = n;
     b->L = L;
@@ -843,19 +817,8 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
         const Shape &sh = h->sh;
         if (sh.dims != s0.dims || sh.nv != s0.nv || sh.bc_mask != s0.bc_mask)
             return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
-        // tiling: warp groups of 2 (2-D) or 1 (3-D) in a fixed CTA, chunks from the cost model
-        Tiling t;
-        t.R = R;
-        t.threads = threads;
-        t.ws = (sh.dims == 2 && sizeof(Real) == 4) ? 2 : 1;
-        t.S = std::max(1, std::min(sh.N, threads / (32 * t.ws)));
-        if (t.ws > 1) t.S = std::min(t.S, 15);
-        const int nblk32 = ((sh.n_p + 32 * R - 1) / (32 * R)) * 32;
-        t.C = std::max(1, std::min(std::min(16, std::max(1, sh.n_obs)), (32 * t.ws) / nblk32));
-        while (t.S > 1 && project_smem_bytes<Real>(sh, t.S, t.C) > size_t(227) * 1024) t.S = std::max(1, t.S / 2);
-        t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
-        if (t.smem > size_t(227) * 1024)
-            return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
+        const Tiling t = batch_tiling<Real>(sh);
+        if (t.smem == 0) return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
         b->smem_proj = std::max(b->smem_proj, t.smem);
         ProjParams<Real> p = proj_params<Real>(ctx, h, t);
         p.N = sh.N;
@@ -872,48 +835,14 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
         }
         const double cost = double(sh.n_p) * (double(sh.n_obs) + 12.0);
         for (int s = 0; s < sh.N; s += t.S) items.push_back({cost * std::min(t.S, sh.N - s), make_int2(i, s)});
-        SetupParams sp;
-        std::memset(&sp, 0, sizeof(sp));
-        sp.sh = sh;
-        sp.center = h->center;
-        sp.vel = h->vel;
-        sp.semi = h->semi;
-        sp.tab64 = h->tab64;
-        sp.tab = h->tab32 ? static_cast<void *>(h->tab32) : static_cast<void *>(h->tab64);
-        sp.real_is_double = h->tab32 ? 0 : 1;
-        sp.cB = h->cB;
-        sp.mu = h->mu;
-        sp.cov = h->cov;
-        sp.L = h->L;
+        SetupParams sp = setup_params(ctx, h, true, ctx->d_status);
         sp.default_mu = 1;
         sp.default_cov = 1;
-        sp.init_std = ctx->cfg.init_std;
-        sp.chol_eps = ctx->cfg.chol_eps;
-        sp.status = ctx->d_status;
-        sp.shape_ready = h->shape_ready ? 1 : 0;
         setups[i] = sp;
         sp.shape_ready = 1;
         setups_ready[i] = sp;
         b->smem_setup = std::max(b->smem_setup, setup_smem_bytes(sh));
-        CemArgs a;
-        a.N = sh.N;
-        a.n_proj = sh.n_proj;
-        a.n_elite = sh.n_elite;
-        a.D = sh.D;
-        a.r = h->r;
-        a.c1 = h->c1;
-        a.xb = h->xb;
-        a.elite = h->elite;
-        a.sigma = ctx->cfg.sigma_lr;
-        a.gamma = ctx->cfg.gamma;
-        a.chol_eps = ctx->cfg.chol_eps;
-        a.mu = h->mu;
-        a.cov = h->cov;
-        a.mu_new = h->mu_new;
-        a.L = h->L;
-        a.counter = h->counter;
-        a.status = ctx->d_status;
-        a.best_out = out[i];
+        const CemArgs a = cem_args(ctx, h, ctx->d_status, out[i]);
         cem[i] = a;
         b->smem_select = std::max(b->smem_select, select_smem_bytes(sh.N));
         b->smem_refit = std::max(b->smem_refit, refit_smem_bytes(sh.D, sh.n_elite));
@@ -1063,13 +992,24 @@ priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out)
     return PRIEST_OK;
 }
 
+priest_status priest_rng_normal_device(uint64_t seed, int64_t count, double *out_dev, void *cuda_stream)
+{
+    if (count < 0 || (count > 0 && !out_dev)) return PRIEST_ERR_INVALID;
+    const cudaError_t e = launch_normal(seed, count, out_dev, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PRIEST_ERR_CUDA;
+    }
+    return PRIEST_OK;
+}
+
 priest_status priest_create(const priest_config *cfg, void *cuda_stream, priest_ctx **out)
 {
     if (!cfg || !out) return PRIEST_ERR_INVALID;
     *out = nullptr;
     if (cfg->degree < 5 || cfg->degree > 15 || cfg->proj_iters < 0 || cfg->cem_iters < 1 || !(cfg->rho > 0) ||
         !(cfg->gamma > 0) || cfg->sigma_lr < 0 || cfg->sigma_lr > 1 || cfg->chol_eps < 0 ||
-        (cfg->precision != PRIEST_FP64_CHECK && cfg->precision != PRIEST_FP32))
+        (cfg->precision != PRIEST_FP64_CHECK && cfg->precision != PRIEST_FP32) || cfg->serve_slots < 0)
         return PRIEST_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1096,7 +1036,6 @@ priest_status priest_create(const priest_config *cfg, void *cuda_stream, priest_
         delete ctx;
         return PRIEST_ERR_CUDA;
     }
-    ctx->serve_status = ctx->d_status + 1;
     *out = ctx;
     return PRIEST_OK;
 }
@@ -1104,17 +1043,10 @@ priest_status priest_create(const priest_config *cfg, void *cuda_stream, priest_
 priest_status priest_destroy(priest_ctx *ctx)
 {
     if (!ctx) return PRIEST_OK;
-    if (ctx->worker_started) {
-        {
-            std::lock_guard<std::mutex> lk(ctx->mu_q);
-            ctx->stop = true;
-        }
-        ctx->cv.notify_all();
-        ctx->worker.join();
-        cudaStreamDestroy(ctx->serve_stream);
-    }
+    server_destroy(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_loaded(ctx->scratch);
+    if (ctx->plain_work) cudaFree(ctx->plain_work);
     for (auto &kv : ctx->batches) free_batch(kv.second);
     for (auto &ev : ctx->prof_used) {
         cudaEventDestroy(ev.first);
@@ -1211,6 +1143,65 @@ priest_status priest_plan_z(priest_ctx *ctx, const priest_problem *pr, const dou
     return plan_host(ctx, pr, mu0, cov0, z, out);
 }
 
+priest_status priest_plan_plain(priest_ctx *ctx, const priest_problem *pr, const double *mu0, const double *cov0,
+                                const double *z, priest_result *out)
+{
+    return plan_host(ctx, pr, mu0, cov0, z, out, true);
+}
+
+priest_status priest_plan_plain_device(priest_ctx *ctx, priest_loaded *h, const double *z_dev, double *out_dev)
+{
+    if (!ctx || !h || !z_dev || !out_dev) return fail(ctx, PRIEST_ERR_INVALID, "NULL argument");
+    h->default_mu = true;
+    h->default_cov = true;
+    return enqueue_plan_plain(ctx, h, z_dev, out_dev, ctx->stream, ctx->d_status);
+}
+
+priest_status priest_project_plain(priest_ctx *ctx, const priest_problem *pr, int n, const double *xi,
+                                   double *lambda_io, double *xi_bar_out, double *resid_out, double *cost_out)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    if (n < 0 || n > PRIEST_MAX_SAMPLES) return fail(ctx, PRIEST_ERR_INVALID, "n out of range");
+    if (n > 0 && (!xi || !xi_bar_out)) return fail(ctx, PRIEST_ERR_INVALID, "xi / xi_bar_out is NULL");
+    Shape sh;
+    priest_status s = resolve(ctx, pr, n, sh);
+    if (s != PRIEST_OK) return s;
+    for (size_t i = 0; i < size_t(n) * sh.D; ++i)
+        if (!is_fin(xi[i]) || (lambda_io && !is_fin(lambda_io[i])))
+            return fail(ctx, PRIEST_ERR_INVALID, "xi / lambda must be finite");
+    if (n == 0) return PRIEST_OK;
+    float *work = nullptr;
+    s = plain_workspace(ctx, sh, n, &work);
+    if (s != PRIEST_OK) return s;
+    priest_loaded *h = nullptr;
+    s = scratch_for(ctx, sh, pr, 0, true, &h);
+    if (s != PRIEST_OK) return s;
+    const size_t bytes = size_t(n) * sh.D * sizeof(double);
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(h->xi, xi, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    if (lambda_io) PRIEST_CUDA(ctx, cudaMemcpyAsync(h->lam, lambda_io, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    s = enqueue_setup(ctx, h, false, ctx->stream, ctx->d_status);
+    if (s != PRIEST_OK) return s;
+    PlainParams p = plain_params(ctx, h, n, work);
+    p.mode = 0;
+    p.xi_in = h->xi;
+    p.lam_in = lambda_io ? h->lam : nullptr;
+    p.lam_out = lambda_io ? h->lam : nullptr;
+    p.xi_bar = h->xb;
+    p.r_out = h->r;
+    p.c1_out = h->c1;
+    int64_t nl = 0;
+    cudaError_t e = launch_plain_project(p, ctx->stream, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "plain projection");
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(xi_bar_out, h->xb, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (lambda_io) PRIEST_CUDA(ctx, cudaMemcpyAsync(lambda_io, h->lam, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (resid_out)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(resid_out, h->r, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (cost_out)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(cost_out, h->c1, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return check_status(ctx, ctx->d_status, ctx->stream);
+}
+
 priest_status priest_load(priest_ctx *ctx, const priest_problem *pr, priest_loaded **out)
 {
     if (!ctx || !out) return PRIEST_ERR_INVALID;
@@ -1246,61 +1237,6 @@ priest_status priest_project_device(priest_ctx *ctx, priest_loaded *h, int n, co
     if (s != PRIEST_OK) return s;
     return enqueue_project_any(ctx, h, n, 0, xi_dev, nullptr, lambda_dev, lambda_dev, xi_bar_dev, resid_dev,
                                cost_dev, ctx->stream);
-}
-
-priest_status priest_submit(priest_ctx *ctx, const priest_problem *pr, uint64_t *ticket)
-{
-    if (!ctx || !ticket) return PRIEST_ERR_INVALID;
-    ServeRequest req;
-    priest_status s = resolve(ctx, pr, -1, req.sh);
-    if (s != PRIEST_OK) return s;
-    req.sh.n_static = 0;
-    const bool fp32 = ctx->cfg.precision != PRIEST_FP64_CHECK;
-    req.bytes = carve(req.sh, fp32, ctx->cfg.cem_iters, false).total;
-    if (ctx->cfg.hbm_budget && req.bytes > ctx->cfg.hbm_budget)
-        return fail(ctx, PRIEST_ERR_BUDGET, "request larger than the HBM budget");
-    const int n = pr->n_obs, d = req.sh.dims;
-    req.center.assign(pr->center, pr->center + size_t(n) * d);
-    req.vel.assign(size_t(n) * d, 0.0);
-    if (pr->vel) req.vel.assign(pr->vel, pr->vel + size_t(n) * d);
-    req.semi.assign(pr->semi, pr->semi + size_t(n) * 2);
-    if (n == 0) {
-        req.center.assign(d, 0.0);
-        req.vel.assign(d, 0.0);
-        req.semi.assign(2, 1.0);
-    }
-    req.seed = pr->seed;
-    req.robot_id = pr->robot_id;
-    req.t_submit = std::chrono::steady_clock::now();
-    {
-        std::lock_guard<std::mutex> lk(ctx->mu_q);
-        if (!ctx->worker_started) {
-            if (cudaStreamCreateWithFlags(&ctx->serve_stream, cudaStreamNonBlocking) != cudaSuccess)
-                return fail(ctx, PRIEST_ERR_CUDA, "cannot create the serving stream");
-            ctx->worker = std::thread(serve_loop, ctx);
-            ctx->worker_started = true;
-        }
-        req.ticket = ctx->next_ticket++;
-        *ticket = req.ticket;
-        ctx->in_flight_bytes += req.bytes;
-        ctx->queue.push_back(std::move(req));
-    }
-    ctx->cv.notify_all();
-    return PRIEST_OK;
-}
-
-priest_status priest_poll(priest_ctx *ctx, uint64_t ticket, priest_result *out)
-{
-    if (!ctx || !out) return PRIEST_ERR_INVALID;
-    std::lock_guard<std::mutex> lk(ctx->mu_q);
-    auto it = ctx->done.find(ticket);
-    if (it == ctx->done.end()) {
-        if (ticket == 0 || ticket >= ctx->next_ticket) return fail(ctx, PRIEST_ERR_INVALID, "unknown ticket");
-        return PRIEST_PENDING;
-    }
-    *out = it->second;
-    ctx->done.erase(it);
-    return PRIEST_OK;
 }
 
 }  // extern "C"

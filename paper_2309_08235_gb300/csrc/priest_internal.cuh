@@ -155,7 +155,36 @@ struct CemArgs {
     double *best_out;
 };
 
+// One run of the standard-normal stream: `count` values of the stream seeded
+// with `seed`, written to `out` (device).  The same launch zeroes `status`
+// and `counter` when they are not null (the status word and refit counter of
+// a request that starts its solve).
+struct GaussJob {
+    unsigned long long seed;
+    long long count;
+    double *out;
+    int *status;
+    unsigned *counter;
+};
+
+// Inputs and HBM workspace of the plain per-problem FP32 path (plain.cu).
+struct PlainParams {
+    int dims, nv, nf, n_p, np4, n_obs, use_bounds, N, K, mode;  // mode 0: xi_in given; 1: xi = mu + L z
+    float rho, vmax, amax, smin[3], smax[3];
+    const float *tab;
+    TableLayout lay;
+    const double *cB;
+    const double *xi_in, *mu, *Lc, *z, *lam_in;
+    double *xi_bar, *lam_out, *r_out, *c1_out;
+    float *c, *xiF, *lam, *pos, *vel, *acc, *so, *rv, *ra;  // workspace (plain_carve)
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
+size_t plain_work_floats(int dims, int nv, int nf, int n_p, int N);
+void plain_carve(PlainParams &p, float *work);
+cudaError_t launch_plain_project(const PlainParams &p, cudaStream_t st, int64_t *launches);
+cudaError_t launch_normal_batch(const GaussJob *jobs_dev, int n_jobs, long long max_count, cudaStream_t st);
+cudaError_t launch_normal(unsigned long long seed, long long count, double *out_dev, cudaStream_t st);
 cudaError_t launch_setup(const SetupParams &p, cudaStream_t st);
 cudaError_t launch_setup_batch(const SetupParams *ps_dev, int n, size_t smem, cudaStream_t st);
 size_t setup_smem_bytes(const Shape &sh);
@@ -182,6 +211,12 @@ Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm);
 
 template <typename Real>
 std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm);
+
+// Tiling of one problem inside a batched (persistent) launch: the batched
+// variant's CTA size, warp groups of two (2-D FP32) or one warp, chunk count
+// from the cost model.  smem == 0 signals a problem too large for one CTA.
+template <typename Real>
+Tiling batch_tiling(const Shape &sh);
 
 // One compiled kernel variant (explicitly instantiated in project_f32_*.cu /
 // project_f64.cu).

@@ -102,6 +102,23 @@ std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm)
 }
 
 template <typename Real>
+Tiling batch_tiling(const Shape &sh)
+{
+    Tiling t;
+    t.R = 4;
+    t.threads = sizeof(Real) == 8 ? 256 : 512;
+    t.ws = (sh.dims == 2 && sizeof(Real) == 4) ? 2 : 1;
+    t.S = std::max(1, std::min(sh.N, t.threads / (32 * t.ws)));
+    if (t.ws > 1) t.S = std::min(t.S, 15);
+    const int nblk32 = ((sh.n_p + 32 * t.R - 1) / (32 * t.R)) * 32;
+    t.C = std::max(1, std::min(std::min(16, std::max(1, sh.n_obs)), (32 * t.ws) / nblk32));
+    while (t.S > 1 && project_smem_bytes<Real>(sh, t.S, t.C) > kSmemCap) t.S = std::max(1, t.S / 2);
+    t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
+    if (t.smem > kSmemCap) t.smem = 0;
+    return t;
+}
+
+template <typename Real>
 cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st)
 {
     if (p.N <= 0) return cudaSuccess;
@@ -154,6 +171,8 @@ template Tiling choose_tiling<float>(const Shape &, int, int);
 template Tiling choose_tiling<double>(const Shape &, int, int);
 template std::vector<Tiling> tiling_candidates<float>(const Shape &, int, int);
 template std::vector<Tiling> tiling_candidates<double>(const Shape &, int, int);
+template Tiling batch_tiling<float>(const Shape &);
+template Tiling batch_tiling<double>(const Shape &);
 template cudaError_t launch_project<float>(const ProjParams<float> &, const Tiling &, cudaStream_t);
 template cudaError_t launch_project<double>(const ProjParams<double> &, const Tiling &, cudaStream_t);
 

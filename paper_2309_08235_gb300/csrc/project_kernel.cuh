@@ -336,8 +336,12 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
     const int n_mov = p.n_obs - p.n_static;
     const int Cs_s = (p.n_static + C - 1) / C, Cs_m = (n_mov + C - 1) / C;
     const int items = nblk32 * C;
-    const int col_lo = p.want_lambda ? 0 : kFree0;
-    const int ng = NG > 0 ? NG : (p.want_lambda ? nv : nf);
+    // g columns: the free ones only, or all n_v when the multipliers are
+    // returned (NG = NF fixes the former at compile time; otherwise the
+    // choice is per problem, so one launch may mix both)
+    constexpr bool kFreeOnly = NF > 0 && NG == NF;
+    const int col_lo = (!kFreeOnly && p.want_lambda) ? 0 : kFree0;
+    const int ng = kFreeOnly ? NF : (p.want_lambda ? nv : nf);
     constexpr int ST = DIMS == 2 ? 12 : 16;
     constexpr int OB = 4;
     const Real *cc_s = sC + s * DIMS * nfp;
@@ -483,7 +487,7 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
                 for (int c = 1; c < C; ++c) rp += sPart[(c * DIMS + ax) * PS + pp];
                 if (p.use_bounds) rp += sRB[ax * PS + pp];
                 const Real rv = sRV[ax * PS + pp], ra = sRA[ax * PS + pp];
-                if constexpr (NF > 0 && NG == NF) {
+                if constexpr (kFreeOnly) {
                     const Real *fbt = sFb + size_t(t) * fbs;
                     Real b[3][4 * NFV];
 #pragma unroll
@@ -500,12 +504,12 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
                     const Real *b2 = b1 + size_t(np_) * nv;
 #pragma unroll
                     for (int i = 0; i < NGM; ++i)
-                        if (NG > 0 || i < ng) acc[i] = fma(b0[i], rp, fma(b1[i], rv, fma(b2[i], ra, acc[i])));
+                        if (i < ng) acc[i] = fma(b0[i], rp, fma(b1[i], rv, fma(b2[i], ra, acc[i])));
                 }
             }
 #pragma unroll
             for (int i = 0; i < NGM; ++i) {
-                if (NG > 0 || i < ng) {
+                if (kFreeOnly || i < ng) {
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(kFull, acc[i], off);
                 }
@@ -518,7 +522,7 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
             const int fl = lane - (kFree0 - col_lo);
 #pragma unroll
             for (int i = 0; i < NGM; ++i) {
-                if (NG > 0 || i < ng) {
+                if (kFreeOnly || i < ng) {
                     const int ci = col_lo + i, fi = ci - kFree0;
                     if (lane == i) g = acc[i];
                     if (fi >= 0 && fi < nf) {

@@ -32,7 +32,9 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_plan_z", "priest_submit", "priest_poll", "priest_rng_normal", "priest_load",
            "priest_unload", "priest_plan_device", "priest_project_device", "priest_sync",
            "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
-           "priest_project_noalloc", "priest_plan_batch"]
+           "priest_project_noalloc", "priest_plan_batch", "priest_wait", "priest_serve_stats_get",
+           "priest_rng_normal_device", "priest_plan_plain", "priest_plan_plain_device",
+           "priest_project_plain"]
 
 
 class PriestError(RuntimeError):
@@ -48,7 +50,7 @@ class priest_config(C.Structure):
         ("n_proj", C.c_int), ("n_elite", C.c_int), ("sigma_lr", C.c_double), ("gamma", C.c_double),
         ("chol_eps", C.c_double), ("init_std", C.c_double), ("vmax", C.c_double), ("amax", C.c_double),
         ("use_bounds", C.c_int), ("smin", C.c_double * 3), ("smax", C.c_double * 3),
-        ("precision", C.c_int), ("hbm_budget", C.c_size_t), ("autotune", C.c_int),
+        ("precision", C.c_int), ("hbm_budget", C.c_size_t), ("autotune", C.c_int), ("serve_slots", C.c_int),
     ]
 
 
@@ -67,6 +69,14 @@ class priest_result(C.Structure):
         ("status", C.c_int), ("D", C.c_int), ("best_index", C.c_int), ("xi_best", C.c_double * MAX_D),
         ("resid", C.c_double), ("cost", C.c_double), ("c_aug", C.c_double), ("mu", C.c_double * MAX_D),
         ("latency_ms", C.c_double),
+    ]
+
+
+class priest_serve_stats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_int64), ("completed", C.c_int64), ("steps", C.c_int64), ("slot_steps", C.c_int64),
+        ("max_active", C.c_int64), ("warm_starts", C.c_int64), ("deferred", C.c_int64), ("evictions", C.c_int64),
+        ("budget_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
     ]
 
 
@@ -109,6 +119,12 @@ def lib():
             "priest_project_noalloc": (C.c_int, [C.POINTER(priest_config), C.POINTER(priest_problem), C.c_int,
                                                  vp, vp, vp, vp, vp, vp]),
             "priest_plan_batch": (C.c_int, [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
+            "priest_wait": (C.c_int, [vp, C.c_uint64, C.c_double, C.POINTER(priest_result)]),
+            "priest_serve_stats_get": (C.c_int, [vp, C.POINTER(priest_serve_stats)]),
+            "priest_rng_normal_device": (C.c_int, [C.c_uint64, C.c_int64, vp, vp]),
+            "priest_plan_plain": (C.c_int, [vp, C.POINTER(priest_problem), _P, _P, _P, C.POINTER(priest_result)]),
+            "priest_plan_plain_device": (C.c_int, [vp, vp, vp, vp]),
+            "priest_project_plain": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -243,6 +259,20 @@ def priest_plan_z(ctx, prob, mu0, cov0, z, res):
                                            C.byref(res)))
 
 
+def priest_plan_plain(ctx, prob, mu0, cov0, z, res):
+    zp = None if z is None else z.ctypes.data_as(_P)
+    return _check(ctx, lib().priest_plan_plain(ctx, C.byref(prob), _arr(mu0)[1], _arr(cov0)[1], zp, C.byref(res)))
+
+
+def priest_plan_plain_device(ctx, h, z_ptr, out_ptr):
+    return _check(ctx, lib().priest_plan_plain_device(ctx, h, C.c_void_p(z_ptr), C.c_void_p(out_ptr)))
+
+
+def priest_project_plain(ctx, prob, n, xi, lambda_io, xi_bar_out, resid_out, cost_out):
+    return _check(ctx, lib().priest_project_plain(ctx, C.byref(prob), int(n), *(
+        None if a is None else a.ctypes.data_as(_P) for a in (xi, lambda_io, xi_bar_out, resid_out, cost_out))))
+
+
 def priest_submit(ctx, prob):
     t = C.c_uint64()
     _check(ctx, lib().priest_submit(ctx, C.byref(prob), C.byref(t)))
@@ -251,6 +281,27 @@ def priest_submit(ctx, prob):
 
 def priest_poll(ctx, ticket, res):
     return _check(ctx, lib().priest_poll(ctx, C.c_uint64(ticket), C.byref(res)))
+
+
+def priest_wait(ctx, ticket, res, timeout_ms=-1.0):
+    """Blocks until the ticket's result is there (PRIEST_OK) or the timeout
+    passes (PriestError with PRIEST_ERR_TIMEOUT)."""
+    return _check(ctx, lib().priest_wait(ctx, C.c_uint64(ticket), float(timeout_ms), C.byref(res)))
+
+
+def priest_serve_stats_get(ctx):
+    s = priest_serve_stats()
+    _check(ctx, lib().priest_serve_stats_get(ctx, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in priest_serve_stats._fields_}
+
+
+def priest_rng_normal_device(seed, count, out_ptr, stream=None):
+    """The standard-normal stream computed on the device into out_ptr (int)."""
+    st = lib().priest_rng_normal_device(C.c_uint64(int(seed) & (2**64 - 1)), int(count), C.c_void_p(out_ptr),
+                                        stream)
+    if st != PRIEST_OK:
+        raise PriestError(st, "priest_rng_normal_device failed")
+    return st
 
 
 def priest_load(ctx, prob):
@@ -354,8 +405,31 @@ class Context:
         priest_project(self.h, prob, n, xi, lam_io, xb, r, c1)
         return xb, lam_io, r, c1
 
+    def project_plain(self, p, xi, lam=None):
+        """As project, through the plain per-problem FP32 path."""
+        D = int(p["dims"]) * (self.cfg.degree + 1)
+        xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64).reshape(-1, D))
+        n = xi.shape[0]
+        lam_io = None if lam is None else np.ascontiguousarray(np.asarray(lam, dtype=np.float64).reshape(n, D)).copy()
+        xb = np.zeros((n, D))
+        r = np.zeros(n)
+        c1 = np.zeros(n)
+        prob, keep = make_problem(p)
+        priest_project_plain(self.h, prob, n, xi, lam_io, xb, r, c1)
+        return xb, lam_io, r, c1
+
+    def plan_plain(self, p, z=None, mu0=None, cov0=None, cem=None):
+        """As plan, through the plain per-problem FP32 path."""
+        prob, keep = make_problem(p, cem, per_problem_shape=cem is not None)
+        res = priest_result()
+        z = None if z is None else np.ascontiguousarray(np.asarray(z, dtype=np.float64))
+        priest_plan_plain(self.h, prob, mu0, cov0, z, res)
+        return result_dict(res)
+
     def plan(self, p, z=None, mu0=None, cov0=None, cem=None):
-        prob, keep = make_problem(p, cem)
+        """Alg. 1 on p; with cem given, the problem's own sizes (dims, n_p,
+        horizon, bounds, sample counts) override the context defaults."""
+        prob, keep = make_problem(p, cem, per_problem_shape=cem is not None)
         res = priest_result()
         if z is None:
             priest_plan(self.h, prob, mu0, cov0, res)
@@ -363,6 +437,25 @@ class Context:
             z = np.ascontiguousarray(np.asarray(z, dtype=np.float64))
             priest_plan_z(self.h, prob, mu0, cov0, z, res)
         return result_dict(res)
+
+    def submit(self, p, cem=None, robot_id=-1, seed=None):
+        """Queues a solve on the serving loop; returns the ticket."""
+        prob, keep = make_problem(p, cem, robot_id=robot_id, seed=seed, per_problem_shape=True)
+        return priest_submit(self.h, prob)
+
+    def poll(self, ticket):
+        """The result dict, or None while the solve is pending."""
+        res = priest_result()
+        st = priest_poll(self.h, ticket, res)
+        return None if st == PRIEST_PENDING else result_dict(res)
+
+    def wait(self, ticket, timeout_ms=-1.0):
+        res = priest_result()
+        priest_wait(self.h, ticket, res, timeout_ms)
+        return result_dict(res)
+
+    def serve_stats(self):
+        return priest_serve_stats_get(self.h)
 
     def launches(self):
         return priest_kernel_launches(self.h)

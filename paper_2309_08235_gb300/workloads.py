@@ -157,6 +157,84 @@ def batched_problems(n_problems=256, seed0=100):
     return out
 
 
+def _place_fast(rng, n, lo, hi, radii, keep_clear, dims):
+    """As _place, vectorised: rejected centres are redrawn together."""
+    lo = np.broadcast_to(np.asarray(lo, dtype=float), (dims,))
+    hi = np.broadcast_to(np.asarray(hi, dtype=float), (dims,))
+    out = lo + (hi - lo) * rng.random((n, dims))
+    keep = np.asarray(keep_clear, dtype=float).reshape(-1, dims)
+    for _ in range(1000):
+        d = np.linalg.norm(out[:, None, :] - keep[None, :, :], axis=2).min(axis=1)
+        bad = d <= radii + 0.5
+        if not bad.any():
+            break
+        out[bad] = lo + (hi - lo) * rng.random((int(bad.sum()), dims))
+    return out
+
+
+def serving_requests(rate=500.0, duration=60.0, seed=7, frac_3d=0.2, frac_warm=0.3, shift_s=0.5,
+                     sizes=None):
+    """A Poisson stream of planning requests (arrival time, problem, CEM
+    overrides, robot id), sizes as in batched_problems: n_obs log-uniform in
+    [10, 400], N in {256, 512, 1024, 2048}, n_p in {60, 100, 150},
+    horizon 0.08 s * n_p.  A fraction frac_3d are 3-D (ellipsoids in
+    20 x 20 x 8 m, v_max 2, a_max 3); a fraction frac_warm are replans of an
+    earlier robot: same goal, obstacles and sizes, the start moved shift_s
+    seconds along the straight start-goal line at the previous request's mean
+    speed and moving obstacles advanced by shift_s.  sizes: optional list of
+    (n_obs, N, n_p) choices that replaces the ranges (small test streams)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    robots = []  # (robot id, last problem)
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        k = len(out)
+        if robots and rng.random() < frac_warm:
+            j = int(rng.integers(max(0, len(robots) - 64), len(robots)))
+            rid, prev, n_samples = robots[j]
+            p = dict(prev)
+            b0 = np.array(prev["b0"], dtype=float)
+            bf = np.array(prev["bf"], dtype=float)
+            step = (bf[:, 0] - b0[:, 0]) * (shift_s / prev["horizon"])
+            b0[:, 0] = b0[:, 0] + step
+            p["b0"] = b0
+            p["center"] = np.asarray(prev["center"]) + shift_s * np.asarray(prev["vel"])
+            p["seed"] = int(rng.integers(0, 2**62))
+            robots[j] = (rid, p, n_samples)
+            out.append((t, p, n_samples, rid))
+            continue
+        if sizes is not None:
+            n_obs, n_samples, n_p = sizes[int(rng.integers(0, len(sizes)))]
+        else:
+            n_obs = int(round(math.exp(rng.uniform(math.log(10), math.log(400)))))
+            n_samples = int(rng.choice([256, 512, 1024, 2048]))
+            n_p = int(rng.choice([60, 100, 150]))
+        horizon = 0.08 * n_p
+        pseed = int(rng.integers(0, 2**62))
+        if rng.random() < frac_3d:
+            a = rng.uniform(0.3, 0.8, n_obs)
+            b = rng.uniform(0.3, 0.8, n_obs)
+            start, goal = np.array([1.0, 1.0, 1.0]), np.array([19.0, 19.0, 7.0])
+            c = _place_fast(rng, n_obs, [0.0, 0.0, 0.0], [20.0, 20.0, 8.0], np.maximum(a, b), [start, goal], 3)
+            p = problem(3, n_p, horizon, start, goal, c, None, np.stack([a, b], 1), 2.0, 3.0, pseed)
+        else:
+            r = rng.uniform(0.2, 0.5, n_obs)
+            start, goal = np.array([1.0, 1.0]), np.array([29.0, 29.0])
+            c = _place_fast(rng, n_obs, 2.0, 28.0, r, [start, goal], 2)
+            v = np.zeros((n_obs, 2))
+            n_dyn = n_obs // 10
+            if n_dyn:
+                v[n_obs - n_dyn:] = rng.uniform(-1.0, 1.0, (n_dyn, 2))
+            p = problem(2, n_p, horizon, start, goal, c, v, np.stack([r, r], 1), VMAX_2D, AMAX_2D, pseed)
+        rid = k
+        robots.append((rid, p, n_samples))
+        out.append((t, p, n_samples, rid))
+    return out
+
+
 def normals(seed, shape):
     """Standard normal draws for the sampling step (passed to both sides)."""
     return np.random.default_rng(seed).standard_normal(shape)

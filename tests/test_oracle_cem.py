@@ -139,6 +139,37 @@ def test_plan_composes_alg1(oracle):
     np.testing.assert_array_equal(a["best"], b["best"])
 
 
+def test_plan_warm_start_composes_alg1(oracle):
+    """The multiplier warm start enters only the first CEM iteration's
+    projection as lambda^0, and the returned multipliers are those of the last
+    projection: the warm plan equals Alg. 1 assembled from the stage functions
+    with that lambda^0; with lam0 = 0 it is the cold plan."""
+    p = W.scene_small_2d(n_obs=6, n_p=30)
+    cem = W.cem_settings(20, 8, 2, n_proj=14, n_elite=4)
+    D = 22
+    z = W.normals(19, (cem["cem_iters"], cem["n_samples"], D))
+    lam0 = W.normals(20, (cem["n_samples"], D)) * 0.5
+    got = oracle.plan(p, cem, z=z, lam0=lam0, want_lam=True)
+    mu = oracle.default_mean(p)
+    cov = np.eye(D) * cem["init_std"] ** 2
+    for l in range(cem["cem_iters"]):
+        S = cov + cem["chol_eps"] * np.trace(cov) / D * np.eye(D)
+        xi = mu + z[l] @ oracle.cholesky(S).T
+        xb, lam = oracle.project(p, xi, cem["proj_iters"], lam=lam0 if l == 0 else None)
+        r, c1 = oracle.residual_cost(p, xb)
+        _, ei = oracle.select(r, c1 + r, cem["n_proj"], cem["n_elite"])
+        mu, cov = oracle.refit(xb[ei], (c1 + r)[ei], mu, cov, cem["sigma_lr"], cem["gamma"])
+    np.testing.assert_allclose(got["best"], xb[ei[0]], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got["mu"], mu, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(got["lam"], lam, rtol=1e-12, atol=1e-12)
+    cold = oracle.plan(p, cem, z=z)
+    zero = oracle.plan(p, cem, z=z, lam0=np.zeros((cem["n_samples"], D)))
+    np.testing.assert_array_equal(zero["best"], cold["best"])
+    np.testing.assert_array_equal(zero["mu"], cold["mu"])
+    # the warm start changes the first projection, hence the answer
+    assert not np.array_equal(got["mu"], cold["mu"])
+
+
 def test_plan_teaser_scene_finds_collision_free(oracle):
     """Fig. teaser: with every initial sample inside the obstacle, PRIEST returns
     a trajectory that clears it (paper's N_b / N_proj / N_elite, fewer iters)."""
