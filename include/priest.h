@@ -271,6 +271,17 @@ priest_status priest_project_plain(priest_ctx *ctx, const priest_problem *prob, 
                                    double *lambda_io, double *xi_bar_out, double *resid_out,
                                    double *cost_out);
 
+/* Diagnostic of the tensor-core path used by PRIEST_MIXED_BF16: one product
+ * D = A B^T on the 5th-generation tensor core (tcgen05.mma, BF16 inputs,
+ * FP32 accumulation in tensor memory), A 128 x k and B n x k row-major BF16
+ * bit patterns (host), D 128 x n FP32 (host).  n a multiple of 16 in
+ * [16, 256], k a multiple of 16 in [16, 64].  swap = 1 exchanges the two
+ * byte strides of the shared-memory descriptors (a layout check: the
+ * product is right only for swap = 0).  Allocates and synchronises; for
+ * tests.  PRIEST_ERR_TIMEOUT if the MMA completion was not observed. */
+priest_status priest_tc_selftest(int n, int k, int swap, const uint16_t *a_host, const uint16_t *b_host,
+                                 float *d_host);
+
 /* Waits for the context stream and reports any kernel-side error status. */
 priest_status priest_sync(priest_ctx *ctx);
 

@@ -34,7 +34,7 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
            "priest_project_noalloc", "priest_plan_batch", "priest_wait", "priest_serve_stats_get",
            "priest_rng_normal_device", "priest_plan_plain", "priest_plan_plain_device",
-           "priest_project_plain"]
+           "priest_project_plain", "priest_tc_selftest"]
 
 
 class PriestError(RuntimeError):
@@ -125,6 +125,7 @@ def lib():
             "priest_plan_plain": (C.c_int, [vp, C.POINTER(priest_problem), _P, _P, _P, C.POINTER(priest_result)]),
             "priest_plan_plain_device": (C.c_int, [vp, vp, vp, vp]),
             "priest_project_plain": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P, _P, _P]),
+            "priest_tc_selftest": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -271,6 +272,18 @@ def priest_plan_plain_device(ctx, h, z_ptr, out_ptr):
 def priest_project_plain(ctx, prob, n, xi, lambda_io, xi_bar_out, resid_out, cost_out):
     return _check(ctx, lib().priest_project_plain(ctx, C.byref(prob), int(n), *(
         None if a is None else a.ctypes.data_as(_P) for a in (xi, lambda_io, xi_bar_out, resid_out, cost_out))))
+
+
+def priest_tc_selftest(a_bf16, b_bf16, swap=0):
+    """D = A B^T on the tensor core; a_bf16 (128 x k) and b_bf16 (n x k) are
+    uint16 BF16 bit patterns.  Returns (status, D)."""
+    a = np.ascontiguousarray(a_bf16, dtype=np.uint16)
+    b = np.ascontiguousarray(b_bf16, dtype=np.uint16)
+    n, k = b.shape
+    d = np.zeros((128, n), dtype=np.float32)
+    st = lib().priest_tc_selftest(int(n), int(k), int(swap), a.ctypes.data_as(C.c_void_p),
+                                  b.ctypes.data_as(C.c_void_p), d.ctypes.data_as(C.c_void_p))
+    return st, d
 
 
 def priest_submit(ctx, prob):
