@@ -57,7 +57,12 @@ typedef enum {
 typedef enum {
     PRIEST_FP64_CHECK = 0,     /* every step in FP64 (parity mode) */
     PRIEST_FP32 = 1,           /* projection in FP32, sampling / refit / Cholesky / KKT in FP64 */
-    PRIEST_MIXED_BF16 = 2      /* reserved: BF16 basis products, FP32 final sweep */
+    PRIEST_MIXED_BF16 = 2      /* FP32 projection whose (point, obstacle) tests are one BF16 tensor-core
+                                  product per CTA (split high/low operands, FP32 accumulation) that
+                                  selects the pairs for the exact FP32 test; same results as FP32 up
+                                  to summation order.  Shapes the tensor-core kernel cannot hold
+                                  (more than ~500 obstacle columns) and the batched / serving paths
+                                  run the FP32 kernel. */
 } priest_precision;
 
 typedef struct priest_ctx priest_ctx;

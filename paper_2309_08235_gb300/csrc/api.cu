@@ -540,11 +540,77 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
     return best;
 }
 
+// PRIEST_MIXED_BF16: the projection with the pair tests on the tensor core
+// (project_tc.cu).  Returns false when the shape does not fit that kernel
+// (too many obstacles for tensor memory, or shared memory); the caller then
+// runs the FMA kernel.
+bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi, const double *z,
+                        const double *lam_in, double *lam_out, double *xb, double *r, double *c1, cudaStream_t st,
+                        priest_status *out)
+{
+    Shape sh = h->sh;
+    sh.N = N;
+    int S = 0;
+    const TcPlan tp = tc_choose(sh, N, ctx->n_sm, &S);
+    if (!tp.smem || S < 1) return false;
+    Tiling t;
+    std::memset(&t, 0, sizeof(t));
+    t.S = S;
+    t.C = tp.nseg;
+    t.ws = 1;
+    TcParams q;
+    std::memset(&q, 0, sizeof(q));
+    q.p = proj_params<float>(ctx, h, t);
+    q.p.N = N;
+    q.p.mode = mode;
+    q.p.xi_in = xi;
+    q.p.mu = h->mu;
+    q.p.Lc = h->L;
+    q.p.z = z;
+    q.p.lam_in = lam_in;
+    q.p.lam_out = lam_out;
+    q.p.want_lambda = lam_out != nullptr;
+    q.p.xi_bar = xb;
+    q.p.r_out = r;
+    q.p.c1_out = c1;
+    q.center = h->center;
+    q.vel = h->vel;
+    q.semi = h->semi;
+    q.origin64 = h->tab64 + table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs).origin;
+    q.status = ctx->d_status;
+    q.tp = tp;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->profile && st == ctx->stream) {
+        if (!ctx->prof_free.empty()) {
+            ev = ctx->prof_free.back();
+            ctx->prof_free.pop_back();
+        } else {
+            cudaEventCreate(&ev.first);
+            cudaEventCreate(&ev.second);
+        }
+        cudaEventRecord(ev.first, st);
+    }
+    cudaError_t e = launch_project_tc(q, st);
+    ctx->launches++;
+    if (ev.first) {
+        cudaEventRecord(ev.second, st);
+        ctx->prof_used.push_back(ev);
+    }
+    *out = e == cudaSuccess ? PRIEST_OK : cuda_fail(ctx, e, "tensor-core projection kernel");
+    return true;
+}
+
 template <typename Real>
 priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi,
                               const double *z, const double *lam_in, double *lam_out, double *xb, double *r,
                               double *c1, cudaStream_t st)
 {
+    if constexpr (sizeof(Real) == 4) {
+        priest_status ts;
+        if (ctx->cfg.precision == PRIEST_MIXED_BF16 &&
+            enqueue_project_tc(ctx, h, N, mode, xi, z, lam_in, lam_out, xb, r, c1, st, &ts))
+            return ts;
+    }
     Shape sh = h->sh;
     sh.N = N;
     Tiling t = choose_tiling<Real>(sh, N, ctx->n_sm);
@@ -631,6 +697,7 @@ priest_status check_status(priest_ctx *ctx, int *d_status, cudaStream_t st)
         PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
         if (hs & kStatusCholesky) return fail(ctx, PRIEST_ERR_NUMERIC, "covariance Cholesky met a non-positive pivot");
         if (hs & kStatusKkt) return fail(ctx, PRIEST_ERR_NUMERIC, "KKT block met a non-positive pivot");
+        if (hs & kStatusTensor) return fail(ctx, PRIEST_ERR_TIMEOUT, "tensor-core completion wait timed out");
         return fail(ctx, PRIEST_ERR_NUMERIC, "numerical failure on the device");
     }
     return PRIEST_OK;
@@ -665,7 +732,7 @@ void gaussian_stream(uint64_t seed, int64_t count, double *out)
 // ---------------------------------------------------------------------------
 priest_status plain_workspace(priest_ctx *ctx, const Shape &sh, int N, float **out)
 {
-    if (ctx->cfg.precision != PRIEST_FP32) return fail(ctx, PRIEST_ERR_INVALID, "the plain path runs in FP32 only");
+    if (ctx->cfg.precision == PRIEST_FP64_CHECK) return fail(ctx, PRIEST_ERR_INVALID, "the plain path runs in FP32 only");
     const size_t need = plain_work_floats(sh.dims, sh.nv, sh.nf, sh.n_p, std::max(N, 1));
     if (need > ctx->plain_cap) {
         PRIEST_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1009,7 +1076,8 @@ priest_status priest_create(const priest_config *cfg, void *cuda_stream, priest_
     *out = nullptr;
     if (cfg->degree < 5 || cfg->degree > 15 || cfg->proj_iters < 0 || cfg->cem_iters < 1 || !(cfg->rho > 0) ||
         !(cfg->gamma > 0) || cfg->sigma_lr < 0 || cfg->sigma_lr > 1 || cfg->chol_eps < 0 ||
-        (cfg->precision != PRIEST_FP64_CHECK && cfg->precision != PRIEST_FP32) || cfg->serve_slots < 0)
+        (cfg->precision != PRIEST_FP64_CHECK && cfg->precision != PRIEST_FP32 && cfg->precision != PRIEST_MIXED_BF16) ||
+        cfg->serve_slots < 0)
         return PRIEST_ERR_INVALID;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

@@ -23,6 +23,7 @@ enum : int {
     kStatusCholesky = 1,   // non-positive pivot in the covariance Cholesky
     kStatusKkt = 2,        // non-positive pivot in the shared KKT block
     kStatusNaN = 4,
+    kStatusTensor = 8,     // a tensor-core completion wait ran out of time
 };
 
 // Resolved shape and scalar data of one problem.
@@ -120,6 +121,28 @@ struct ProjParams {
     const double *xi_in, *mu, *Lc, *z, *lam_in;
     double *xi_bar, *lam_out, *r_out, *c1_out;
 };
+
+// Plan of a tensor-core projection launch (project_tc.cu): M-tiles of 128
+// trajectory points, obstacle columns (static then moving, each padded to 16),
+// tiles per tensor-memory wave, column segments per tile, operand layout.
+struct TcPlan {
+    int rows, tiles, ns_pad, nm_pad, tpw, waves, nseg, kA;
+    uint32_t ncols;                            // tensor-memory columns allocated
+    size_t smem;                               // dynamic shared memory (0: shape not supported)
+    size_t off_marg, off_a, off_bs, off_bm;    // byte offsets of margins, A, B_static, B_moving
+};
+
+struct TcParams {
+    ProjParams<float> p;                       // p.S samples per CTA, p.C = nseg
+    const double *center, *vel, *semi;         // FP64 obstacles, static first
+    const double *origin64;                    // frame origin (FP64 tables)
+    int *status;
+    TcPlan tp;
+};
+
+TcPlan tc_plan(const Shape &sh, int S);
+TcPlan tc_choose(const Shape &sh, int N, int n_sm, int *S_out);
+cudaError_t launch_project_tc(const TcParams &q, cudaStream_t st);
 
 // Tiling chosen for one projection launch.
 struct Tiling {
