@@ -40,12 +40,21 @@ FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 
 
-def workload_desc(p, cem):
+WORKLOADS = {"clutter2d": "clutter2d_fp32", "ellipsoid3d": "ellipsoid3d_mixed"}
+
+
+def workload_desc(p, cem, precision="fp32"):
+    prec = ("FP32 projection" if precision == "fp32" else
+            "FP32 projection, pair tests selected by a split-BF16 tensor-core product")
+    if p["dims"] == 3:
+        return (f"3-D point-to-point: {p['n_obs']} static ellipsoids in 20x20x8 m, N={cem['n_samples']} samples, "
+                f"n_p={p['n_p']}, degree {p['degree']}, K={cem['proj_iters']} projection iters, "
+                f"L={cem['cem_iters']} CEM iters, {cem['n_elite']} elites, {prec}")
     return (f"2-D clutter: {p['n_obs'] - int(np.count_nonzero(np.abs(p['vel']).sum(1)))} static + "
             f"{int(np.count_nonzero(np.abs(p['vel']).sum(1)))} moving circles in 30x30 m, "
             f"N={cem['n_samples']} samples, n_p={p['n_p']}, degree {p['degree']}, "
             f"K={cem['proj_iters']} projection iters, L={cem['cem_iters']} CEM iters, "
-            f"{cem['n_elite']} elites, FP32 projection")
+            f"{cem['n_elite']} elites, {prec}")
 
 
 def flops_per_sample_iter(p, nf=5):
@@ -188,13 +197,14 @@ def run_ours(args):
 
         dist.init_process_group("nccl")
     B.build()
-    p, cem = W.workload(WORKLOAD)
+    p, cem = W.workload(WORKLOADS.get(args.workload, WORKLOAD))
     N, K, L = cem["n_samples"], cem["proj_iters"], cem["cem_iters"]
     D = p["dims"] * (p["degree"] + 1)
     units = N * K * L
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    ctx = P.Context(p, cem, precision=P.PRIEST_FP32, stream=stream.cuda_stream)
+    prec = P.PRIEST_MIXED_BF16 if args.precision == "mixed" else P.PRIEST_FP32
+    ctx = P.Context(p, cem, precision=prec, stream=stream.cuda_stream)
     prob, keep = P.make_problem(p, cem)
     h = P.priest_load(ctx.h, prob)
     z_host = torch.from_numpy(W.normals(1000 + rank, (L, N, D))).pin_memory()
@@ -251,12 +261,14 @@ def run_ours(args):
     peak = fp32_peak_tflops()
     traffic = None
     prof_path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if os.path.exists(prof_path):
+    kname = ("project_kernel (FP32, %d-D)" % p["dims"] if args.precision == "fp32" else
+             "project_tc_kernel (tcgen05 pair tests, %d-D)" % p["dims"])
+    if os.path.exists(prof_path) and args.precision == "fp32" and p["dims"] == 2:
         for ln in open(prof_path):
             if ln.startswith("project_kernel_bytes_per_launch:"):
                 traffic = int(ln.split(":", 1)[1])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "project_kernel (FP32, 2-D)",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
                 "flops_per_launch": flops_launch,
                 "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
@@ -310,7 +322,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(p, cem), "l2": "flushed between timed steps (256 MB write)",
+            "config": {"workload": workload_desc(p, cem, args.precision),
+                       "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "units_per_step": units},
             "solves_per_s": args.steps * world / (total_ms / 1e3),
@@ -530,7 +543,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["clutter2d", "batched", "serving"], default="clutter2d",
+    ap.add_argument("--workload", choices=["clutter2d", "ellipsoid3d", "batched", "serving"], default="clutter2d",
                     help="clutter2d: the default bench line; batched: 256 uneven problems; serving: Poisson "
                          "request stream (both report only)")
     ap.add_argument("--batch-problems", type=int, default=256)
@@ -539,6 +552,8 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--seq-sample", type=int, default=300)
     ap.add_argument("--plain-steps", type=int, default=10, help="timed solves of the plain per-problem path")
+    ap.add_argument("--precision", choices=["fp32", "mixed"], default="fp32",
+                    help="fp32: FMA pair tests; mixed: pair tests selected by the BF16 tensor-core product")
     ap.add_argument("--dump", default=None, help="serving: save per-request arrival / latency / sizes (.npz)")
     args = ap.parse_args()
     if args.impl == "reference":

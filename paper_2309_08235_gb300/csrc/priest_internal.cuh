@@ -124,9 +124,9 @@ struct ProjParams {
 
 // Plan of a tensor-core projection launch (project_tc.cu): M-tiles of 128
 // trajectory points, obstacle columns (static then moving, each padded to 16),
-// tiles per tensor-memory wave, column segments per tile, operand layout.
+// column segments per tile (units of work), operand layout.
 struct TcPlan {
-    int rows, tiles, ns_pad, nm_pad, tpw, waves, nseg, kA;
+    int rows, tiles, ns_pad, nm_pad, nseg, regw, kA;  // regw: tensor-memory columns of one segment region
     uint32_t ncols;                            // tensor-memory columns allocated
     size_t smem;                               // dynamic shared memory (0: shape not supported)
     size_t off_marg, off_a, off_bs, off_bm;    // byte offsets of margins, A, B_static, B_moving

@@ -47,6 +47,7 @@ namespace {
 constexpr int kTcThreads = 512;
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr uint64_t kTcWaitNs = 2000000000ull;  // MMA completion wait limit (2 s)
+constexpr int kMaxSeg = 32;                     // column segments per tile
 
 using detail::kFull;
 using detail::ld4;
@@ -242,11 +243,107 @@ __device__ __forceinline__ void exact_pair(const float *o, float x, float y, flo
     }
 }
 
+// MMAs of one unit (tile, column segment) into the tensor-memory region at
+// column `dcol`: the segment's static columns with K = 16, its moving ones
+// with K = 32.  Issued by one thread; the caller commits.
+template <int DIMS>
+__device__ __forceinline__ void issue_unit(const TcPlan &tp, int tile, int lo, int hi, const unsigned char *sA,
+                                           const unsigned char *sBs, const unsigned char *sBm, uint32_t dcol)
+{
+    const uint32_t a_addr = tc::smem_u32(sA) + uint32_t(tile) * 16u * tc::sbo(tp.kA);
+    const int s_lo = lo, s_hi = min(hi, tp.ns_pad);
+    if (s_hi > s_lo) {
+        const uint64_t ad = tc::smem_desc(a_addr, tc::kLbo, tc::sbo(tp.kA));
+        const uint64_t bd = tc::smem_desc(tc::smem_u32(sBs) + uint32_t(s_lo / 8) * tc::sbo(16), tc::kLbo, tc::sbo(16));
+        tc::mma_bf16(dcol, ad, bd, tc::idesc_bf16_f32(128, s_hi - s_lo), 0u);
+    }
+    const int m_lo = max(lo, tp.ns_pad), m_hi = hi;
+    if (m_hi > m_lo) {
+        const uint32_t id = tc::idesc_bf16_f32(128, m_hi - m_lo);
+        for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ad = tc::smem_desc(a_addr + uint32_t(ks) * 2u * tc::kLbo, tc::kLbo, tc::sbo(tp.kA));
+            const uint64_t bd = tc::smem_desc(tc::smem_u32(sBm) + uint32_t((m_lo - tp.ns_pad) / 8) * tc::sbo(32) +
+                                                  uint32_t(ks) * 2u * tc::kLbo,
+                                              tc::kLbo, tc::sbo(32));
+            tc::mma_bf16(dcol + uint32_t(m_lo - lo), ad, bd, id, ks ? 1u : 0u);
+        }
+    }
+}
+
+struct CdArgs {
+    const float *part, *rb, *rv, *ra;  // this (sample, axis): residual planes, offset to the sample
+    const float *basis, *fb, *W;
+    float *lam, *c;
+    const float *xi;
+    int part_stride, C, use_bounds, n_p, nv, nf, nfp, fbs;
+    float rho;
+};
+
+// g = F^T (F xi_bar - e) (eq. lag) for one (sample, axis), lambda -= rho g,
+// and the shared-inverse step c += W (xi_F + lambda_F - rho g_F - c) on the
+// free columns.  FREE: the NGT = nf free columns from the packed basis;
+// otherwise ng <= NGT columns from col_lo (all n_v when the multipliers are
+// returned).  One warp; lanes over time stamps.
+template <int NGT, bool FREE>
+__device__ __forceinline__ void cd_unit(const CdArgs &a, int col_lo, int ng, int lane)
+{
+    float acc[NGT];
+#pragma unroll
+    for (int i = 0; i < NGT; ++i) acc[i] = 0.f;
+    for (int t = lane; t < a.n_p; t += 32) {
+        float rp = a.part[t];
+        for (int c = 1; c < a.C; ++c) rp += a.part[c * a.part_stride + t];
+        if (a.use_bounds) rp += a.rb[t];
+        const float rv = a.rv[t], ra = a.ra[t];
+        if constexpr (FREE) {
+            constexpr int NV4 = (NGT + 3) / 4;
+            const float *fbt = a.fb + size_t(t) * a.fbs;
+            float b[3][4 * NV4];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int v = 0; v < NV4; ++v)
+                    ld4(fbt + q * a.nfp + 4 * v, b[q][4 * v], b[q][4 * v + 1], b[q][4 * v + 2], b[q][4 * v + 3]);
+#pragma unroll
+            for (int i = 0; i < NGT; ++i) acc[i] = fmaf(b[0][i], rp, fmaf(b[1][i], rv, fmaf(b[2][i], ra, acc[i])));
+        } else {
+            const float *b0 = a.basis + size_t(t) * a.nv + col_lo;
+            const float *b1 = b0 + size_t(a.n_p) * a.nv;
+            const float *b2 = b1 + size_t(a.n_p) * a.nv;
+#pragma unroll
+            for (int i = 0; i < NGT; ++i)
+                if (i < ng) acc[i] = fmaf(b0[i], rp, fmaf(b1[i], rv, fmaf(b2[i], ra, acc[i])));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NGT; ++i)
+        if (FREE || i < ng)
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(kFull, acc[i], off);
+    float g = 0.f, du = 0.f;
+    const int fl = lane - (kFree0 - col_lo);
+#pragma unroll
+    for (int i = 0; i < NGT; ++i) {
+        if (FREE || i < ng) {
+            const int ci = col_lo + i, fi = ci - kFree0;
+            if (lane == i) g = acc[i];
+            if (fi >= 0 && fi < a.nf) {
+                const float ui = a.xi[fi] + (a.lam[ci] - a.rho * acc[i]) - a.rho * acc[i] - a.c[fi];
+                if (fl >= 0 && fl < a.nf) du = fmaf(a.W[fl * a.nf + fi], ui, du);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < ng) a.lam[col_lo + lane] -= a.rho * g;
+    if (fl >= 0 && fl < a.nf && lane < ng) a.c[fl] += du;
+    __syncwarp();
+}
+
 template <int DIMS, int NF>
 __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParams q)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar[8];  // two per warpgroup
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const ProjParams<float> &p = q.p;
@@ -267,6 +364,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
     float *sXi = sm + L.xi, *sLam = sm + L.lam, *sC = sm + L.c, *sPos = sm + L.pos;
     float *sRV = sm + L.rv, *sRA = sm + L.ra, *sRB = sm + L.rb, *sPart = sm + L.part;
     float *sMarg = reinterpret_cast<float *>(smem_raw + tp.off_marg);
+    float *sTrow = sMarg + tp.tiles * 128;  // time of each row's point
     unsigned char *sA = smem_raw + tp.off_a, *sBs = smem_raw + tp.off_bs, *sBm = smem_raw + tp.off_bm;
     const float rho = p.rho, vmax = p.vmax, amax = p.amax, vmax2 = vmax * vmax, amax2 = amax * amax;
     const int st = obs_stride(DIMS);
@@ -313,6 +411,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
     // margin scale (non-negative floats, maxima through their bit patterns):
     // O = max_j |o_j| + T |v_j|, a_max, kappa_max
     __shared__ int s_oe, s_am, s_km;
+    __shared__ int s_seg[kMaxSeg + 1];  // first 16-column chunk of each segment
+    if (tid <= tp.nseg) s_seg[tid] = (tid * ncol16) / tp.nseg;
+    for (int i = tid; i < tp.tiles * 128; i += kTcThreads) sTrow[i] = sT[i % np_];
     if (tid == 0) {
         s_oe = 0;
         s_am = 0;
@@ -337,16 +438,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
     }
     // tensor memory, completion barrier
     if (warp == 0) tc::tmem_alloc(&s_tmem, tp.ncols);
-    if (tid == 0) {
-        tc::mbar_init(&s_mbar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (tid < 8) tc::mbar_init(&s_mbar[tid], 1);
+    if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = s_tmem;
+    // phase-A point walk without divisions: thread tid starts at point tid
+    const int s_a0 = tid / np_, t_a0 = tid - (tid / np_) * np_;
+    const int step_s = kTcThreads / np_, step_t = kTcThreads - (kTcThreads / np_) * np_;
     const float oeff = __int_as_float(s_oe) + __int_as_float(s_am) + 1.f, kmax = __int_as_float(s_km);
-    uint32_t parity = 0;
+    uint32_t par = 0;  // phase parities of this warpgroup's two barriers
     float smin[DIMS], smax[DIMS];
 #pragma unroll
     for (int ax = 0; ax < DIMS; ++ax) {
@@ -359,8 +461,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
     for (int k = 0; k <= p.K; ++k) {
         const bool fin = (k == p.K);
         // ---- A: trajectory, velocity / acceleration / workspace residuals, features
-        for (int i = tid; i < n_pts; i += kTcThreads) {
-            const int s = i / np_, t = i - s * np_;
+        for (int i = tid, s = s_a0, t = t_a0; i < n_pts;
+             i += kTcThreads, s += step_s, t += step_t, s += (t >= np_), t -= (t >= np_) ? np_ : 0) {
             const float *cc = sC + s * DIMS * nfp;
             float pos[DIMS], vel[DIMS], acc[DIMS];
 #pragma unroll
@@ -450,51 +552,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        // ---- B: pair tests on the tensor core, wave by wave
-        for (int w = 0; w < tp.waves && ncol16 > 0; ++w) {
-            const int t0 = w * tp.tpw, t1 = min(tp.tiles, t0 + tp.tpw);
-            if (tid == 0) {
-                for (int tile = t0; tile < t1; ++tile) {
-                    const uint32_t dcol = tbase + uint32_t((tile - t0) * (tp.ns_pad + tp.nm_pad));
-                    const uint32_t a_addr = tc::smem_u32(sA) + uint32_t(tile) * 16u * tc::sbo(tp.kA);
-                    // static obstacles: K = 16, N in pieces of at most 256
-                    for (int c0 = 0; c0 < tp.ns_pad; c0 += 256) {
-                        const int n = min(256, tp.ns_pad - c0);
-                        const uint64_t ad = tc::smem_desc(a_addr, tc::kLbo, tc::sbo(tp.kA));
-                        const uint64_t bd = tc::smem_desc(tc::smem_u32(sBs) + uint32_t(c0 / 8) * tc::sbo(16), tc::kLbo,
-                                                          tc::sbo(16));
-                        tc::mma_bf16(dcol + uint32_t(c0), ad, bd, tc::idesc_bf16_f32(128, n), 0u);
-                    }
-                    // moving obstacles: K = 32 (two steps)
-                    for (int c0 = 0; c0 < tp.nm_pad; c0 += 256) {
-                        const int n = min(256, tp.nm_pad - c0);
-                        const uint32_t id = tc::idesc_bf16_f32(128, n);
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t ad = tc::smem_desc(a_addr + uint32_t(ks) * 2u * tc::kLbo, tc::kLbo,
-                                                              tc::sbo(tp.kA));
-                            const uint64_t bd =
-                                tc::smem_desc(tc::smem_u32(sBm) + uint32_t(c0 / 8) * tc::sbo(32) + uint32_t(ks) * 2u * tc::kLbo,
-                                              tc::kLbo, tc::sbo(32));
-                            tc::mma_bf16(dcol + uint32_t(tp.ns_pad + c0), ad, bd, id, ks ? 1u : 0u);
-                        }
-                    }
+        // ---- B: pair tests on the tensor core.  Units (tile, column segment)
+        //      go round-robin to the warpgroups; each warpgroup owns two
+        //      tensor-memory regions and runs its own pipeline: its leader
+        //      issues the MMAs of the next unit into one region while the
+        //      warpgroup scans the other.
+        if (ncol16 > 0) {
+            const int units = tp.tiles * tp.nseg;
+            const bool leader = (tid & 127) == 0;
+            int it = 0;
+            // (tile, segment) of this warpgroup's current and next unit, advanced by 4 units a step
+            int tile = wg / tp.nseg, seg = wg - (wg / tp.nseg) * tp.nseg;
+            int ntile = tile, nseg_ = seg + 4;
+            while (nseg_ >= tp.nseg) {
+                nseg_ -= tp.nseg;
+                ++ntile;
+            }
+            if (leader && wg < units) {
+                issue_unit<DIMS>(tp, tile, 16 * s_seg[seg], 16 * s_seg[seg + 1], sA, sBs, sBm,
+                                 tbase + uint32_t(2 * wg) * tp.regw);
+                tc::mma_commit(&s_mbar[2 * wg]);
+            }
+            for (int u = wg; u < units; u += 4, ++it) {
+                const int b = it & 1;
+                if (leader && u + 4 < units) {
+                    issue_unit<DIMS>(tp, ntile, 16 * s_seg[nseg_], 16 * s_seg[nseg_ + 1], sA, sBs, sBm,
+                                     tbase + uint32_t(2 * wg + (b ^ 1)) * tp.regw);
+                    tc::mma_commit(&s_mbar[2 * wg + (b ^ 1)]);
                 }
-                tc::mma_commit(&s_mbar);
-            }
-            __syncwarp();
-            // (warp-uniform outcome: the TMEM loads below are warp-collective)
-            const bool ok = __all_sync(kFull, tc::mbar_wait_bounded(&s_mbar, parity, kTcWaitNs));
-            parity ^= 1u;
-            if (!ok) {
-                s_abort = 1;
-                if (q.status) atomicOr(q.status, kStatusTensor);
-            }
-            tc::fence_after_sync();
-            // scan: units (tile, column segment) over the warpgroups
-            const int units = (t1 - t0) * tp.nseg;
-            for (int u = wg; u < units && ok; u += kTcThreads / 128) {
-                const int tile = t0 + u / tp.nseg, seg = u - (u / tp.nseg) * tp.nseg;
-                const int c16a = (seg * ncol16) / tp.nseg, c16b = ((seg + 1) * ncol16) / tp.nseg;
+                // (warp-uniform outcome: the TMEM loads below are warp-collective)
+                const bool ok = __all_sync(kFull, tc::mbar_wait_bounded(&s_mbar[2 * wg + b], (par >> b) & 1u, kTcWaitNs));
+                par ^= 1u << b;
+                if (!ok) {
+                    s_abort = 1;
+                    if (q.status) atomicOr(q.status, kStatusTensor);
+                }
+                tc::fence_after_sync();
+                const int c16a = s_seg[seg], c16b = s_seg[seg + 1];
                 const int row = 32 * wq + lane, i = tile * 128 + row;
                 const bool valid = i < n_pts;
                 float x = 0.f, y = 0.f, z = 0.f, tt = 0.f, m = -1.f;
@@ -502,32 +596,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
                     x = sPos[i];
                     y = sPos[PS + i];
                     if (DIMS == 3) z = sPos[2 * PS + i];
-                    tt = sT[i - (i / np_) * np_];
+                    tt = sTrow[i];
                     m = sMarg[i];
                 }
                 float rx = 0.f, ry = 0.f, rz = 0.f, r2 = 0.f;
-                const uint32_t taddr = tbase + (uint32_t(32 * wq) << 16) + uint32_t((tile - t0) * (tp.ns_pad + tp.nm_pad));
-                for (int c16 = c16a; c16 < c16b; ++c16) {
-                    uint32_t v[16];
+                const uint32_t taddr = tbase + (uint32_t(32 * wq) << 16) + uint32_t(2 * wg + b) * tp.regw;
+                for (int c16 = c16a; c16 < c16b && ok; c16 += 2) {
+                    // two 16-column loads in flight, then one wait
+                    const bool two = c16 + 1 < c16b;
+                    uint32_t v[32];
                     __syncwarp();
-                    tc::tmem_ld16(taddr + uint32_t(16 * c16), v);
+                    tc::tmem_ld16(taddr + uint32_t(16 * (c16 - c16a)), *reinterpret_cast<uint32_t(*)[16]>(v));
+                    if (two) tc::tmem_ld16(taddr + uint32_t(16 * (c16 + 1 - c16a)), *reinterpret_cast<uint32_t(*)[16]>(v + 16));
                     tc::tmem_wait_ld();
-                    float qmin = __uint_as_float(v[0]);
+                    if (!two) {
 #pragma unroll
-                    for (int e = 1; e < 16; ++e) qmin = fminf(qmin, __uint_as_float(v[e]));
-                    if (valid && qmin < m) {
-#pragma unroll 1
-                        for (int e = 0; e < 16; ++e) {
-                            if (!(__uint_as_float(v[e]) < m)) continue;
+                        for (int e = 16; e < 32; ++e) v[e] = 0x7f800000u;  // +inf
+                    }
+                    float mn[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) mn[e] = fminf(__uint_as_float(v[e]), __uint_as_float(v[e + 16]));
+#pragma unroll
+                    for (int w2 = 8; w2 > 0; w2 >>= 1)
+#pragma unroll
+                        for (int e = 0; e < w2; ++e) mn[e] = fminf(mn[e], mn[e + w2]);
+                    if (mn[0] < m) {  // rare: candidates (padding columns hold +1e30, invalid rows m = -1)
+                        uint32_t mask = 0;
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) mask |= (__uint_as_float(v[e]) < m ? 1u : 0u) << e;
+                        while (mask) {
+                            const int e = __ffs(mask) - 1;
+                            mask &= mask - 1;
                             const int col = 16 * c16 + e;
-                            int j;
-                            if (col < tp.ns_pad) {
-                                if (col >= p.n_static) continue;
-                                j = col;
-                            } else {
-                                j = p.n_static + (col - tp.ns_pad);
-                                if (j >= p.n_obs) continue;
-                            }
+                            const int j = col < tp.ns_pad ? col : p.n_static + (col - tp.ns_pad);
                             exact_pair<DIMS>(sObs + size_t(j) * st, x, y, z, tt, fin, rx, ry, rz, r2);
                         }
                     }
@@ -542,12 +643,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
                         slot[0] = r2;
                     }
                 }
+                // the region is free again once all 128 threads have read it
+                tc::fence_before_sync();
+                asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory");
+                tc::fence_after_sync();
+                tile = ntile;
+                seg = nseg_;
+                nseg_ += 4;
+                while (nseg_ >= tp.nseg) {
+                    nseg_ -= tp.nseg;
+                    ++ntile;
+                }
             }
-            tc::fence_before_sync();
             __syncthreads();
-            tc::fence_after_sync();
-            if (s_abort) break;
         }
+        if (s_abort) break;
         if (ncol16 == 0) {  // no obstacles: empty residual slots
             for (int i = tid; i < n_pts; i += kTcThreads)
                 for (int ax = 0; ax < (fin ? 1 : DIMS); ++ax) sPart[ax * PS + i] = 0.f;
@@ -558,48 +668,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
         //      warp per (sample, axis)
         for (int u = warp; u < S_act * DIMS; u += kTcWarps) {
             const int s = u / DIMS, ax = u - s * DIMS;
-            const int ps0 = s * np_;
-            float acc[kMaxNv];
-#pragma unroll
-            for (int i = 0; i < kMaxNv; ++i) acc[i] = 0.f;
-            for (int t = lane; t < np_; t += 32) {
-                const int pp = ps0 + t;
-                float rp = sPart[ax * PS + pp];
-                for (int c = 1; c < C; ++c) rp += sPart[(c * DIMS + ax) * PS + pp];
-                if (p.use_bounds) rp += sRB[ax * PS + pp];
-                const float rv = sRV[ax * PS + pp], ra = sRA[ax * PS + pp];
-                const float *b0 = sBasis + size_t(t) * nv + col_lo;
-                const float *b1 = b0 + size_t(np_) * nv;
-                const float *b2 = b1 + size_t(np_) * nv;
-#pragma unroll
-                for (int i = 0; i < kMaxNv; ++i)
-                    if (i < ng) acc[i] = fmaf(b0[i], rp, fmaf(b1[i], rv, fmaf(b2[i], ra, acc[i])));
-            }
-#pragma unroll
-            for (int i = 0; i < kMaxNv; ++i)
-                if (i < ng)
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(kFull, acc[i], off);
-            float *lam = sLam + (s * DIMS + ax) * nv;
-            float *cc = sC + (s * DIMS + ax) * nfp;
-            const float *xi = sXi + (s * DIMS + ax) * nfp;
-            float g = 0.f, du = 0.f;
-            const int fl = lane - (kFree0 - col_lo);
-#pragma unroll
-            for (int i = 0; i < kMaxNv; ++i) {
-                if (i < ng) {
-                    const int ci = col_lo + i, fi = ci - kFree0;
-                    if (lane == i) g = acc[i];
-                    if (fi >= 0 && fi < nf) {
-                        const float ui = xi[fi] + (lam[ci] - rho * acc[i]) - rho * acc[i] - cc[fi];
-                        if (fl >= 0 && fl < nf) du = fmaf(sW[fl * nf + fi], ui, du);
-                    }
+            CdArgs ca{sPart + ax * PS + s * np_, sRB + ax * PS + s * np_, sRV + ax * PS + s * np_,
+                      sRA + ax * PS + s * np_, sBasis, sFb, sW, sLam + (s * DIMS + ax) * nv,
+                      sC + (s * DIMS + ax) * nfp, sXi + (s * DIMS + ax) * nfp, DIMS * PS, C, p.use_bounds, np_, nv,
+                      nf, nfp, fbs, rho};
+            if constexpr (NF > 0) {
+                if (!p.want_lambda) {
+                    cd_unit<NF, true>(ca, kFree0, NF, lane);
+                    continue;
                 }
             }
-            __syncwarp();
-            if (lane < ng) lam[col_lo + lane] -= rho * g;
-            if (fl >= 0 && fl < nf && lane < ng) cc[fl] += du;
-            __syncwarp();
+            cd_unit<kMaxNv, false>(ca, col_lo, ng, lane);
         }
         __syncthreads();
     }
@@ -634,7 +713,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
             if (p.lam_out) p.lam_out[gi] = double(sLam[(s * DIMS + ax) * nv + cl]);
         }
     }
-    if (s_abort) tc::mbar_wait_bounded(&s_mbar, parity ^ 1u, kTcWaitNs);  // work still in flight
+    if (s_abort && (tid & 127) == 0)  // work still in flight
+        for (int b = 0; b < 2; ++b) tc::mbar_wait_bounded(&s_mbar[2 * wg + b], (par >> b) & 1u, kTcWaitNs);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tbase, tp.ncols);
@@ -660,20 +740,20 @@ TcPlan tc_plan(const Shape &sh, int S)
     tp.kA = tp.nm_pad ? 32 : 16;
     tp.rows = S * sh.n_p;
     tp.tiles = (tp.rows + 127) / 128;
-    if (ntot > 512) return tp;
-    tp.tpw = ntot ? std::max(1, std::min(tp.tiles, 512 / ntot)) : tp.tiles;
-    tp.waves = (tp.tiles + tp.tpw - 1) / tp.tpw;
-    const int used = std::max(32, tp.tpw * ntot);
+    if (ntot > 1024) return tp;
+    // column segments of at most 64 columns; each warpgroup double-buffers
+    // one segment in tensor memory (8 regions of regw columns)
+    const int ncol16 = ntot / 16;
+    tp.nseg = std::max(1, (ncol16 + 3) / 4);
+    if (tp.nseg > kMaxSeg) return tp;
+    tp.regw = 16 * ((std::max(ncol16, 1) + tp.nseg - 1) / tp.nseg);
     tp.ncols = 32;
-    while (tp.ncols < uint32_t(used)) tp.ncols <<= 1;
-    // column segments so that each wave has at least one unit per warpgroup
-    const int per_wave = std::min(tp.tiles, tp.tpw);
-    tp.nseg = std::max(1, std::min(std::max(1, ntot / 16), (4 + per_wave - 1) / per_wave));
+    while (tp.ncols < uint32_t(8 * tp.regw)) tp.ncols <<= 1;
     const size_t fl = detail::smem_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, S, tp.nseg, sh.use_bounds).total *
                       sizeof(float);
     size_t o = up(fl, 16);
-    tp.off_marg = o;
-    o = up(o + sizeof(float) * tp.tiles * 128, 1024);
+    tp.off_marg = o;  // margins, then row times
+    o = up(o + 2 * sizeof(float) * tp.tiles * 128, 1024);
     tp.off_a = o;
     o = up(o + size_t(tp.tiles) * 128 * tp.kA * 2, 1024);
     tp.off_bs = o;
@@ -696,8 +776,10 @@ TcPlan tc_choose(const Shape &sh, int N, int n_sm, int *S_out)
         if (!tp.smem) continue;
         const int ctas = (N + S - 1) / S;
         const int waves = (ctas + n_sm - 1) / n_sm;
-        // per-CTA work ~ rows padded to tiles; mild preference for fewer rows
-        const double cost = double(waves) * (double(tp.tiles) * 128.0 + 64.0);
+        // per-CTA time ~ the longest warpgroup pipeline (units of regw
+        // columns x 128 rows) plus the per-point phases
+        const int units = tp.tiles * tp.nseg;
+        const double cost = double(waves) * (double((units + 3) / 4) * tp.regw + 0.5 * S * sh.n_p);
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
             best = tp;
