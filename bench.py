@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2309_08235_gb300 import replicas as R  # noqa: E402
+
 WORKLOAD = "clutter2d_fp32"
 METRIC = "projected sample-iters/s; solves/s & p99 latency vs plain GPU path, at oracle tol"
 UNIT = "sample-iters/s"
@@ -128,10 +130,7 @@ class ClockSampler:
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    return rank, world, local
+    return R.env()
 
 
 def cpu_oracle_rate(p, cem, n_samples, seed=0):
@@ -228,8 +227,7 @@ def run_ours(args):
     P.priest_profile_enable(ctx.h, 1)
     l0 = ctx.launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
+    R.barrier(dist)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for e0, e1 in evs:
@@ -239,20 +237,16 @@ def run_ours(args):
             e1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    R.barrier(dist)
     clocks = sampler.stop()
     P.priest_profile_enable(ctx.h, 0)
     launches = ctx.launches() - l0
     n_proj_launch, proj_ms = P.priest_profile_read(ctx.h)
     P.priest_sync(ctx.h)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = units * args.steps * world / (total_ms / 1e3)
+    # whole job: all ranks' units over the slowest rank's device time
+    value, t_max, _ = R.job_rate(units * args.steps, sum(step_ms) / 1e3, dist, dev)
+    total_ms = 1e3 * t_max
 
     # ---- roofline of the dominant kernel (the fused projection)
     avg_proj_ms = proj_ms / max(1, n_proj_launch)
@@ -279,18 +273,13 @@ def run_ours(args):
     for _ in range(2):
         P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
     e2e_steps = max(3, min(args.steps, 50))
-    if dist:
-        dist.barrier()
+    R.barrier(dist)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_rate, e2e_s, _ = R.job_rate(units * e2e_steps, time.perf_counter() - t0, dist, dev)
     obs_bytes = 8 * (p["n_obs"] * (2 * p["dims"] + 2))
-    e2e = {"value": units * e2e_steps * world / e2e_s, "unit": UNIT,
+    e2e = {"value": e2e_rate, "unit": UNIT,
            "h2d_bytes_per_step": int(z_np.nbytes + obs_bytes),
            "d2h_bytes_per_step": int(8 * (D + 4 + D)),
            "api": "priest_plan_z (host buffers, blocking)"}

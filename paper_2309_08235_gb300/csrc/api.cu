@@ -863,6 +863,138 @@ void free_batch(BatchPlan *b)
     delete b;
 }
 
+// Autotuner of the batched launch: per class of problem shape (dims,
+// degree, mask, n_p, obstacles rounded up to a multiple of 32, moving ones
+// present, bounds), every candidate tiling is timed on a representative
+// problem of the batch.  The trial launch is the batched kernel itself over
+// that problem's items, repeated until they fill the GPU twice, so the
+// measure is throughput (per-iteration marginal time: K = 10 minus K = 2).
+std::vector<int> batch_class(const Shape &sh, int dbl)
+{
+    return {-1, dbl, sh.dims, sh.nv, sh.nf, sh.bc_mask, sh.n_p, (sh.n_obs + 31) / 32, sh.n_obs > sh.n_static,
+            sh.use_bounds, std::min(sh.N, 16)};
+}
+
+template <typename Real>
+Tiling batch_tiling_for(priest_ctx *ctx, const Shape &sh)
+{
+    auto it = ctx->tuned.find(batch_class(sh, sizeof(Real) == 8));
+    if (it == ctx->tuned.end()) return batch_tiling<Real>(sh);
+    Tiling t = it->second;
+    t.S = std::max(1, std::min(t.S, sh.N));
+    t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
+    if (t.smem > size_t(227) * 1024) return batch_tiling<Real>(sh);
+    return t;
+}
+
+template <typename Real>
+priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
+                         const std::vector<SetupParams> &setups)
+{
+    std::vector<int> reps;  // one representative problem per untuned class
+    {
+        std::map<std::vector<int>, int> seen;
+        for (int i = 0; i < n; ++i) {
+            const std::vector<int> key = batch_class(probs[i]->sh, sizeof(Real) == 8);
+            if (ctx->tuned.count(key) || seen.count(key)) continue;
+            seen[key] = i;
+            reps.push_back(i);
+        }
+    }
+    if (reps.empty()) return PRIEST_OK;
+    cudaStream_t st = ctx->stream;
+    // tables, means and first sampling factors of every problem
+    void *dsetup = nullptr;
+    PRIEST_CUDA(ctx, cudaMalloc(&dsetup, sizeof(SetupParams) * n));
+    size_t smem_setup = 0;
+    for (int i = 0; i < n; ++i) smem_setup = std::max(smem_setup, setup_smem_bytes(probs[i]->sh));
+    cudaError_t e = cudaMemcpyAsync(dsetup, setups.data(), sizeof(SetupParams) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_setup_batch(static_cast<SetupParams *>(dsetup), n, smem_setup, st);
+    ctx->launches++;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dsetup);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "setup before tuning");
+    for (int i = 0; i < n; ++i) probs[i]->shape_ready = true;
+    const int fill = 2 * ctx->n_sm;
+    void *dbuf = nullptr;
+    size_t dcap = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int i : reps) {
+        priest_loaded *h = probs[i];
+        const Shape &sh = h->sh;
+        Tiling best = batch_tiling<Real>(sh);
+        float best_us = 1e30f;
+        for (const Tiling &t : batch_candidates<Real>(sh)) {
+            ProjParams<Real> p = proj_params<Real>(ctx, h, t);
+            p.N = sh.N;
+            p.mode = 1;
+            p.mu = h->mu;
+            p.Lc = h->L;
+            p.z = z[i];
+            p.xi_bar = h->xb;
+            p.r_out = h->r;
+            p.c1_out = h->c1;
+            std::vector<int2> it;
+            while (int(it.size()) < fill)
+                for (int s = 0; s < sh.N; s += t.S) it.push_back(make_int2(0, s));
+            const size_t need = 2 * sizeof(ProjParams<Real>) + sizeof(int2) * it.size() + 256;
+            if (need > dcap) {
+                if (dbuf) cudaFree(dbuf);
+                dbuf = nullptr;
+                dcap = 0;
+                if (cudaMalloc(&dbuf, need) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;
+                }
+                dcap = need;
+            }
+            ProjParams<Real> pk[2] = {p, p};
+            pk[0].K = 2;
+            pk[1].K = 10;
+            char *d = static_cast<char *>(dbuf);
+            int *cnt = reinterpret_cast<int *>(d);
+            ProjParams<Real> *dp = reinterpret_cast<ProjParams<Real> *>(d + 256);
+            int2 *di = reinterpret_cast<int2 *>(d + 256 + 2 * sizeof(ProjParams<Real>));
+            e = cudaMemcpyAsync(dp, pk, sizeof(pk), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(di, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice, st);
+            float ms[2] = {0.f, 0.f};
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                const int k = rep == 0 ? 0 : rep - 1;  // rep 0 warms up
+                e = cudaMemsetAsync(cnt, 0, sizeof(int), st);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)
+                    e = launch_project_batch<Real>(dp + k, di, int(it.size()), cnt, sh.dims, 4, 0, sh.nf, sh.nv, 0,
+                                                   t.smem, 0, st);
+                ctx->launches++;
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess && rep > 0) cudaEventElapsedTime(&ms[k], e0, e1);
+            }
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                e = cudaSuccess;
+                continue;
+            }
+            // marginal time per iteration per sample processed
+            const float us = 1e3f * (ms[1] - ms[0]) / 8.f / float(it.size() * t.S);
+            if (us < best_us) {
+                best_us = us;
+                best = t;
+            }
+        }
+        ctx->tuned[batch_class(sh, sizeof(Real) == 8)] = best;
+        if (getenv("PRIEST_AUTOTUNE_LOG"))
+            fprintf(stderr, "priest batch autotune: n_p=%d n_obs=%d -> S=%d C=%d ws=%d (%.4f us / sample-iteration)\n",
+                    sh.n_p, sh.n_obs, best.S, best.C, best.ws, best_us);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (dbuf) cudaFree(dbuf);
+    return PRIEST_OK;
+}
+
 template <typename Real>
 priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
                           double *const *out, BatchPlan *b)
@@ -875,6 +1007,16 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
     b->nf = s0.nf;
     b->nv = s0.nv;
     b->dbl = sizeof(Real) == 8;
+    if (ctx->cfg.autotune) {
+        std::vector<SetupParams> sps(n);
+        for (int i = 0; i < n; ++i) {
+            sps[i] = setup_params(ctx, probs[i], true, ctx->d_status);
+            sps[i].default_mu = 1;
+            sps[i].default_cov = 1;
+        }
+        const priest_status ts = tune_batch<Real>(ctx, n, probs, z, sps);
+        if (ts != PRIEST_OK) return ts;
+    }
     std::vector<ProjParams<Real>> params(size_t(L) * n);
     std::vector<SetupParams> setups(n), setups_ready(n);
     std::vector<CemArgs> cem(n);
@@ -884,7 +1026,7 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
         const Shape &sh = h->sh;
         if (sh.dims != s0.dims || sh.nv != s0.nv || sh.bc_mask != s0.bc_mask)
             return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
-        const Tiling t = batch_tiling<Real>(sh);
+        const Tiling t = batch_tiling_for<Real>(ctx, sh);
         if (t.smem == 0) return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
         b->smem_proj = std::max(b->smem_proj, t.smem);
         ProjParams<Real> p = proj_params<Real>(ctx, h, t);

@@ -240,6 +240,8 @@ std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm);
 // from the cost model.  smem == 0 signals a problem too large for one CTA.
 template <typename Real>
 Tiling batch_tiling(const Shape &sh);
+template <typename Real>
+std::vector<Tiling> batch_candidates(const Shape &sh);
 
 // One compiled kernel variant (explicitly instantiated in project_f32_*.cu /
 // project_f64.cu).

@@ -118,6 +118,33 @@ Tiling batch_tiling(const Shape &sh)
     return t;
 }
 
+// Candidates of the batched launch's autotuner: warp-group sizes and chunk
+// counts for the batched variant's CTA, within the shared-memory cap.
+template <typename Real>
+std::vector<Tiling> batch_candidates(const Shape &sh)
+{
+    std::vector<Tiling> out;
+    const int threads = sizeof(Real) == 8 ? 256 : 512;
+    for (int ws = 1; ws <= 4; ws *= 2) {
+        Tiling t;
+        t.R = 4;
+        t.threads = threads;
+        t.ws = ws;
+        t.S = std::max(1, std::min(sh.N, threads / (32 * ws)));
+        if (ws > 1) t.S = std::min(t.S, 15);
+        for (int C = 1; C <= std::min(4, std::max(1, sh.n_obs)); C *= 2) {
+            t.C = C;
+            int S = t.S;
+            while (S > 1 && project_smem_bytes<Real>(sh, S, C) > kSmemCap) S = std::max(1, S / 2);
+            Tiling u = t;
+            u.S = S;
+            u.smem = project_smem_bytes<Real>(sh, S, C);
+            if (u.smem <= kSmemCap) out.push_back(u);
+        }
+    }
+    return out;
+}
+
 template <typename Real>
 cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st)
 {
@@ -173,6 +200,8 @@ template std::vector<Tiling> tiling_candidates<float>(const Shape &, int, int);
 template std::vector<Tiling> tiling_candidates<double>(const Shape &, int, int);
 template Tiling batch_tiling<float>(const Shape &);
 template Tiling batch_tiling<double>(const Shape &);
+template std::vector<Tiling> batch_candidates<float>(const Shape &);
+template std::vector<Tiling> batch_candidates<double>(const Shape &);
 template cudaError_t launch_project<float>(const ProjParams<float> &, const Tiling &, cudaStream_t);
 template cudaError_t launch_project<double>(const ProjParams<double> &, const Tiling &, cudaStream_t);
 
