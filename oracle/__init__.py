@@ -94,6 +94,9 @@ def _load():
                                        C.c_uint64, _P, _P, _P, _P, _P, _PI]),
                 "orc_plan_warm": (C.c_int, [C.POINTER(_Problem), C.POINTER(_Cem), _P, _P, _P, _P,
                                             C.c_uint64, _P, _P, _P, _P, _P, _PI, _P]),
+                "orc_multi_default_means": (C.c_int, [C.POINTER(_Problem), C.c_int, C.c_double, _P]),
+                "orc_plan_multi": (C.c_int, [C.POINTER(_Problem), C.POINTER(_Cem), C.c_int, _P, _P, _P,
+                                             C.c_uint64, _P, _P, _PI, _P, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -340,3 +343,39 @@ def plan(p, cem, mu0=None, cov0=None, z=None, seed=None, lam0=None, want_lam=Fal
     if want_lam:
         out["lam"] = lam_out
     return out
+
+
+def multi_default_means(p, M, spread):
+    """D-PRIEST default means (M x D): the straight line bowed sideways."""
+    s, keep = _problem(p)
+    out = np.zeros((M, n_coeffs(p)))
+    _check(_load().orc_multi_default_means(C.byref(s), int(M), float(spread), _dptr(out)), "orc_multi_default_means")
+    return out
+
+
+def plan_multi(p, cem, M, mu0=None, cov0=None, z=None, seed=None):
+    """D-PRIEST (Sec. D-PRIEST): M distributions refined in parallel on one
+    stacked projection; returns the best over the M and each distribution's
+    best elite."""
+    s, keep = _problem(p)
+    c = _Cem()
+    for name, _ in _Cem._fields_:
+        setattr(c, name, type(getattr(c, name))(cem[name]))
+    D = n_coeffs(p)
+    mu0 = None if mu0 is None else _f64(mu0, (M, D))
+    cov0 = None if cov0 is None else _f64(cov0, (M, D, D))
+    z = None if z is None else _f64(z)
+    best = np.zeros(D)
+    bc = C.c_double()
+    bd = C.c_int()
+    db = np.zeros((M, D))
+    dr = np.zeros(M)
+    dc = np.zeros(M)
+    mu = np.zeros((M, D))
+    seed = int(p.get("seed", 0) if seed is None else seed)
+    rc = _load().orc_plan_multi(C.byref(s), C.byref(c), int(M), _dptr(mu0), _dptr(cov0), _dptr(z),
+                                C.c_uint64(seed & (2**64 - 1)), _dptr(best), C.byref(bc), C.byref(bd), _dptr(db),
+                                _dptr(dr), _dptr(dc), _dptr(mu))
+    _check(rc, "orc_plan_multi")
+    return {"best": best, "c_aug": bc.value, "dist": bd.value, "dist_best": db, "dist_r": dr, "dist_c_aug": dc,
+            "mu": mu}

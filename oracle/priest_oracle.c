@@ -910,3 +910,152 @@ int orc_plan_warm(const orc_problem *pr, const orc_cem *cem, const double *mu0, 
     free(eidx);
     return rc;
 }
+
+/* ----------------------------------------------------------------------- */
+/* D-PRIEST (Sec. D-PRIEST, Fig. fig_decentralized).                        */
+/* ----------------------------------------------------------------------- */
+
+/* Default means of the M distributions: the straight-line coefficients
+ * with every interior coefficient (k = 1 .. n-1) moved by
+ * (j - (M-1)/2) * spread along the unit normal of the start-goal line
+ * (2-D: the line rotated by +90 degrees; 3-D: the horizontal normal; x when
+ * that is undefined).  The trajectory then bows sideways by that amount
+ * times (1 - B_0 - B_n), zero at both ends. */
+int orc_multi_default_means(const orc_problem *pr, int M, double spread, double *mu)
+{
+    int D, nv, j, ax, k;
+    double d[3] = {0, 0, 0}, nrm[3] = {0, 0, 0}, h;
+    if (check_problem(pr) || M < 1) return -1;
+    nv = pr->degree + 1;
+    D = pr->dims * nv;
+    for (ax = 0; ax < pr->dims; ++ax) d[ax] = pr->bf[ax][0] - pr->b0[ax][0];
+    h = sqrt(d[0] * d[0] + d[1] * d[1]);
+    if (h > 1e-12) {
+        nrm[0] = -d[1] / h;
+        nrm[1] = d[0] / h;
+    } else {
+        nrm[0] = 1.0;
+    }
+    for (j = 0; j < M; ++j) {
+        const double off = ((double)j - 0.5 * (double)(M - 1)) * spread;
+        double *m = mu + (size_t)j * D;
+        orc_default_mean(pr, m);
+        for (ax = 0; ax < pr->dims; ++ax)
+            for (k = 1; k < pr->degree; ++k) m[ax * nv + k] += off * nrm[ax];
+    }
+    return 0;
+}
+
+/* D-PRIEST: M distributions (mu_j, Sigma_j), N_b / M samples each, stacked
+ * row-wise (rows j * N_b/M .. are distribution j's), one projection of all
+ * rows, then per distribution the residual / cost, ConstraintEliteSet of
+ * N_proj / M, EliteSet of N_elite / M and the refit; after L iterations the
+ * best elite of each distribution, and over them the lowest c_aug (ties:
+ * the lower j).  z: L x N_b x D (row j * N_b/M + i at iteration l) or NULL
+ * for the stream seeded by `seed`. */
+int orc_plan_multi(const orc_problem *pr, const orc_cem *cem, int M, const double *mu0, const double *cov0,
+                   const double *z, uint64_t seed, double *best, double *best_caug, int *best_dist,
+                   double *dist_best, double *dist_r, double *dist_caug, double *mu_out)
+{
+    int D, N, L, nj, npj, nej, l, i, j, k, q, rc = 0;
+    double *mu, *cov, *Lc, *Sh, *xi, *xb, *r, *c1, *caug, *zz = NULL, *el, *elc, *bcaug;
+    int *eidx, *bidx;
+    if (check_problem(pr) || !cem || M < 1) return -1;
+    N = cem->n_samples;
+    L = cem->cem_iters;
+    if (N <= 0 || N % M || L <= 0 || cem->proj_iters < 0) return -1;
+    nj = N / M;
+    npj = cem->n_proj / M > 0 ? cem->n_proj / M : 1;
+    nej = cem->n_elite / M > 0 ? cem->n_elite / M : 1;
+    if (npj > nj || nej > npj) return -1;
+    D = pr->dims * (pr->degree + 1);
+    mu = (double *)malloc(sizeof(double) * ((size_t)M * (D + 2 * D * D) + D * D + 2 * (size_t)N * D + 3 * N +
+                                            (size_t)nej * (D + 1) + M));
+    eidx = (int *)malloc(sizeof(int) * ((size_t)M * nej + M));
+    if (!mu || !eidx) return -2;
+    cov = mu + (size_t)M * D;
+    Lc = cov + (size_t)M * D * D;
+    Sh = Lc + (size_t)M * D * D;
+    xi = Sh + D * D;
+    xb = xi + (size_t)N * D;
+    r = xb + (size_t)N * D;
+    c1 = r + N;
+    caug = c1 + N;
+    el = caug + N;
+    elc = el + (size_t)nej * D;
+    bcaug = elc + nej;
+    bidx = eidx + (size_t)M * nej;
+    if (mu0)
+        for (i = 0; i < M * D; ++i) mu[i] = mu0[i];
+    else
+        orc_multi_default_means(pr, M, 2.0 * cem->init_std, mu);
+    for (j = 0; j < M; ++j)
+        for (i = 0; i < D * D; ++i)
+            cov[(size_t)j * D * D + i] = cov0 ? cov0[(size_t)j * D * D + i]
+                                              : ((i / D == i % D) ? cem->init_std * cem->init_std : 0.0);
+    if (!z) {
+        zz = (double *)malloc(sizeof(double) * (size_t)L * N * D);
+        orc_rng_normal(seed, (int64_t)L * N * D, zz);
+        z = zz;
+    }
+    for (l = 0; l < L && rc == 0; ++l) {
+        /* samples of every distribution, stacked row-wise */
+        for (j = 0; j < M && rc == 0; ++j) {
+            const double *cj = cov + (size_t)j * D * D;
+            double *Lj = Lc + (size_t)j * D * D, tr = 0.0, eps;
+            for (i = 0; i < D; ++i) tr += cj[i * D + i];
+            eps = cem->chol_eps * tr / (double)D;
+            for (i = 0; i < D * D; ++i) Sh[i] = cj[i];
+            for (i = 0; i < D; ++i) Sh[i * D + i] += eps;
+            rc = orc_cholesky(D, Sh, Lj);
+            for (i = 0; i < nj && rc == 0; ++i) {
+                const int row = j * nj + i;
+                const double *zi = z + ((size_t)l * N + row) * D;
+                for (k = 0; k < D; ++k) {
+                    double s = mu[(size_t)j * D + k];
+                    for (q = 0; q <= k; ++q) s += Lj[k * D + q] * zi[q];
+                    xi[(size_t)row * D + k] = s;
+                }
+            }
+        }
+        if (rc) break;
+        /* one projection of all rows */
+        rc = orc_project(pr, cem->proj_iters, N, xi, NULL, NULL, xb);
+        if (rc) break;
+        orc_residual_cost(pr, N, xb, r, c1);
+        for (i = 0; i < N; ++i) caug[i] = c1[i] + r[i];
+        /* per distribution: selections and refit */
+        for (j = 0; j < M && rc == 0; ++j) {
+            int *ej = eidx + (size_t)j * nej;
+            rc = orc_select(nj, r + (size_t)j * nj, caug + (size_t)j * nj, npj, nej, NULL, ej);
+            if (rc) break;
+            for (i = 0; i < nej; ++i) {
+                for (k = 0; k < D; ++k) el[(size_t)i * D + k] = xb[((size_t)j * nj + ej[i]) * D + k];
+                elc[i] = caug[(size_t)j * nj + ej[i]];
+            }
+            rc = orc_refit(D, nej, el, elc, cem->sigma_lr, cem->gamma, mu + (size_t)j * D, cov + (size_t)j * D * D);
+            bidx[j] = j * nj + ej[0];
+            bcaug[j] = caug[bidx[j]];
+        }
+    }
+    if (rc == 0) {
+        int jb = 0;
+        for (j = 1; j < M; ++j)
+            if (bcaug[j] < bcaug[jb]) jb = j;
+        for (k = 0; k < D; ++k) best[k] = xb[(size_t)bidx[jb] * D + k];
+        if (best_caug) *best_caug = bcaug[jb];
+        if (best_dist) *best_dist = jb;
+        for (j = 0; j < M; ++j) {
+            if (dist_best)
+                for (k = 0; k < D; ++k) dist_best[(size_t)j * D + k] = xb[(size_t)bidx[j] * D + k];
+            if (dist_r) dist_r[j] = r[bidx[j]];
+            if (dist_caug) dist_caug[j] = bcaug[j];
+        }
+        if (mu_out)
+            for (i = 0; i < M * D; ++i) mu_out[i] = mu[i];
+    }
+    free(zz);
+    free(mu);
+    free(eidx);
+    return rc;
+}

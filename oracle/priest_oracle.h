@@ -139,6 +139,16 @@ int orc_plan_warm(const orc_problem *pr, const orc_cem *cem, const double *mu0, 
                   const double *lam0, const double *z, uint64_t seed, double *best, double *best_r,
                   double *best_caug, double *mu_out, double *cov_out, int *elite_out, double *lam_out);
 
+/* D-PRIEST (Sec. D-PRIEST): M distributions, N_b / M samples each, stacked
+ * row-wise for one projection, selections (N_proj / M, N_elite / M) and
+ * refits per distribution, best of M by c_aug.  orc_multi_default_means
+ * gives the default means (the straight line bowed sideways by
+ * (j - (M-1)/2) spread). */
+int orc_multi_default_means(const orc_problem *pr, int M, double spread, double *mu);
+int orc_plan_multi(const orc_problem *pr, const orc_cem *cem, int M, const double *mu0, const double *cov0,
+                   const double *z, uint64_t seed, double *best, double *best_caug, int *best_dist,
+                   double *dist_best, double *dist_r, double *dist_caug, double *mu_out);
+
 #ifdef __cplusplus
 }
 #endif
