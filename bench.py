@@ -524,6 +524,47 @@ def run_serving(args):
     return 0
 
 
+def run_dpriest(args):
+    """D-PRIEST scaling (the paper's per-iteration time against the number
+    of distributions): the 2-D clutter scene with M distributions of a fixed
+    N_b / M = 1000 samples each, K = 100, L = 5, one stacked projection launch
+    per CEM iteration.  Reports per-iteration time and projected
+    sample-iters/s for each M.  Not the default bench line."""
+    import torch
+
+    from paper_2309_08235_gb300 import build as B
+    from paper_2309_08235_gb300 import priest as P
+    from paper_2309_08235_gb300 import workloads as W
+
+    B.build()
+    p, cem0 = W.workload("clutter2d_fp32")
+    K, L, nj = cem0["proj_iters"], cem0["cem_iters"], 1000
+    prec = P.PRIEST_MIXED_BF16 if args.precision == "mixed" else P.PRIEST_FP32
+    rows = []
+    for M in (1, 2, 4, 8):
+        cem = W.cem_settings(M * nj, K, L, n_elite=100 * M)
+        z = W.normals(3000 + M, (L, M * nj, 22))
+        with P.Context(p, cem, precision=prec) as ctx:
+            for _ in range(max(1, args.warmup)):
+                ctx.plan_multi(p, M, z=z)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                r = ctx.plan_multi(p, M, z=z)
+            dt = (time.perf_counter() - t0) / args.steps
+        rows.append({"M": M, "samples": M * nj, "ms_per_solve": 1e3 * dt, "ms_per_cem_iteration": 1e3 * dt / L,
+                     "sample_iters_per_s": M * nj * K * L / dt, "best_dist": r["dist"],
+                     "best_c_aug": r["best"]["c_aug"]})
+    line = {"metric": METRIC, "value": rows[-1]["sample_iters_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows[-1]["ms_per_solve"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "D-PRIEST sweep on the 2-D clutter scene: M distributions x 1000 samples, "
+                                   "K=100, L=5 (host draws, blocking priest_plan_multi)"},
+            "sweep": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -532,7 +573,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["clutter2d", "ellipsoid3d", "batched", "serving"], default="clutter2d",
+    ap.add_argument("--workload", choices=["clutter2d", "ellipsoid3d", "batched", "serving", "dpriest"],
+                    default="clutter2d",
                     help="clutter2d: the default bench line; batched: 256 uneven problems; serving: Poisson "
                          "request stream (both report only)")
     ap.add_argument("--batch-problems", type=int, default=256)
@@ -551,6 +593,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "dpriest":
+        return run_dpriest(args)
     return run_ours(args)
 
 

@@ -163,6 +163,29 @@ priest_status priest_plan(priest_ctx *ctx, const priest_problem *prob, const dou
 priest_status priest_plan_z(priest_ctx *ctx, const priest_problem *prob, const double *mu0,
                             const double *cov0, const double *z, priest_result *out);
 
+/* D-PRIEST (Sec. D-PRIEST, Fig. fig_decentralized): M Gaussian
+ * distributions refined in parallel.  Each draws N_b / M samples (N_b =
+ * prob's / the context's sample count, a multiple of M); the samples of all
+ * distributions are stacked row-wise (rows j N_b/M .. (j+1) N_b/M - 1 belong
+ * to distribution j) and projected in one launch; the selections
+ * (N_proj / M, N_elite / M, at least 1) and refits then run per
+ * distribution in one segmented launch each.  After L iterations *best is
+ * the lowest-c_aug member over the M distributions' best elites (ties: the
+ * lower j), *best_dist its distribution, per_dist[j] (M entries, or NULL)
+ * each distribution's best elite and final mean; best_index is the sample's
+ * index inside its distribution.
+ *   mu0: M x D means or NULL: the straight-line coefficients with the
+ *        interior coefficients moved by (j - (M-1)/2) * 2 init_std along the
+ *        start-goal line's normal (2-D: rotated +90 degrees; 3-D: horizontal);
+ *   cov0: M x D x D or NULL (init_std^2 I);
+ *   z: L x N_b x D standard normals (host) or NULL for the host stream of
+ *      prob->seed.
+ * Blocks until done.  Errors: PRIEST_ERR_INVALID (M < 1, N_b not a multiple
+ * of M, counts), PRIEST_ERR_NUMERIC, PRIEST_ERR_CUDA. */
+priest_status priest_plan_multi(priest_ctx *ctx, const priest_problem *prob, int M, const double *mu0,
+                                const double *cov0, const double *z, priest_result *best, int *best_dist,
+                                priest_result *per_dist);
+
 /* Serving (continuous batching).  priest_submit copies the problem, queues
  * it and returns a ticket at once.  A worker thread admits queued requests in
  * arrival order while their device buffers fit the budget (cfg.hbm_budget,

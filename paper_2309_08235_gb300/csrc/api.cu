@@ -249,6 +249,7 @@ ProjParams<Real> proj_params(const priest_ctx *ctx, const priest_loaded *h, cons
                                               : reinterpret_cast<const Real *>(h->tab32);
     p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
     p.cB = h->cB;
+    p.seg_len = h->seg_len;
     return p;
 }
 
@@ -1178,6 +1179,166 @@ priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
     return PRIEST_OK;
 }
 
+// D-PRIEST default means: the straight-line coefficients with every
+// interior coefficient moved by (j - (M-1)/2) spread along the unit normal of
+// the start-goal line (2-D: rotated by +90 degrees; 3-D: the horizontal
+// normal; x when undefined).
+void multi_default_means(const Shape &sh, int M, double spread, double *mu)
+{
+    const int nv = sh.nv, n = sh.degree, D = sh.D;
+    double d[3] = {0.0, 0.0, 0.0}, nrm[3] = {0.0, 0.0, 0.0};
+    for (int ax = 0; ax < sh.dims; ++ax) d[ax] = sh.bf[ax][0] - sh.b0[ax][0];
+    const double h = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+    if (h > 1e-12) {
+        nrm[0] = -d[1] / h;
+        nrm[1] = d[0] / h;
+    } else {
+        nrm[0] = 1.0;
+    }
+    for (int j = 0; j < M; ++j) {
+        const double off = (double(j) - 0.5 * double(M - 1)) * spread;
+        for (int ax = 0; ax < sh.dims; ++ax)
+            for (int k = 0; k < nv; ++k) {
+                double v = sh.b0[ax][0] + (sh.bf[ax][0] - sh.b0[ax][0]) * double(k) / double(n);
+                if (k >= 1 && k < n) v += off * nrm[ax];
+                mu[size_t(j) * D + ax * nv + k] = v;
+            }
+    }
+}
+
+priest_status plan_multi(priest_ctx *ctx, const priest_problem *pr, int M, const double *mu0, const double *cov0,
+                         const double *z_host, priest_result *best, int *best_dist, priest_result *per_dist)
+{
+    if (!ctx || !best || M < 1) return fail(ctx, PRIEST_ERR_INVALID, "NULL argument or M < 1");
+    Shape sh;
+    priest_status s = resolve(ctx, pr, -1, sh);
+    if (s != PRIEST_OK) return s;
+    const int N = sh.N, D = sh.D, L = ctx->cfg.cem_iters;
+    if (N % M) return fail(ctx, PRIEST_ERR_INVALID, "n_samples must be a multiple of M");
+    const int nj = N / M, npj = std::max(1, sh.n_proj / M), nej = std::max(1, sh.n_elite / M);
+    if (npj > nj || nej > npj) return fail(ctx, PRIEST_ERR_INVALID, "need n_elite / M <= n_proj / M <= n_samples / M");
+    priest_loaded *h = nullptr;
+    s = scratch_for(ctx, sh, pr, L, false, &h);
+    if (s != PRIEST_OK) return s;
+    // per-distribution state: mu, Sigma, L, mu', elites, result rows, refit counters, CEM arguments
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = round_up(o + bytes);
+        return at;
+    };
+    const size_t o_mu = take(sizeof(double) * M * D), o_cov = take(sizeof(double) * M * D * D),
+                 o_L = take(sizeof(double) * M * D * D), o_mn = take(sizeof(double) * M * D),
+                 o_el = take(sizeof(int) * M * nej), o_out = take(sizeof(double) * M * (D + 5)),
+                 o_cnt = take(sizeof(unsigned) * M), o_args = take(sizeof(CemArgs) * M);
+    char *blk = nullptr;
+    PRIEST_CUDA(ctx, cudaMalloc(reinterpret_cast<void **>(&blk), o));
+    struct Free {
+        char *p;
+        ~Free() { cudaFree(p); }
+    } guard{blk};
+    double *mu = reinterpret_cast<double *>(blk + o_mu), *cov = reinterpret_cast<double *>(blk + o_cov);
+    double *Lc = reinterpret_cast<double *>(blk + o_L), *mn = reinterpret_cast<double *>(blk + o_mn);
+    int *el = reinterpret_cast<int *>(blk + o_el);
+    double *out = reinterpret_cast<double *>(blk + o_out);
+    unsigned *cnt = reinterpret_cast<unsigned *>(blk + o_cnt);
+    CemArgs *args = reinterpret_cast<CemArgs *>(blk + o_args);
+    cudaStream_t st = ctx->stream;
+    // inputs: draws, means, covariances, argument blocks
+    const size_t nz = size_t(L) * N * D;
+    std::vector<double> zbuf, hmu(size_t(M) * D), hcov;
+    if (!z_host) {
+        zbuf.resize(nz);
+        gaussian_stream(pr->seed, int64_t(nz), zbuf.data());
+        z_host = zbuf.data();
+    }
+    if (mu0)
+        std::copy(mu0, mu0 + size_t(M) * D, hmu.begin());
+    else
+        multi_default_means(sh, M, 2.0 * ctx->cfg.init_std, hmu.data());
+    if (!cov0) {
+        hcov.assign(size_t(M) * D * D, 0.0);
+        for (int j = 0; j < M; ++j)
+            for (int i = 0; i < D; ++i) hcov[size_t(j) * D * D + size_t(i) * D + i] = ctx->cfg.init_std * ctx->cfg.init_std;
+        cov0 = hcov.data();
+    }
+    std::vector<CemArgs> ha(M);
+    for (int j = 0; j < M; ++j) {
+        CemArgs &a = ha[j];
+        std::memset(&a, 0, sizeof(a));
+        a.N = nj;
+        a.n_proj = npj;
+        a.n_elite = nej;
+        a.D = D;
+        a.r = h->r + size_t(j) * nj;
+        a.c1 = h->c1 + size_t(j) * nj;
+        a.xb = h->xb + size_t(j) * nj * D;
+        a.elite = el + size_t(j) * nej;
+        a.sigma = ctx->cfg.sigma_lr;
+        a.gamma = ctx->cfg.gamma;
+        a.chol_eps = ctx->cfg.chol_eps;
+        a.mu = mu + size_t(j) * D;
+        a.cov = cov + size_t(j) * D * D;
+        a.mu_new = mn + size_t(j) * D;
+        a.L = Lc + size_t(j) * D * D;
+        a.counter = cnt + j;
+        a.status = ctx->d_status;
+        a.best_out = out + size_t(j) * (D + 5);
+    }
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(h->z, z_host, nz * sizeof(double), cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(mu, hmu.data(), sizeof(double) * M * D, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(cov, cov0, sizeof(double) * M * D * D, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(args, ha.data(), sizeof(CemArgs) * M, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned) * M, st));
+    // a0: tables once, then the first sampling factor of each distribution
+    for (int j = 0; j < M; ++j) {
+        SetupParams sp = setup_params(ctx, h, true, ctx->d_status);
+        sp.mu = mu + size_t(j) * D;
+        sp.cov = cov + size_t(j) * D * D;
+        sp.L = Lc + size_t(j) * D * D;
+        sp.default_mu = 0;
+        sp.default_cov = 0;
+        sp.shape_ready = (j > 0 || h->shape_ready) ? 1 : 0;
+        cudaError_t e = launch_setup(sp, st);
+        ctx->launches++;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "setup kernel");
+    }
+    h->shape_ready = true;
+    // per CEM iteration: one projection of all distributions' rows, then
+    // selections and refits per distribution (segmented)
+    double *mu_keep = h->mu, *L_keep = h->L;
+    h->mu = mu;
+    h->L = Lc;
+    h->seg_len = nj;
+    const size_t sel_smem = select_smem_bytes(nj), ref_smem = refit_smem_bytes(D, nej);
+    for (int l = 0; l < L && s == PRIEST_OK; ++l) {
+        s = enqueue_project_any(ctx, h, N, 1, nullptr, h->z + size_t(l) * N * D, nullptr, nullptr, h->xb, h->r,
+                                h->c1, st);
+        if (s != PRIEST_OK) break;
+        cudaError_t e = launch_select_batch(args, M, sel_smem, st);
+        if (e == cudaSuccess) e = launch_refit_batch(args, M, D, ref_smem, st);
+        ctx->launches += 2;
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "segmented selection / refit");
+    }
+    h->mu = mu_keep;
+    h->L = L_keep;
+    h->seg_len = 0;
+    if (s != PRIEST_OK) return s;
+    // best of M (ties: the lower j)
+    std::vector<double> ho(size_t(M) * (D + 5)), hm(size_t(M) * D);
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(ho.data(), out, sizeof(double) * ho.size(), cudaMemcpyDeviceToHost, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(hm.data(), mu, sizeof(double) * hm.size(), cudaMemcpyDeviceToHost, st));
+    s = check_status(ctx, ctx->d_status, st);
+    if (s != PRIEST_OK) return s;
+    int jb = 0;
+    for (int j = 1; j < M; ++j)
+        if (ho[size_t(j) * (D + 5) + D + 2] < ho[size_t(jb) * (D + 5) + D + 2]) jb = j;
+    for (int j = 0; j < M && per_dist; ++j) fill_result(sh, &ho[size_t(j) * (D + 5)], &hm[size_t(j) * D], &per_dist[j]);
+    fill_result(sh, &ho[size_t(jb) * (D + 5)], &hm[size_t(jb) * D], best);
+    if (best_dist) *best_dist = jb;
+    return PRIEST_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1357,6 +1518,13 @@ priest_status priest_plan_plain(priest_ctx *ctx, const priest_problem *pr, const
                                 const double *z, priest_result *out)
 {
     return plan_host(ctx, pr, mu0, cov0, z, out, true);
+}
+
+priest_status priest_plan_multi(priest_ctx *ctx, const priest_problem *pr, int M, const double *mu0,
+                                const double *cov0, const double *z, priest_result *best, int *best_dist,
+                                priest_result *per_dist)
+{
+    return plan_multi(ctx, pr, M, mu0, cov0, z, best, best_dist, per_dist);
 }
 
 priest_status priest_plan_plain_device(priest_ctx *ctx, priest_loaded *h, const double *z_dev, double *out_dev)

@@ -33,6 +33,7 @@ struct priest_loaded {
     double *lam = nullptr;  // N x D
     bool default_mu = true, default_cov = true;
     bool shape_ready = false;  // basis and Gram blocks computed for this shape
+    int seg_len = 0;           // D-PRIEST: samples per distribution while mu / L hold M of them
 };
 
 namespace priest {

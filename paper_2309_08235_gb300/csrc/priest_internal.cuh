@@ -114,6 +114,8 @@ template <typename Real>
 struct ProjParams {
     int dims, nv, nf, n_p, n_obs, n_static, use_bounds;
     int N, K, S, C, WS, want_lambda, mode;  // mode 0: xi_in given; 1: xi = mu + L z; WS warps per sample
+    int seg_len;                            // mode 1: samples per distribution (mu, Lc hold one per
+                                            // segment of seg_len rows; 0 = a single distribution)
     Real rho, vmax, amax, smin[3], smax[3];
     const Real *tab;
     TableLayout lay;

@@ -302,9 +302,10 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
         if (p.mode == 0) {
             x = p.xi_in[gi];
         } else {
-            const double *Lrow = p.Lc + size_t(d) * D;
+            const size_t seg = p.seg_len > 0 ? size_t((s0 + s) / p.seg_len) : 0;  // D-PRIEST distribution
+            const double *Lrow = p.Lc + (seg * D + d) * D;
             const double *zi = p.z + size_t(s0 + s) * D;
-            x = p.mu[d];
+            x = p.mu[seg * D + d];
             for (int k = 0; k <= d; ++k) x = fma(Lrow[k], zi[k], x);
         }
         const int f = col - kFree0;

@@ -34,7 +34,7 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
            "priest_project_noalloc", "priest_plan_batch", "priest_wait", "priest_serve_stats_get",
            "priest_rng_normal_device", "priest_plan_plain", "priest_plan_plain_device",
-           "priest_project_plain", "priest_tc_selftest"]
+           "priest_project_plain", "priest_tc_selftest", "priest_plan_multi"]
 
 
 class PriestError(RuntimeError):
@@ -126,6 +126,8 @@ def lib():
             "priest_plan_plain_device": (C.c_int, [vp, vp, vp, vp]),
             "priest_project_plain": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P, _P, _P]),
             "priest_tc_selftest": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, vp, vp]),
+            "priest_plan_multi": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P,
+                                            C.POINTER(priest_result), C.POINTER(C.c_int), C.POINTER(priest_result)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -286,6 +288,18 @@ def priest_tc_selftest(a_bf16, b_bf16, swap=0):
     return st, d
 
 
+def priest_plan_multi(ctx, prob, M, mu0, cov0, z):
+    """D-PRIEST; returns (best result, best distribution, list of M per-distribution results)."""
+    best = priest_result()
+    per = (priest_result * int(M))()
+    bd = C.c_int()
+    zp = None if z is None else np.ascontiguousarray(z, dtype=np.float64)
+    _check(ctx, lib().priest_plan_multi(ctx, C.byref(prob), int(M), _arr(mu0)[1], _arr(cov0)[1],
+                                        None if zp is None else zp.ctypes.data_as(_P), C.byref(best), C.byref(bd),
+                                        per))
+    return best, bd.value, [per[j] for j in range(int(M))]
+
+
 def priest_submit(ctx, prob):
     t = C.c_uint64()
     _check(ctx, lib().priest_submit(ctx, C.byref(prob), C.byref(t)))
@@ -438,6 +452,13 @@ class Context:
         z = None if z is None else np.ascontiguousarray(np.asarray(z, dtype=np.float64))
         priest_plan_plain(self.h, prob, mu0, cov0, z, res)
         return result_dict(res)
+
+    def plan_multi(self, p, M, z=None, mu0=None, cov0=None, cem=None):
+        """D-PRIEST over M distributions: dict with the best result, its
+        distribution and every distribution's result."""
+        prob, keep = make_problem(p, cem, per_problem_shape=cem is not None)
+        best, bd, per = priest_plan_multi(self.h, prob, M, mu0, cov0, z)
+        return {"best": result_dict(best), "dist": bd, "per_dist": [result_dict(r) for r in per]}
 
     def plan(self, p, z=None, mu0=None, cov0=None, cem=None):
         """Alg. 1 on p; with cem given, the problem's own sizes (dims, n_p,

@@ -1,0 +1,75 @@
+"""GPU parity of D-PRIEST (priest_plan_multi: M distributions on one stacked
+projection launch, segmented selections and refits, best of M) against the
+FP64 oracle's orc_plan_multi, with the same standard-normal draws."""
+import numpy as np
+import pytest
+
+from gpu_common import TOL_FP32, TOL_FP64, rel_err, scale_of, scene
+from paper_2309_08235_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2309_08235_gb300 import build, priest
+
+    build.build()
+    return priest
+
+
+@pytest.mark.parametrize("dims,M,nj", [(2, 3, 40), (3, 2, 33), (2, 5, 16)])
+def test_fp64_dpriest_matches_oracle(P, oracle, dims, M, nj):
+    p = scene(dims=dims, n_obs=12, n_dyn=2, n_p=36)
+    D = dims * 11
+    cem = W.cem_settings(M * nj, 12, 3, n_proj=M * (nj * 3 // 4), n_elite=M * 4, dims=dims)
+    z = W.normals(41 + M, (3, M * nj, D))
+    want = oracle.plan_multi(p, cem, M, z=z)
+    with P.Context(p, cem, precision=P.PRIEST_FP64_CHECK) as ctx:
+        got = ctx.plan_multi(p, M, z=z)
+    s = scale_of(p)
+    assert got["dist"] == want["dist"]
+    assert rel_err(got["best"]["best"], want["best"], s) < TOL_FP64
+    for j in range(M):
+        assert rel_err(got["per_dist"][j]["best"], want["dist_best"][j], s) < TOL_FP64
+        assert rel_err(got["per_dist"][j]["mu"], want["mu"][j], s) < TOL_FP64
+        assert abs(got["per_dist"][j]["c_aug"] - want["dist_c_aug"][j]) < TOL_FP64 * max(1.0, want["dist_c_aug"][j])
+
+
+def test_one_distribution_equals_plan(P, oracle):
+    p = scene(dims=2, n_obs=10, n_p=30)
+    cem = W.cem_settings(64, 10, 2, dims=2)
+    z = W.normals(5, (2, 64, 22))
+    with P.Context(p, cem, precision=P.PRIEST_FP64_CHECK) as ctx:
+        a = ctx.plan_multi(p, 1, z=z)
+        b = ctx.plan(p, z=z)
+    assert a["dist"] == 0
+    np.testing.assert_array_equal(a["best"]["best"], b["best"])
+
+
+def test_fp32_dpriest_close_to_oracle(P, oracle):
+    p = scene(dims=2, n_obs=16, n_dyn=2, n_p=40)
+    M, nj = 4, 64
+    cem = W.cem_settings(M * nj, 20, 3, dims=2)
+    z = W.normals(44, (3, M * nj, 22))
+    want = oracle.plan_multi(p, cem, M, z=z)
+    for prec in (P.PRIEST_FP32, P.PRIEST_MIXED_BF16):
+        with P.Context(p, cem, precision=prec) as ctx:
+            got = ctx.plan_multi(p, M, z=z)
+        best = got["best"]
+        # every distribution's answer re-evaluated by the oracle
+        for j, res in enumerate(got["per_dist"]):
+            r_o, c1_o = oracle.residual_cost(p, res["best"][None])
+            assert abs(res["r"] - r_o[0]) < TOL_FP32 * max(1.0, r_o[0])
+            assert abs(res["c_aug"] - (r_o[0] + c1_o[0])) < TOL_FP32 * max(1.0, c1_o[0])
+        assert best["c_aug"] == min(r["c_aug"] for r in got["per_dist"])
+        assert best["c_aug"] <= want["c_aug"] * (1 + 1e-3) + 1e-3
+
+
+def test_dpriest_rejects_uneven_split(P, oracle):
+    p = scene(dims=2, n_obs=4, n_p=20)
+    cem = W.cem_settings(30, 4, 1, dims=2)
+    with P.Context(p, cem) as ctx:
+        with pytest.raises(P.PriestError) as e:
+            ctx.plan_multi(p, 4)
+        assert e.value.status == P.PRIEST_ERR_INVALID
