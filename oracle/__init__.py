@@ -53,6 +53,8 @@ class _Problem(C.Structure):
         ("n_obs", C.c_int),
         ("center", C.POINTER(C.c_double)), ("vel", C.POINTER(C.c_double)),
         ("semi", C.POINTER(C.c_double)),
+        ("cost_kind", C.c_int), ("w_acc", C.c_double), ("w_curv", C.c_double), ("w_path", C.c_double),
+        ("curv_eps", C.c_double),
     ]
 
 
@@ -164,6 +166,11 @@ def _problem(p):
     s.center = _dptr(center)
     s.vel = _dptr(vel)
     s.semi = _dptr(semi)
+    s.cost_kind = int(p.get("cost_kind", 0))
+    s.w_acc = float(p.get("w_acc", 1.0))
+    s.w_curv = float(p.get("w_curv", 0.0))
+    s.w_path = float(p.get("w_path", 0.0))
+    s.curv_eps = float(p.get("curv_eps", 0.1))
     return s, (center, vel, semi)
 
 

@@ -556,6 +556,52 @@ int orc_project(const orc_problem *pr, int K, int N, const double *xi, const dou
 /* Residual and cost (Alg. 1 lines "compute the residuals", "evaluate").    */
 /* ----------------------------------------------------------------------- */
 
+/* c_1 contribution of one time stamp.  Point-to-point benchmark: |a|^2.
+ * BARN-style cost (acceleration, curvature and path-following penalties):
+ * w_acc |a|^2 + w_curv kappa^2 + w_path d^2, kappa = |v x a| /
+ * (|v|^2 + eps^2)^(3/2) (the curvature of the path, regularised where the
+ * robot is at rest), d = distance from the point to its projection on the
+ * straight start-goal segment (clamped to the segment). */
+static double point_cost(const orc_problem *pr, int dims, const double *p, const double *v, const double *a)
+{
+    double a2 = 0.0, v2 = 0.0, c2, den, s[3] = {0, 0, 0}, u[3] = {0, 0, 0}, len = 0.0, lam = 0.0, d2 = 0.0;
+    int ax;
+    for (ax = 0; ax < dims; ++ax) {
+        a2 += a[ax] * a[ax];
+        v2 += v[ax] * v[ax];
+    }
+    if (pr->cost_kind != 1) return a2;
+    /* |v x a|^2 */
+    if (dims == 2) {
+        const double cz = v[0] * a[1] - v[1] * a[0];
+        c2 = cz * cz;
+    } else {
+        const double cx = v[1] * a[2] - v[2] * a[1], cy = v[2] * a[0] - v[0] * a[2], cz = v[0] * a[1] - v[1] * a[0];
+        c2 = cx * cx + cy * cy + cz * cz;
+    }
+    den = v2 + pr->curv_eps * pr->curv_eps;
+    /* kappa^2 = |v x a|^2 / den^3 */
+    for (ax = 0; ax < dims; ++ax) {
+        s[ax] = pr->b0[ax][0];
+        u[ax] = pr->bf[ax][0] - pr->b0[ax][0];
+        len += u[ax] * u[ax];
+    }
+    len = sqrt(len);
+    if (len > 0.0) {
+        for (ax = 0; ax < dims; ++ax) {
+            u[ax] /= len;
+            lam += (p[ax] - s[ax]) * u[ax];
+        }
+        if (lam < 0.0) lam = 0.0;
+        if (lam > len) lam = len;
+    }
+    for (ax = 0; ax < dims; ++ax) {
+        const double e = p[ax] - s[ax] - lam * u[ax];
+        d2 += e * e;
+    }
+    return pr->w_acc * a2 + pr->w_curv * c2 / (den * den * den) + pr->w_path * d2;
+}
+
 int orc_residual_cost(const orc_problem *pr, int N, const double *xi_bar, double *r, double *c1)
 {
     orc_ws w;
@@ -610,7 +656,7 @@ int orc_residual_cost(const orc_problem *pr, int N, const double *xi_bar, double
                     if (x < pr->smin[ax]) r2 += (pr->smin[ax] - x) * (pr->smin[ax] - x);
                     if (x > pr->smax[ax]) r2 += (x - pr->smax[ax]) * (x - pr->smax[ax]);
                 }
-            cost += a2;
+            cost += point_cost(pr, w.dims, pos + 3 * t, vel + 3 * t, acc + 3 * t);
         }
         if (r) r[i] = sqrt(r2);
         if (c1) c1[i] = cost;

@@ -44,6 +44,13 @@ typedef struct {
     double bf[3][3];     /* [axis][q] final values */
     int n_obs;
     const double *center, *vel, *semi;
+    /* c_1: 0 = sum of squared accelerations (point-to-point benchmark);
+     * 1 = BARN-style (Sec. Baselines and Benchmarks): per time stamp
+     * w_acc |a|^2 + w_curv kappa^2 + w_path d^2 with the curvature
+     * kappa = |v x a| / (|v|^2 + curv_eps^2)^(3/2) and d the distance from the
+     * point to the start-goal segment */
+    int cost_kind;
+    double w_acc, w_curv, w_path, curv_eps;
 } orc_problem;
 
 typedef struct {

@@ -139,6 +139,60 @@ def scene_ellipsoids_3d(seed=2, n_obs=200, n_p=150, horizon=10.0, vmax=2.0, amax
     return problem(3, n_p, horizon, start, goal, c, None, np.stack([a, b], 1), vmax, amax, seed)
 
 
+# BARN-style cost weights (chosen: the paper names the three terms but gives
+# no weights) and the curvature regularisation of rest states.
+BARN_WEIGHTS = {"w_acc": 1.0, "w_curv": 0.1, "w_path": 1.0, "curv_eps": 0.1}
+
+
+def with_barn_cost(p, **w):
+    """The problem with the BARN-style cost c_1: acceleration, curvature and
+    path-following (distance to the straight start-goal segment) penalties."""
+    q = dict(p)
+    q["cost_kind"] = 1
+    q.update(BARN_WEIGHTS)
+    q.update(w)
+    return q
+
+
+def scene_dynamic_2d(seed=3, n_obs=10, n_p=100, horizon=10.0):
+    """Dynamic environment: n_obs circles r = 0.3 m moving at 0.1 m/s against
+    the robot's direction, start (0, 0) -> goal (8, 0), v_max 1 m/s, a_max
+    1 m/s^2 (chosen), centres U[2, 7] x U[-1.5, 1.5], BARN-style cost."""
+    rng = np.random.default_rng(seed)
+    r = np.full(n_obs, 0.3)
+    start, goal = np.array([0.0, 0.0]), np.array([8.0, 0.0])
+    c = np.stack([rng.uniform(2.0, 7.0, n_obs), rng.uniform(-1.5, 1.5, n_obs)], 1)
+    v = np.tile(np.array([[-0.1, 0.0]]), (n_obs, 1))
+    p = problem(2, n_p, horizon, start, goal, c, v, np.stack([r, r], 1), 1.0, 1.0, seed)
+    return with_barn_cost(p)
+
+
+def scene_p2p_2d(seed=4, n_obs=50, n_p=100, horizon=8.0):
+    """Point-to-point 2-D: n_obs circles r = 0.4 m, centres U[1, 19]^2 kept
+    clear of start (0, 0) and goal (20, 20); v_max 5, a_max 5 (chosen)."""
+    rng = np.random.default_rng(seed)
+    r = np.full(n_obs, 0.4)
+    start, goal = np.array([0.0, 0.0]), np.array([20.0, 20.0])
+    c = _place(rng, n_obs, 1.0, 19.0, r, [start, goal], 2)
+    return problem(2, n_p, horizon, start, goal, c, None, np.stack([r, r], 1), 5.0, 5.0, seed)
+
+
+def scene_p2p_3d(seed=5, n_obs=25, n_p=100, horizon=6.0):
+    """Point-to-point 3-D room of 7 x 7 x 3 m: n_obs spheres r = 0.68 m,
+    start (0.5, 0.5, 0.5) -> goal (6.5, 6.5, 2.5); v_max 3, a_max 3 (chosen)."""
+    rng = np.random.default_rng(seed)
+    r = np.full(n_obs, 0.68)
+    start, goal = np.array([0.5, 0.5, 0.5]), np.array([6.5, 6.5, 2.5])
+    c = _place(rng, n_obs, [0.0, 0.0, 0.0], [7.0, 7.0, 3.0], r, [start, goal], 3)
+    return problem(3, n_p, horizon, start, goal, c, None, np.stack([r, r], 1), 3.0, 3.0, seed)
+
+
+# The paper's solver settings for its benchmarks: N = 13 CEM iterations,
+# N_b = 110 samples, N_proj = 80, N_elite = 20 (projection iterations not
+# given: 50 chosen).
+PAPER_CEM = {"n_samples": 110, "cem_iters": 13, "n_proj": 80, "n_elite": 20, "proj_iters": 50}
+
+
 def batched_problems(n_problems=256, seed0=100):
     """Uneven 2-D problems: n_obs log-uniform in [10, 400], N in
     {256, 512, 1024, 2048}, n_p in {60, 100, 150}, horizon = 0.08 s * n_p,
@@ -251,4 +305,14 @@ def workload(name: str):
     if name == "ellipsoid3d_mixed":
         p = scene_ellipsoids_3d()
         return p, cem_settings(2000, 100, 4, n_elite=200, dims=3)
+    c = PAPER_CEM
+    if name == "p2p2d":
+        return scene_p2p_2d(), cem_settings(c["n_samples"], c["proj_iters"], c["cem_iters"], c["n_proj"],
+                                            c["n_elite"], dims=2)
+    if name == "p2p3d":
+        return scene_p2p_3d(), cem_settings(c["n_samples"], c["proj_iters"], c["cem_iters"], c["n_proj"],
+                                            c["n_elite"], dims=3)
+    if name == "dynamic2d":
+        return scene_dynamic_2d(), cem_settings(c["n_samples"], c["proj_iters"], c["cem_iters"], c["n_proj"],
+                                                c["n_elite"], dims=2)
     raise KeyError(name)
