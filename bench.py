@@ -42,12 +42,18 @@ FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 
 
-WORKLOADS = {"clutter2d": "clutter2d_fp32", "ellipsoid3d": "ellipsoid3d_mixed"}
+WORKLOADS = {"clutter2d": "clutter2d_fp32", "ellipsoid3d": "ellipsoid3d_mixed", "p2p2d": "p2p2d", "p2p3d": "p2p3d",
+             "dynamic2d": "dynamic2d"}
 
 
-def workload_desc(p, cem, precision="fp32"):
+def workload_desc(p, cem, precision="fp32", name="clutter2d"):
     prec = ("FP32 projection" if precision == "fp32" else
             "FP32 projection, pair tests selected by a split-BF16 tensor-core product")
+    if name in ("p2p2d", "p2p3d", "dynamic2d"):
+        return (f"{name}: {p['n_obs']} obstacles, dims {p['dims']}, N={cem['n_samples']} samples, n_p={p['n_p']}, "
+                f"K={cem['proj_iters']}, L={cem['cem_iters']} CEM iters (the paper's N_b = 110, N = 13), "
+                f"{cem['n_elite']} elites, cost {'BARN-style' if p.get('cost_kind', 0) == 1 else 'sum |acc|^2'}, "
+                f"{prec}")
     if p["dims"] == 3:
         return (f"3-D point-to-point: {p['n_obs']} static ellipsoids in 20x20x8 m, N={cem['n_samples']} samples, "
                 f"n_p={p['n_p']}, degree {p['degree']}, K={cem['proj_iters']} projection iters, "
@@ -311,7 +317,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(p, cem, args.precision),
+            "config": {"workload": workload_desc(p, cem, args.precision, args.workload),
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "units_per_step": units},
@@ -573,7 +579,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["clutter2d", "ellipsoid3d", "batched", "serving", "dpriest"],
+    ap.add_argument("--workload", choices=["clutter2d", "ellipsoid3d", "p2p2d", "p2p3d", "dynamic2d", "batched",
+                                           "serving", "dpriest"],
                     default="clutter2d",
                     help="clutter2d: the default bench line; batched: 256 uneven problems; serving: Poisson "
                          "request stream (both report only)")

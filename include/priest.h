@@ -112,6 +112,14 @@ typedef struct {
     /* per-problem overrides; 0 keeps the context default */
     int dims, n_p, n_samples, n_proj, n_elite;
     double horizon, vmax, amax;
+    /* c_1 of Alg. 1: 0 = sum over time stamps of |acc|^2 (point-to-point
+     * benchmark); 1 = BARN-style cost (Sec. Baselines and Benchmarks): per
+     * time stamp w_acc |a|^2 + w_curv kappa^2 + w_path d^2, kappa = |v x a| /
+     * (|v|^2 + curv_eps^2)^(3/2), d = distance from the point to the
+     * straight start-goal segment.  Weights finite and >= 0, curv_eps > 0
+     * (used only with cost_kind 1). */
+    int cost_kind;
+    double w_acc, w_curv, w_path, curv_eps;
 } priest_problem;
 
 /* Result of one solve. */

@@ -111,6 +111,16 @@ priest_status resolve(const priest_config &c, const priest_problem *pr, int n_ov
                 return fail(PRIEST_ERR_INVALID, "obstacle velocity is not finite");
         }
     }
+    sh.cost_kind = pr->cost_kind;
+    sh.w_acc = pr->w_acc;
+    sh.w_curv = pr->w_curv;
+    sh.w_path = pr->w_path;
+    sh.curv_eps = pr->curv_eps;
+    if (sh.cost_kind != 0 && sh.cost_kind != 1) return fail(PRIEST_ERR_INVALID, "cost_kind must be 0 or 1");
+    if (sh.cost_kind == 1 &&
+        (!(sh.w_acc >= 0) || !(sh.w_curv >= 0) || !(sh.w_path >= 0) || !std::isfinite(sh.w_acc) ||
+         !std::isfinite(sh.w_curv) || !std::isfinite(sh.w_path) || !(sh.curv_eps > 0) || !std::isfinite(sh.curv_eps)))
+        return fail(PRIEST_ERR_INVALID, "cost weights must be finite and >= 0, curv_eps > 0");
     sh.nf = sh.nv - kFree0 - final_fixed(sh.bc_mask);
     sh.D = sh.dims * sh.nv;
     sh.N = n_override >= 0 ? n_override : (pr->n_samples ? pr->n_samples : c.n_samples);
@@ -250,6 +260,7 @@ ProjParams<Real> proj_params(const priest_ctx *ctx, const priest_loaded *h, cons
     p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
     p.cB = h->cB;
     p.seg_len = h->seg_len;
+    p.cost = make_cost<Real>(sh);
     return p;
 }
 
@@ -775,6 +786,7 @@ PlainParams plain_params(priest_ctx *ctx, const priest_loaded *h, int N, float *
     p.tab = h->tab32;
     p.lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
     p.cB = h->cB;
+    p.cost = make_cost<float>(sh);
     plain_carve(p, work);
     return p;
 }

@@ -82,6 +82,15 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
             if (!fin(pr->center[j * sh.dims + ax]) || (pr->vel && !fin(pr->vel[j * sh.dims + ax])))
                 return PRIEST_ERR_INVALID;
     }
+    sh.cost_kind = pr->cost_kind;
+    sh.w_acc = pr->w_acc;
+    sh.w_curv = pr->w_curv;
+    sh.w_path = pr->w_path;
+    sh.curv_eps = pr->curv_eps;
+    if ((sh.cost_kind != 0 && sh.cost_kind != 1) ||
+        (sh.cost_kind == 1 && (!(sh.w_acc >= 0) || !(sh.w_curv >= 0) || !(sh.w_path >= 0) || !fin(sh.w_acc) ||
+                               !fin(sh.w_curv) || !fin(sh.w_path) || !(sh.curv_eps > 0) || !fin(sh.curv_eps))))
+        return PRIEST_ERR_INVALID;
     sh.nf = sh.nv - kFree0 - final_fixed(sh.bc_mask);
     sh.D = sh.dims * sh.nv;
     sh.N = n;
@@ -176,6 +185,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         p.cB = sp.cB;
         p.xi_in = xi_dev; p.lam_in = lambda_dev; p.lam_out = lambda_dev; p.want_lambda = lambda_dev != nullptr;
         p.xi_bar = xi_bar_dev; p.r_out = resid_dev; p.c1_out = cost_dev;
+        p.cost = make_cost<float>(sh);
         if (launch_project<float>(p, t, st) != cudaSuccess) return PRIEST_ERR_CUDA;
     } else {
         const Tiling t = choose_tiling<double>(sh, n, n_sm);
@@ -192,6 +202,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         p.cB = sp.cB;
         p.xi_in = xi_dev; p.lam_in = lambda_dev; p.lam_out = lambda_dev; p.want_lambda = lambda_dev != nullptr;
         p.xi_bar = xi_bar_dev; p.r_out = resid_dev; p.c1_out = cost_dev;
+        p.cost = make_cost<double>(sh);
         if (launch_project<double>(p, t, st) != cudaSuccess) return PRIEST_ERR_CUDA;
     }
     // ---- wait, then report the setup kernel's status word

@@ -185,7 +185,13 @@ __global__ void __launch_bounds__(kPlainThreads) plain_resid_kernel(const PlainP
                     r = fmaf(h, h, fmaf(l, l, r));
                 }
             set_el(rq, i, r);
-            set_el(a2o, i, a2);
+            float vv[3] = {0.f, 0.f, 0.f}, aa[3] = {0.f, 0.f, 0.f};
+            for (int ax = 0; ax < dims; ++ax) {
+                vv[ax] = el(V[ax], i);
+                aa[ax] = el(A[ax], i);
+            }
+            set_el(a2o, i, dims == 2 ? point_cost<float, 2>(p.cost, x, vv, aa, a2)
+                                     : point_cost<float, 3>(p.cost, x, vv, aa, a2));
         }
     }
     if (!fin) {

@@ -33,7 +33,70 @@ struct Shape {
     double smin[3], smax[3];
     double b0[3][3], bf[3][3];
     int N, n_proj, n_elite, D;
+    int cost_kind;                          // c_1: 0 = sum |a|^2; 1 = BARN-style
+    double w_acc, w_curv, w_path, curv_eps;
 };
+
+// c_1 of the final pass (Alg. 1 cost): the point-to-point benchmark's
+// squared acceleration, or the BARN-style cost w_acc |a|^2 + w_curv kappa^2 +
+// w_path d^2 with kappa = |v x a| / (|v|^2 + eps^2)^(3/2) and d the distance
+// to the straight start-goal segment (s, unit u, length len; positions in
+// the origin-shifted frame of the tables).
+template <typename Real>
+struct CostParams {
+    int kind;
+    Real w_acc, w_curv, w_path, eps2;
+    Real s[3], u[3], len;
+};
+
+template <typename Real>
+inline CostParams<Real> make_cost(const Shape &sh)
+{
+    CostParams<Real> c;
+    c.kind = sh.cost_kind;
+    c.w_acc = Real(sh.w_acc);
+    c.w_curv = Real(sh.w_curv);
+    c.w_path = Real(sh.w_path);
+    c.eps2 = Real(sh.curv_eps * sh.curv_eps);
+    double u[3] = {0.0, 0.0, 0.0}, len = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double org = ax < sh.dims ? 0.5 * (sh.b0[ax][0] + sh.bf[ax][0]) : 0.0;
+        c.s[ax] = Real(ax < sh.dims ? sh.b0[ax][0] - org : 0.0);
+        u[ax] = ax < sh.dims ? sh.bf[ax][0] - sh.b0[ax][0] : 0.0;
+        len += u[ax] * u[ax];
+    }
+    len = len > 0.0 ? __builtin_sqrt(len) : 0.0;
+    for (int ax = 0; ax < 3; ++ax) c.u[ax] = Real(len > 0.0 ? u[ax] / len : 0.0);
+    c.len = Real(len);
+    return c;
+}
+
+template <typename Real, int DIMS>
+__host__ __device__ __forceinline__ Real point_cost(const CostParams<Real> &c, const Real *p, const Real *v,
+                                                    const Real *a, Real a2)
+{
+    if (c.kind != 1) return a2;
+    Real v2 = Real(0), c2, lam = Real(0), d2 = Real(0);
+    for (int ax = 0; ax < DIMS; ++ax) v2 += v[ax] * v[ax];
+    if (DIMS == 2) {
+        const Real cz = v[0] * a[1] - v[1] * a[0];
+        c2 = cz * cz;
+    } else {
+        const Real cx = v[1] * a[DIMS - 1] - v[DIMS - 1] * a[1], cy = v[DIMS - 1] * a[0] - v[0] * a[DIMS - 1],
+                   cz = v[0] * a[1] - v[1] * a[0];
+        c2 = cx * cx + cy * cy + cz * cz;
+    }
+    const Real den = v2 + c.eps2;
+    if (c.len > Real(0)) {
+        for (int ax = 0; ax < DIMS; ++ax) lam += (p[ax] - c.s[ax]) * c.u[ax];
+        lam = lam < Real(0) ? Real(0) : (lam > c.len ? c.len : lam);
+    }
+    for (int ax = 0; ax < DIMS; ++ax) {
+        const Real e = p[ax] - c.s[ax] - lam * c.u[ax];
+        d2 += e * e;
+    }
+    return c.w_acc * a2 + c.w_curv * c2 / (den * den * den) + c.w_path * d2;
+}
 
 // Number of coefficients fixed at the final time by the Bernstein end-point
 // conditions (mask 0, 1, 3, 7 -> 0, 1, 2, 3).
@@ -116,6 +179,7 @@ struct ProjParams {
     int N, K, S, C, WS, want_lambda, mode;  // mode 0: xi_in given; 1: xi = mu + L z; WS warps per sample
     int seg_len;                            // mode 1: samples per distribution (mu, Lc hold one per
                                             // segment of seg_len rows; 0 = a single distribution)
+    CostParams<Real> cost;
     Real rho, vmax, amax, smin[3], smax[3];
     const Real *tab;
     TableLayout lay;
@@ -196,6 +260,7 @@ struct GaussJob {
 struct PlainParams {
     int dims, nv, nf, n_p, np4, n_obs, use_bounds, N, K, mode;  // mode 0: xi_in given; 1: xi = mu + L z
     float rho, vmax, amax, smin[3], smax[3];
+    CostParams<float> cost;
     const float *tab;
     TableLayout lay;
     const double *cB;

@@ -427,7 +427,7 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
                     }
                 }
                 sRV[pt] = rq;
-                sRA[pt] = a2;
+                sRA[pt] = point_cost<Real, DIMS>(p.cost, pos, vel, acc, a2);
             }
         }
         group_sync(bar, GT);

@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) project_tc_kernel(const TcParam
                     }
                 }
                 sRV[i] = rq;
-                sRA[i] = a2;
+                sRA[i] = point_cost<float, DIMS>(p.cost, pos, vel, acc, a2);
             }
             if (ncol16 > 0) {
                 write_features<DIMS>(sA, i, tp.kA, pos[0], pos[1], DIMS == 3 ? pos[DIMS - 1] : 0.f, sT[t]);

@@ -61,6 +61,8 @@ class priest_problem(C.Structure):
         ("bc_final_mask", C.c_int), ("seed", C.c_uint64), ("robot_id", C.c_int64),
         ("dims", C.c_int), ("n_p", C.c_int), ("n_samples", C.c_int), ("n_proj", C.c_int),
         ("n_elite", C.c_int), ("horizon", C.c_double), ("vmax", C.c_double), ("amax", C.c_double),
+        ("cost_kind", C.c_int), ("w_acc", C.c_double), ("w_curv", C.c_double), ("w_path", C.c_double),
+        ("curv_eps", C.c_double),
     ]
 
 
@@ -201,6 +203,11 @@ def make_problem(p, cem=None, robot_id=-1, seed=None, per_problem_shape=False):
     s.bc_final_mask = int(p.get("bc_final_mask", 7))
     s.seed = int(p.get("seed", 0) if seed is None else seed) & (2**64 - 1)
     s.robot_id = int(robot_id)
+    s.cost_kind = int(p.get("cost_kind", 0))
+    s.w_acc = float(p.get("w_acc", 1.0))
+    s.w_curv = float(p.get("w_curv", 0.0))
+    s.w_path = float(p.get("w_path", 0.0))
+    s.curv_eps = float(p.get("curv_eps", 0.1))
     if per_problem_shape:
         s.dims = dims
         s.n_p = int(p["n_p"])
