@@ -537,6 +537,10 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
             if (rep > 0) t_k[rep - 1] = ms;
         }
         const float ms = ok ? (t_k[1] - t_k[0]) / float(k_hi - k_lo) : 1e30f;
+        if (const char *lv = getenv("PRIEST_AUTOTUNE_LOG"))
+            if (atoi(lv) >= 2)
+                fprintf(stderr, "priest autotune candidate: S=%d C=%d R=%d threads=%d ws=%d smem=%zu -> %.2f us / iteration\n",
+                        t.S, t.C, t.R, t.threads, t.ws, t.smem, 1e3f * ms);
         if (ms < best_ms) {
             best_ms = ms;
             best = t;

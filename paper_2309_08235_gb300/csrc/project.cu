@@ -17,7 +17,8 @@ struct Variant {
 template <typename Real>
 const std::vector<Variant> &variants()
 {
-    static const std::vector<Variant> f32 = {{2, 4, 512}, {2, 8, 512}, {2, 4, 1024}, {3, 4, 256}, {3, 4, 512}};
+    static const std::vector<Variant> f32 = {{2, 4, 512}, {2, 5, 512}, {2, 8, 512}, {2, 5, 1024},
+                                             {3, 4, 512}, {3, 5, 256}, {3, 5, 512}};
     static const std::vector<Variant> f64 = {{2, 4, 256}, {3, 4, 256}};
     return sizeof(Real) == 8 ? f64 : f32;
 }
@@ -30,7 +31,18 @@ constexpr size_t kSmemCap = 227 * 1024;
 template <typename Real>
 size_t project_smem_bytes(const Shape &sh, int S, int C)
 {
-    return detail::smem_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, S, C, sh.use_bounds).total * sizeof(Real);
+    size_t total = detail::smem_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, S, C, sh.use_bounds).total;
+    if (sizeof(Real) == 4) total = detail::pair_layout(sh.dims, sh.n_obs, sh.n_static, C, total).total;
+    return total * sizeof(Real);
+}
+
+// Lane groups of one sample's obstacle loop: R points per item, spaced by the
+// group count (FP32); blocks of 32 lanes x R points (FP64).
+template <typename Real>
+int lane_groups(int n_p, int R)
+{
+    if (sizeof(Real) == 4) return (n_p + R - 1) / R;
+    return ((n_p + 32 * R - 1) / (32 * R)) * 32;
 }
 
 // Samples per CTA for a given group size: enough that the grid covers the SMs
@@ -51,15 +63,15 @@ template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm)
 {
     Tiling t;
-    t.R = 4;
-    t.threads = sizeof(Real) == 8 ? 256 : (sh.dims == 2 ? 1024 : 512);
+    t.R = sizeof(Real) == 8 ? 4 : 5;
+    t.threads = sizeof(Real) == 8 ? 256 : 512;
     const int S0 = std::max(1, (n_samples + n_sm - 1) / n_sm);
     t.ws = 1;
     while (t.ws < 8 && S0 * 32 * (2 * t.ws) <= t.threads && S0 <= 15) t.ws *= 2;
     int S = samples_per_cta(n_samples, n_sm, t.threads, t.ws);
     while (S > 1 && project_smem_bytes<Real>(sh, S, 1) > kSmemCap) S = std::max(1, S * 3 / 4);
-    const int nblk32 = ((sh.n_p + 32 * t.R - 1) / (32 * t.R)) * 32;
-    int C = std::max(1, (32 * t.ws) / nblk32);
+    const int ng = lane_groups<Real>(sh.n_p, t.R);
+    int C = std::max(1, (32 * t.ws) / ng);
     C = std::min(C, std::max(1, std::min(16, sh.n_obs)));
     while (C > 1 && project_smem_bytes<Real>(sh, S, C) > kSmemCap) --C;
     t.S = S;
@@ -80,12 +92,12 @@ std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm)
         for (int ws = 1; ws <= 8 && 32 * ws <= v.threads; ws *= 2) {
             int S = samples_per_cta(n_samples, n_sm, v.threads, ws);
             while (S > 1 && project_smem_bytes<Real>(sh, S, 1) > kSmemCap) S = std::max(1, S * 3 / 4);
-            const int nblk32 = ((sh.n_p + 32 * v.R - 1) / (32 * v.R)) * 32;
+            const int ng = lane_groups<Real>(sh.n_p, v.R);
             const int cmax = std::max(1, std::min(16, sh.n_obs));
             for (int C = 1; C <= cmax; ++C) {
                 const size_t smem = project_smem_bytes<Real>(sh, S, C);
                 if (smem > kSmemCap) break;
-                const int rounds = (nblk32 * C + 32 * ws - 1) / (32 * ws);
+                const int rounds = (ng * C + 32 * ws - 1) / (32 * ws);
                 if (rounds > 2) break;
                 Tiling t;
                 t.S = S;
@@ -105,13 +117,13 @@ template <typename Real>
 Tiling batch_tiling(const Shape &sh)
 {
     Tiling t;
-    t.R = 4;
+    t.R = sizeof(Real) == 8 ? 4 : 5;
     t.threads = sizeof(Real) == 8 ? 256 : 512;
     t.ws = (sh.dims == 2 && sizeof(Real) == 4) ? 2 : 1;
     t.S = std::max(1, std::min(sh.N, t.threads / (32 * t.ws)));
     if (t.ws > 1) t.S = std::min(t.S, 15);
-    const int nblk32 = ((sh.n_p + 32 * t.R - 1) / (32 * t.R)) * 32;
-    t.C = std::max(1, std::min(std::min(16, std::max(1, sh.n_obs)), (32 * t.ws) / nblk32));
+    const int ng = lane_groups<Real>(sh.n_p, t.R);
+    t.C = std::max(1, std::min(std::min(16, std::max(1, sh.n_obs)), (32 * t.ws) / ng));
     while (t.S > 1 && project_smem_bytes<Real>(sh, t.S, t.C) > kSmemCap) t.S = std::max(1, t.S / 2);
     t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
     if (t.smem > kSmemCap) t.smem = 0;
@@ -127,7 +139,7 @@ std::vector<Tiling> batch_candidates(const Shape &sh)
     const int threads = sizeof(Real) == 8 ? 256 : 512;
     for (int ws = 1; ws <= 4; ws *= 2) {
         Tiling t;
-        t.R = 4;
+        t.R = sizeof(Real) == 8 ? 4 : 5;
         t.threads = threads;
         t.ws = ws;
         t.S = std::max(1, std::min(sh.N, threads / (32 * ws)));
@@ -153,18 +165,23 @@ cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStrea
         if (p.dims == 2) return launch_variant<Real, 2, 4, 256>(p, t, st);
         return launch_variant<Real, 3, 4, 256>(p, t, st);
     } else {
+        if (t.S * 32 * t.ws > t.threads) return cudaErrorInvalidValue;
         if (p.dims == 2) {
             if (t.R == 4 && t.threads == 512) return launch_variant<Real, 2, 4, 512>(p, t, st);
+            if (t.R == 5 && t.threads == 512) return launch_variant<Real, 2, 5, 512>(p, t, st);
             if (t.R == 8 && t.threads == 512) return launch_variant<Real, 2, 8, 512>(p, t, st);
-            return launch_variant<Real, 2, 4, 1024>(p, t, st);
+            if (t.R == 5 && t.threads == 1024) return launch_variant<Real, 2, 5, 1024>(p, t, st);
+            return cudaErrorInvalidValue;  // not a compiled variant
         }
-        if (t.threads == 256) return launch_variant<Real, 3, 4, 256>(p, t, st);
-        return launch_variant<Real, 3, 4, 512>(p, t, st);
+        if (t.R == 4 && t.threads == 512) return launch_variant<Real, 3, 4, 512>(p, t, st);
+        if (t.R == 5 && t.threads == 256) return launch_variant<Real, 3, 5, 256>(p, t, st);
+        if (t.R == 5 && t.threads == 512) return launch_variant<Real, 3, 5, 512>(p, t, st);
+        return cudaErrorInvalidValue;
     }
 }
 
 // Batched launches use one variant per precision and dimension: 2-D
-// (R = 4, 512 threads), 3-D (R = 4, 512 threads), FP64 (R = 4, 256 threads).
+// (R = 5, 512 threads), 3-D (R = 5, 512 threads), FP64 (R = 4, 256 threads).
 template <typename Real>
 cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 *items_dev, int n_items,
                                  int *counter_dev, int dims, int R, int threads, int nf, int nv, int want_lambda,
@@ -181,9 +198,9 @@ cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 
                                                      want_lambda, smem, grid, st);
     } else {
         if (dims == 2)
-            return launch_variant_batch<Real, 2, 4, 512>(params_dev, items_dev, n_items, counter_dev, nf, nv,
+            return launch_variant_batch<Real, 2, 5, 512>(params_dev, items_dev, n_items, counter_dev, nf, nv,
                                                          want_lambda, smem, grid, st);
-        return launch_variant_batch<Real, 3, 4, 512>(params_dev, items_dev, n_items, counter_dev, nf, nv,
+        return launch_variant_batch<Real, 3, 5, 512>(params_dev, items_dev, n_items, counter_dev, nf, nv,
                                                      want_lambda, smem, grid, st);
     }
 }

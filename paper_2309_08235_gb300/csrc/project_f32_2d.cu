@@ -3,18 +3,10 @@
 
 namespace priest {
 
-template cudaError_t launch_variant<float, 2, 4, 512>(const ProjParams<float> &, const Tiling &,
-                                                         cudaStream_t);
-template cudaError_t launch_variant<float, 2, 8, 512>(const ProjParams<float> &, const Tiling &,
-                                                         cudaStream_t);
-template cudaError_t launch_variant<float, 2, 4, 1024>(const ProjParams<float> &, const Tiling &,
-                                                         cudaStream_t);
+template cudaError_t launch_variant<float, 2, 4, 512>(const ProjParams<float> &, const Tiling &, cudaStream_t);
+template cudaError_t launch_variant<float, 2, 5, 512>(const ProjParams<float> &, const Tiling &, cudaStream_t);
 
-template cudaError_t launch_variant_batch<float, 2, 4, 512>(const ProjParams<float> *, const int2 *, int, int *,
-                                                              int, int, int, size_t, int, cudaStream_t);
-template cudaError_t launch_variant_batch<float, 2, 8, 512>(const ProjParams<float> *, const int2 *, int, int *,
-                                                              int, int, int, size_t, int, cudaStream_t);
-template cudaError_t launch_variant_batch<float, 2, 4, 1024>(const ProjParams<float> *, const int2 *, int, int *,
+template cudaError_t launch_variant_batch<float, 2, 5, 512>(const ProjParams<float> *, const int2 *, int, int *,
                                                               int, int, int, size_t, int, cudaStream_t);
 
 }  // namespace priest

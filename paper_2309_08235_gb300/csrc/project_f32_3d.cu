@@ -3,14 +3,11 @@
 
 namespace priest {
 
-template cudaError_t launch_variant<float, 3, 4, 256>(const ProjParams<float> &, const Tiling &,
-                                                         cudaStream_t);
-template cudaError_t launch_variant<float, 3, 4, 512>(const ProjParams<float> &, const Tiling &,
-                                                         cudaStream_t);
+template cudaError_t launch_variant<float, 3, 4, 512>(const ProjParams<float> &, const Tiling &, cudaStream_t);
+template cudaError_t launch_variant<float, 3, 5, 256>(const ProjParams<float> &, const Tiling &, cudaStream_t);
+template cudaError_t launch_variant<float, 3, 5, 512>(const ProjParams<float> &, const Tiling &, cudaStream_t);
 
-template cudaError_t launch_variant_batch<float, 3, 4, 256>(const ProjParams<float> *, const int2 *, int, int *,
-                                                              int, int, int, size_t, int, cudaStream_t);
-template cudaError_t launch_variant_batch<float, 3, 4, 512>(const ProjParams<float> *, const int2 *, int, int *,
+template cudaError_t launch_variant_batch<float, 3, 5, 512>(const ProjParams<float> *, const int2 *, int, int *,
                                                               int, int, int, size_t, int, cudaStream_t);
 
 }  // namespace priest

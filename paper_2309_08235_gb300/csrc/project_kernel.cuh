@@ -71,6 +71,52 @@ __host__ __device__ inline SmemLayout smem_layout(int dims, int nv, int nf, int 
     return L;
 }
 
+// FP32 pair records of the packed obstacle loop, placed after the main layout
+// (FP32 kernels only).  Obstacles are taken two at a time so one f32x2 FMA
+// evaluates a point against both; every obstacle chunk holds the same number
+// of pairs (short chunks are padded with records that never test positive),
+// so all lanes of a warp run the same trip counts.
+//   static pair (2-D, 8 floats):  {m2x_j, m2x_j', m2y_j, m2y_j'} {nthr_j, nthr_j', 0, 0}
+//   static pair (3-D, 12 floats): {m2x, m2x', m2y, m2y'} {m2z, m2z', kap, kap'} {nthr, nthr', 0, 0}
+//   moving pair (2-D, 12 floats): {ia, ia', nox, nox'} {noy, noy', nvx, nvx'} {nvy, nvy', 0, 0}
+//   moving pair (3-D, 16 floats): {ia, ia', ib, ib'} {nox, nox', noy, noy'} {noz, noz', nvx, nvx'}
+//                                 {nvy, nvy', nvz, nvz'}
+// with m2 = -2 o, nthr = -thr of the pre-filter, (ia, ib) = 1 / (a, b), no = -o / (a, b),
+// nv = -v / (a, b) (the obstacle records' fields).
+struct PairLayout {
+    int pcs, pcm;      // static / moving pairs per chunk
+    size_t st, mv;     // offsets (Real units) of the static / moving pair records
+    size_t total;
+};
+
+__host__ __device__ inline int pair_rec_static(int dims) { return dims == 2 ? 8 : 12; }
+__host__ __device__ inline int pair_rec_moving(int dims) { return dims == 2 ? 12 : 16; }
+
+__host__ __device__ inline PairLayout pair_layout(int dims, int n_obs, int n_static, int C, size_t base)
+{
+    PairLayout P;
+    const int n_mov = n_obs - n_static;
+    P.pcs = (n_static + 2 * C - 1) / (2 * C);
+    P.pcm = (n_mov + 2 * C - 1) / (2 * C);
+    P.st = base;
+    size_t o = align8(base + size_t(C) * P.pcs * pair_rec_static(dims));
+    P.mv = o;
+    o = align8(o + size_t(C) * P.pcm * pair_rec_moving(dims));
+    P.total = o;
+    return P;
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Three-input minimum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
@@ -240,6 +286,206 @@ __device__ __forceinline__ void moving_obstacle(const Real *o, const Real (&px)[
     }
 }
 
+// ---- packed FP32 obstacle loop ---------------------------------------------
+// One item = R points of one sample (time stamps g, g + G, ..., G = ceil(n_p / R))
+// against one obstacle chunk.  Each point is held twice in a float2 so one
+// f32x2 FMA evaluates it against an obstacle pair; a running three-input
+// minimum per point over a batch of pairs and one warp vote per batch find
+// the (rare) candidates, which are then recomputed with the same operations
+// and tested exactly.
+
+// Exact test of static obstacle j against one point (scalar coordinates),
+// from the obstacle record, and its residual contribution.
+template <int DIMS>
+__device__ __forceinline__ void exact_static_f32(const float *sObs, int j, float x, float y, float z, bool fin,
+                                                 float *slot, int PS)
+{
+    constexpr int ST = DIMS == 2 ? 12 : 16;
+    const float *o = sObs + size_t(j) * ST;
+    float ia, nox, noy, noz = 0.f, ib = 0.f, a, b = 0.f, d0, d1;
+    if constexpr (DIMS == 2) {
+        a = o[3];
+        ld4(o + 4, ia, nox, noy, d0);
+    } else {
+        ld4(o + 4, d0, a, b, d1);
+        ld4(o + 8, ia, nox, noy, noz);
+        ib = o[12];
+    }
+    const float dx = fmaf(x, ia, nox), dy = fmaf(y, ia, noy);
+    const float dz = (DIMS == 3) ? fmaf(z, ib, noz) : 0.f;
+    const float q = (DIMS == 3) ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
+    if (q < 1.f) active_pair<float, DIMS>(dx, dy, dz, q, a, b, fin, slot, PS);
+}
+
+// Pre-filter values of one static pair record against one point: the
+// expanded test without |p|^2, to be compared with -|p|^2.
+template <int DIMS>
+__device__ __forceinline__ float2 static_value(const float *q, float2 xd, float2 yd, float2 zd, float2 zzd)
+{
+    const float4 A = *reinterpret_cast<const float4 *>(q);
+    const float4 B = *reinterpret_cast<const float4 *>(q + 4);
+    if constexpr (DIMS == 2) {
+        return ffma2(xd, make_float2(A.x, A.y), ffma2(yd, make_float2(A.z, A.w), make_float2(B.x, B.y)));
+    } else {
+        const float4 Cc = *reinterpret_cast<const float4 *>(q + 8);
+        return ffma2(xd, make_float2(A.x, A.y),
+                     ffma2(yd, make_float2(A.z, A.w),
+                           ffma2(zd, make_float2(B.x, B.y), ffma2(zzd, make_float2(B.z, B.w), make_float2(Cc.x, Cc.y)))));
+    }
+}
+
+// Scaled offsets and squared scaled distance of one moving pair record
+// against one point at its time stamp.
+template <int DIMS>
+__device__ __forceinline__ float2 moving_value(const float *q, float2 xd, float2 yd, float2 zd, float2 td, float2 &dx,
+                                               float2 &dy, float2 &dz)
+{
+    const float4 A = *reinterpret_cast<const float4 *>(q);
+    const float4 B = *reinterpret_cast<const float4 *>(q + 4);
+    const float4 Cc = *reinterpret_cast<const float4 *>(q + 8);
+    if constexpr (DIMS == 2) {
+        const float2 ia = make_float2(A.x, A.y);
+        dx = ffma2(xd, ia, ffma2(td, make_float2(B.z, B.w), make_float2(A.z, A.w)));
+        dy = ffma2(yd, ia, ffma2(td, make_float2(Cc.x, Cc.y), make_float2(B.x, B.y)));
+        dz = make_float2(0.f, 0.f);
+        return ffma2(dx, dx, fmul2(dy, dy));
+    } else {
+        const float4 Dd = *reinterpret_cast<const float4 *>(q + 12);
+        const float2 ia = make_float2(A.x, A.y), ib = make_float2(A.z, A.w);
+        dx = ffma2(xd, ia, ffma2(td, make_float2(Cc.z, Cc.w), make_float2(B.x, B.y)));
+        dy = ffma2(yd, ia, ffma2(td, make_float2(Dd.x, Dd.y), make_float2(B.z, B.w)));
+        dz = ffma2(zd, ib, ffma2(td, make_float2(Dd.z, Dd.w), make_float2(Cc.x, Cc.y)));
+        return ffma2(dx, dx, ffma2(dy, dy, fmul2(dz, dz)));
+    }
+}
+
+template <int DIMS, int R>
+struct PackedPoints {
+    float2 x[R], y[R], z[R], zz[R], t[R];
+    float npq[R];  // -(x^2 + y^2)
+};
+
+// Static pairs [k0, k0 + nb) of a chunk whose first obstacle is j0: the
+// candidates of the flagged points, tested exactly in obstacle order.
+template <int DIMS, int R>
+__device__ __forceinline__ void static_rescan(const float *rec, const float *sObs, int k0, int nb, int j0,
+                                              const PackedPoints<DIMS, R> &P, const float (&m)[R], bool fin,
+                                              float *slot0, int G, int PS)
+{
+    constexpr int RS = DIMS == 2 ? 8 : 12;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (m[r] < P.npq[r]) {
+            for (int b = k0; b < k0 + nb; ++b) {
+                const float2 v = static_value<DIMS>(rec + size_t(b) * RS, P.x[r], P.y[r], P.z[r], P.zz[r]);
+                if (v.x < P.npq[r])
+                    exact_static_f32<DIMS>(sObs, j0 + 2 * b, P.x[r].x, P.y[r].x, P.z[r].x, fin, slot0 + G * r, PS);
+                if (v.y < P.npq[r])
+                    exact_static_f32<DIMS>(sObs, j0 + 2 * b + 1, P.x[r].x, P.y[r].x, P.z[r].x, fin, slot0 + G * r,
+                                           PS);
+            }
+        }
+    }
+}
+
+template <int DIMS, int R>
+__device__ __forceinline__ void moving_rescan(const float *rec, const float *sObs, int k0, int nb, int j0,
+                                              const PackedPoints<DIMS, R> &P, const float (&m)[R], bool fin,
+                                              float *slot0, int G, int PS)
+{
+    constexpr int RM = DIMS == 2 ? 12 : 16;
+    constexpr int ST = DIMS == 2 ? 12 : 16;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (m[r] < 1.f) {
+            for (int b = k0; b < k0 + nb; ++b) {
+                float2 dx, dy, dz;
+                const float2 q = moving_value<DIMS>(rec + size_t(b) * RM, P.x[r], P.y[r], P.z[r], P.t[r], dx, dy, dz);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float qh = h ? q.y : q.x;
+                    if (qh < 1.f) {
+                        const float *o = sObs + size_t(j0 + 2 * b + h) * ST;
+                        const float a = (DIMS == 2) ? o[3] : o[5], bb = (DIMS == 2) ? o[3] : o[6];
+                        active_pair<float, DIMS>(h ? dx.y : dx.x, h ? dy.y : dy.x, h ? dz.y : dz.x, qh, a, bb, fin,
+                                                 slot0 + G * r, PS);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// All static and moving pairs of one chunk against the item's points.  `am`
+// is the mask of the warp's lanes that hold an item (all run the same trip
+// counts).
+template <int DIMS, int R, int NPB>
+__device__ __forceinline__ void packed_pairs(const float *srec, const float *mrec, const float *sObs, int pcs,
+                                             int pcm, int js0, int jm0, const PackedPoints<DIMS, R> &P, bool fin,
+                                             float *slot0, int G, int PS, unsigned am)
+{
+    constexpr int RS = DIMS == 2 ? 8 : 12;
+    constexpr int RM = DIMS == 2 ? 12 : 16;
+    int k = 0;
+    for (; k + NPB <= pcs; k += NPB) {
+        float m[R];
+#pragma unroll
+        for (int b = 0; b < NPB; ++b) {
+            const float *q = srec + size_t(k + b) * RS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 v = static_value<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r]);
+                m[r] = (b == 0) ? fminf(v.x, v.y) : fmin3(m[r], v.x, v.y);
+            }
+        }
+        bool f = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f |= m[r] < P.npq[r];
+        if (__any_sync(am, f)) static_rescan<DIMS, R>(srec, sObs, k, NPB, js0, P, m, fin, slot0, G, PS);
+    }
+    if (k < pcs) {
+        float m[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) m[r] = INFINITY;
+        for (int b = k; b < pcs; ++b) {
+            const float *q = srec + size_t(b) * RS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float2 v = static_value<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r]);
+                m[r] = fmin3(m[r], v.x, v.y);
+            }
+        }
+        bool f = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f |= m[r] < P.npq[r];
+        if (__any_sync(am, f)) static_rescan<DIMS, R>(srec, sObs, k, pcs - k, js0, P, m, fin, slot0, G, PS);
+    }
+    // moving obstacles: the batch minimum is the exact squared scaled distance
+    constexpr int NPM = 2;
+    for (k = 0; k < pcm; k += NPM) {
+        const int nb = min(NPM, pcm - k);
+        float m[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) m[r] = INFINITY;
+#pragma unroll
+        for (int b = 0; b < NPM; ++b) {
+            if (b < nb) {
+                const float *q = mrec + size_t(k + b) * RM;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float2 dx, dy, dz;
+                    const float2 v = moving_value<DIMS>(q, P.x[r], P.y[r], P.z[r], P.t[r], dx, dy, dz);
+                    m[r] = fmin3(m[r], v.x, v.y);
+                }
+            }
+        }
+        bool f = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f |= m[r] < 1.f;
+        if (__any_sync(am, f)) moving_rescan<DIMS, R>(mrec, sObs, k, nb, jm0, P, m, fin, slot0, G, PS);
+    }
+}
+
 // NF: free coefficients (0 = runtime); NG: columns of the transposed basis
 // product (0 = runtime, <= 16).  Each sample of the CTA is owned by its own
 // group of p.WS warps, which runs all K iterations with group barriers only.
@@ -294,6 +540,63 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
         sC[e] = Real(0);
     }
     __syncthreads();
+    // FP32: obstacle pair records of the packed loop, from the obstacle records
+    constexpr bool kPacked = sizeof(Real) == 4;
+    const PairLayout PL = pair_layout(DIMS, p.n_obs, p.n_static, C, L.total);
+    if constexpr (kPacked) {
+        constexpr int ST = DIMS == 2 ? 12 : 16;
+        constexpr int RS = DIMS == 2 ? 8 : 12, RM = DIMS == 2 ? 12 : 16;
+        const int ns = p.n_static;
+        for (int q = tid; q < C * PL.pcs; q += T) {
+            const int c = q / PL.pcs, k = q - c * PL.pcs;
+            Real *d = sm + PL.st + size_t(q) * RS;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = c * 2 * PL.pcs + 2 * k + h;
+                const bool ok = j < ns;
+                const Real *o = sObs + size_t(ok ? j : 0) * ST;
+                d[h] = ok ? o[0] : Real(0);
+                d[2 + h] = ok ? o[1] : Real(0);
+                if constexpr (DIMS == 2) {
+                    d[4 + h] = ok ? -o[2] : Real(3e38);  // padding: never below -|p|^2
+                    d[6 + h] = Real(0);
+                } else {
+                    d[4 + h] = ok ? o[2] : Real(0);
+                    d[6 + h] = ok ? o[4] : Real(0);
+                    d[8 + h] = ok ? -o[3] : Real(3e38);
+                    d[10 + h] = Real(0);
+                }
+            }
+        }
+        for (int q = tid; q < C * PL.pcm; q += T) {
+            const int c = q / PL.pcm, k = q - c * PL.pcm;
+            Real *d = sm + PL.mv + size_t(q) * RM;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = ns + c * 2 * PL.pcm + 2 * k + h;
+                const bool ok = j < p.n_obs;
+                const Real *o = sObs + size_t(ok ? j : 0) * ST;
+                // padding: scaled offset (4, 4[, 4]) at every time, never active
+                if constexpr (DIMS == 2) {
+                    d[h] = ok ? o[4] : Real(0);       // ia
+                    d[2 + h] = ok ? o[5] : Real(4);   // nox
+                    d[4 + h] = ok ? o[6] : Real(4);   // noy
+                    d[6 + h] = ok ? o[8] : Real(0);   // nvx
+                    d[8 + h] = ok ? o[9] : Real(0);   // nvy
+                    d[10 + h] = Real(0);
+                } else {
+                    d[h] = ok ? o[8] : Real(0);        // ia
+                    d[2 + h] = ok ? o[12] : Real(0);   // ib
+                    d[4 + h] = ok ? o[9] : Real(4);    // nox
+                    d[6 + h] = ok ? o[10] : Real(4);   // noy
+                    d[8 + h] = ok ? o[11] : Real(4);   // noz
+                    d[10 + h] = ok ? o[13] : Real(0);  // nvx
+                    d[12 + h] = ok ? o[14] : Real(0);  // nvy
+                    d[14 + h] = ok ? o[15] : Real(0);  // nvz
+                }
+            }
+        }
+    }
     for (int e = tid; e < S_act * D; e += T) {
         const int s = e / D, d = e - s * D;
         const int ax = d / nv, col = d - ax * nv;
@@ -433,6 +736,48 @@ __device__ void project_body(const ProjParams<Real> &p, int s0)
         group_sync(bar, GT);
         // ---- B: obstacle pairs, per (lane group of R points, obstacle chunk);
         //      each item owns its points' slots of its chunk in sPart
+        if constexpr (kPacked) {
+            const int G = (np_ + R - 1) / R, itemsP = G * C;
+            for (int base = 0; base < itemsP; base += GT) {
+                const int it = base + lt;
+                const unsigned am = __ballot_sync(kFull, it < itemsP);
+                if (it < itemsP) {
+                    const int c = it / G, g = it - c * G;
+                    Real *slot0 = sPart + size_t(c) * DIMS * PS + ps0 + g;
+                    PackedPoints<DIMS, R> P;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int tl = g + G * r;
+                        const bool ok = tl < np_;
+                        // padding points sit far outside every obstacle
+                        const float x = ok ? sPos[ps0 + tl] : 1e15f;
+                        const float y = ok ? sPos[PS + ps0 + tl] : 1e15f;
+                        const float z = (DIMS == 3 && ok) ? sPos[2 * PS + ps0 + tl] : 0.f;
+                        const float tv = ok ? sT[tl] : 0.f;
+                        P.x[r] = make_float2(x, x);
+                        P.y[r] = make_float2(y, y);
+                        P.z[r] = make_float2(z, z);
+                        P.zz[r] = make_float2(z * z, z * z);
+                        P.t[r] = make_float2(tv, tv);
+                        P.npq[r] = -fmaf(x, x, y * y);
+                        if (ok) {
+                            slot0[G * r] = Real(0);
+                            if (!fin) {
+                                slot0[PS + G * r] = Real(0);
+                                if (DIMS == 3) slot0[2 * PS + G * r] = Real(0);
+                            }
+                        }
+                    }
+                    packed_pairs<DIMS, R, 4>(reinterpret_cast<const float *>(sm + PL.st) +
+                                                 size_t(c) * PL.pcs * pair_rec_static(DIMS),
+                                             reinterpret_cast<const float *>(sm + PL.mv) +
+                                                 size_t(c) * PL.pcm * pair_rec_moving(DIMS),
+                                             reinterpret_cast<const float *>(sObs), PL.pcs, PL.pcm,
+                                             c * 2 * PL.pcs, p.n_static + c * 2 * PL.pcm, P, fin,
+                                             reinterpret_cast<float *>(slot0), G, PS, am);
+                }
+            }
+        } else
         for (int it = lt; it < items; it += GT) {
             const int c = it / nblk32, g = it - c * nblk32;
             const int pl = (g >> 5) * (32 * R) + (g & 31);  // first local point of the lane
