@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpriest.so")
-SOURCES = ["setup.cu", "project.cu", "project_f32_2d.cu", "project_f32_2d_wide.cu", "project_f32_3d.cu", "project_f64.cu", "cem.cu", "api.cu",
+SOURCES = ["setup.cu", "project.cu", "project_f32_2d.cu", "project_f32_2d_wide.cu", "project_f32_3d.cu", "project_pts.cu", "project_f64.cu", "cem.cu", "api.cu",
            "noalloc.cu", "serve.cu", "rng.cu", "plain.cu", "tc_selftest.cu", "project_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

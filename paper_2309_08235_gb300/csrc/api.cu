@@ -449,8 +449,8 @@ priest_status enqueue_setup(priest_ctx *ctx, priest_loaded *h, bool plan_mode, c
 
 // Optional persistent record of tuned tilings: the file named by the
 // environment variable PRIEST_TUNE_CACHE holds one line per shape,
-// "<10 key integers> S C R threads ws".  Read once per context, appended to
-// after each new tuning.
+// "<10 key integers> S C R threads ws kind".  Read once per context, appended
+// to after each new tuning.
 void load_tune_cache(priest_ctx *ctx)
 {
     const char *path = getenv("PRIEST_TUNE_CACHE");
@@ -458,17 +458,22 @@ void load_tune_cache(priest_ctx *ctx)
     ctx->tune_cache_loaded = true;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    std::vector<int> v(15);
-    for (;;) {
-        int got = 0;
-        for (int i = 0; i < 15; ++i) got += fscanf(f, "%d", &v[i]);
-        if (got != 15) break;
+    char line[512];
+    while (fgets(line, sizeof(line), f)) {
+        std::vector<int> v;
+        char *c = line, *end = nullptr;
+        for (long x = strtol(c, &end, 10); end != c; x = strtol(c, &end, 10)) {
+            v.push_back(int(x));
+            c = end;
+        }
+        if (v.size() != 16) continue;  // lines of another format are ignored
         Tiling t;
         t.S = v[10];
         t.C = v[11];
         t.R = v[12];
         t.threads = v[13];
         t.ws = v[14];
+        t.kind = v[15];
         t.smem = 0;
         ctx->tuned[std::vector<int>(v.begin(), v.begin() + 10)] = t;
     }
@@ -482,7 +487,7 @@ void save_tune_entry(const std::vector<int> &key, const Tiling &t)
     FILE *f = fopen(path, "a");
     if (!f) return;
     for (int k : key) fprintf(f, "%d ", k);
-    fprintf(f, "%d %d %d %d %d\n", t.S, t.C, t.R, t.threads, t.ws);
+    fprintf(f, "%d %d %d %d %d %d\n", t.S, t.C, t.R, t.threads, t.ws, t.kind);
     fclose(f);
 }
 
@@ -501,7 +506,7 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
         Tiling t = it->second;
-        if (t.smem == 0) t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
+        if (t.smem == 0) t.smem = t.kind == 1 ? pts_smem_bytes(sh, t.S, t.R) : project_smem_bytes<Real>(sh, t.S, t.C);
         return t;
     }
     std::vector<Tiling> cands = tiling_candidates<Real>(sh, N, ctx->n_sm);
@@ -539,8 +544,8 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
         const float ms = ok ? (t_k[1] - t_k[0]) / float(k_hi - k_lo) : 1e30f;
         if (const char *lv = getenv("PRIEST_AUTOTUNE_LOG"))
             if (atoi(lv) >= 2)
-                fprintf(stderr, "priest autotune candidate: S=%d C=%d R=%d threads=%d ws=%d smem=%zu -> %.2f us / iteration\n",
-                        t.S, t.C, t.R, t.threads, t.ws, t.smem, 1e3f * ms);
+                fprintf(stderr, "priest autotune candidate: kind=%d S=%d C=%d R=%d threads=%d ws=%d smem=%zu -> %.2f us / iteration\n",
+                        t.kind, t.S, t.C, t.R, t.threads, t.ws, t.smem, 1e3f * ms);
         if (ms < best_ms) {
             best_ms = ms;
             best = t;
@@ -549,8 +554,8 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (getenv("PRIEST_AUTOTUNE_LOG"))
-        fprintf(stderr, "priest autotune: %zu candidates, best S=%d C=%d R=%d threads=%d ws=%d (%.2f us / iteration)\n",
-                cands.size(), best.S, best.C, best.R, best.threads, best.ws, 1e3f * best_ms);
+        fprintf(stderr, "priest autotune: %zu candidates, best kind=%d S=%d C=%d R=%d threads=%d ws=%d (%.2f us / iteration)\n",
+                cands.size(), best.kind, best.S, best.C, best.R, best.threads, best.ws, 1e3f * best_ms);
     ctx->tuned[key] = best;
     save_tune_entry(key, best);
     return best;

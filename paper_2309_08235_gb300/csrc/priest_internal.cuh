@@ -215,10 +215,17 @@ struct Tiling {
     int S;        // samples per CTA
     int C;        // obstacle chunks per CTA
     int threads;  // CTA size
-    int R;        // points per obstacle-loop item (template value)
+    int R;        // points per obstacle-loop item / per thread (template value)
     int ws;       // warps per sample
     size_t smem;  // dynamic shared memory bytes
+    int kind = 0; // 0: chunked kernel (project_kernel.cuh); 1: point-owner FP32 kernel (project_pts.cuh)
 };
+
+// FP32 point-owner kernel (project_pts.cu): degree 10 with 5 free coefficients.
+bool pts_supported(const Shape &sh);
+size_t pts_smem_bytes(const Shape &sh, int S, int R);
+int pts_threads(const Shape &sh, int S, int R);
+int pts_max_threads(int R);
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` (the default limit
 // counts static shared memory too, so it is raised whenever more is asked
@@ -295,6 +302,7 @@ size_t project_smem_bytes(const Shape &sh, int S, int C);
 
 template <typename Real>
 cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st);
+cudaError_t launch_project_pts(const ProjParams<float> &p, const Tiling &t, cudaStream_t st);
 
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm);

@@ -56,12 +56,54 @@ int samples_per_cta(int n_samples, int n_sm, int threads, int ws)
     return std::max(1, S);
 }
 
+// Point-owner tiling (FP32, project_pts.cuh): S samples per CTA with R points
+// per thread; smem == 0 when the CTA does not fit.
+Tiling pts_tiling(const Shape &sh, int S, int R)
+{
+    Tiling t;
+    t.kind = 1;
+    t.R = R;
+    t.S = S;
+    t.C = 1;
+    t.ws = 0;
+    t.threads = pts_threads(sh, S, R);
+    t.smem = pts_smem_bytes(sh, S, R);
+    if (t.threads > pts_max_threads(R) || t.smem > kSmemCap) t.smem = 0;
+    return t;
+}
+
+// Point-owner candidates: two or four points per thread, the samples of one
+// wave over the SMs (or the most that fit one CTA), and half that.
+std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
+{
+    std::vector<Tiling> out;
+    if (!pts_supported(sh)) return out;
+    for (int R : {2, 4}) {
+        const int tps = (sh.n_p + R - 1) / R;
+        const int s_max = std::max(1, pts_max_threads(R) / tps);
+        const int s1 = std::min(s_max, std::max(1, (n_samples + n_sm - 1) / n_sm));
+        const int s2 = (s1 + 1) / 2;
+        for (int S : {s1, s2}) {
+            if (S == s2 && s2 == s1) continue;
+            const Tiling t = pts_tiling(sh, S, R);
+            if (t.smem > 0) out.push_back(t);
+        }
+    }
+    return out;
+}
+
 // Default tiling: the largest compiled variant, the largest warp group that
 // fits the CTA, and the obstacle chunk count that gives each group's threads
 // about one item each, within the shared-memory cap.
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm)
 {
+    if (sizeof(Real) == 4 && pts_supported(sh)) {
+        const int tps = (sh.n_p + 1) / 2;
+        const int S = std::min(std::max(1, pts_max_threads(2) / tps), std::max(1, (n_samples + n_sm - 1) / n_sm));
+        const Tiling p = pts_tiling(sh, S, 2);
+        if (p.smem > 0) return p;
+    }
     Tiling t;
     t.R = sizeof(Real) == 8 ? 4 : 5;
     t.threads = sizeof(Real) == 8 ? 256 : 512;
@@ -87,6 +129,7 @@ template <typename Real>
 std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm)
 {
     std::vector<Tiling> out;
+    if (sizeof(Real) == 4) out = pts_candidates(sh, n_samples, n_sm);
     for (const Variant &v : variants<Real>()) {
         if (v.dims != sh.dims) continue;
         for (int ws = 1; ws <= 8 && 32 * ws <= v.threads; ws *= 2) {
@@ -165,6 +208,7 @@ cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStrea
         if (p.dims == 2) return launch_variant<Real, 2, 4, 256>(p, t, st);
         return launch_variant<Real, 3, 4, 256>(p, t, st);
     } else {
+        if (t.kind == 1) return launch_project_pts(p, t, st);
         if (t.S * 32 * t.ws > t.threads) return cudaErrorInvalidValue;
         if (p.dims == 2) {
             if (t.R == 4 && t.threads == 512) return launch_variant<Real, 2, 4, 512>(p, t, st);

@@ -1,0 +1,56 @@
+// project_pts.cu -- launch of the FP32 point-owner projection kernel
+// (project_pts.cuh): shared-memory size and dispatch over the compiled
+// (dims, points per thread, fixed-column multipliers) variants.
+#include "project_pts.cuh"
+
+namespace priest {
+
+size_t pts_smem_bytes(const Shape &sh, int S, int R)
+{
+    return pts::pts_layout(sh.dims, sh.nf, sh.nv, sh.n_p, sh.n_obs, sh.n_static, S, R).total * sizeof(float);
+}
+
+int pts_threads(const Shape &sh, int S, int R) { return ((S * pts::pts_tps(sh.n_p, R) + 31) / 32) * 32; }
+
+int pts_max_threads(int R) { return R <= 2 ? pts::pts_max_threads<2>() : pts::pts_max_threads<4>(); }
+
+bool pts_supported(const Shape &sh) { return sh.nf == 5 && sh.nv == 11 && (sh.dims == 2 || sh.dims == 3); }
+
+namespace {
+
+template <int DIMS, int R, bool WL>
+cudaError_t launch_pts_one(const ProjParams<float> &p, const Tiling &t, cudaStream_t st)
+{
+    static size_t granted = 0;  // per instantiation
+    cudaError_t e = reserve_smem(pts::pts_kernel<DIMS, R, 5, WL>, t.smem, granted);
+    if (e != cudaSuccess) return e;
+    const int grid = (p.N + t.S - 1) / t.S;
+    pts::pts_kernel<DIMS, R, 5, WL><<<grid, t.threads, t.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int DIMS, int R>
+cudaError_t launch_pts_wl(const ProjParams<float> &p, const Tiling &t, cudaStream_t st)
+{
+    return p.want_lambda ? launch_pts_one<DIMS, R, true>(p, t, st) : launch_pts_one<DIMS, R, false>(p, t, st);
+}
+
+}  // namespace
+
+cudaError_t launch_project_pts(const ProjParams<float> &p, const Tiling &t, cudaStream_t st)
+{
+    if (p.N <= 0) return cudaSuccess;
+    if (p.nf != 5 || p.nv != 11) return cudaErrorInvalidValue;
+    const int tps = pts::pts_tps(p.n_p, t.R);
+    if (t.S * tps > t.threads || t.threads % 32 != 0 || t.threads > pts_max_threads(t.R)) return cudaErrorInvalidValue;
+    if (p.dims == 2) {
+        if (t.R == 2) return launch_pts_wl<2, 2>(p, t, st);
+        if (t.R == 4) return launch_pts_wl<2, 4>(p, t, st);
+    } else if (p.dims == 3) {
+        if (t.R == 2) return launch_pts_wl<3, 2>(p, t, st);
+        if (t.R == 4) return launch_pts_wl<3, 4>(p, t, st);
+    }
+    return cudaErrorInvalidValue;  // not a compiled variant
+}
+
+}  // namespace priest

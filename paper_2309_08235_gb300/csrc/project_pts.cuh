@@ -1,0 +1,698 @@
+// project_pts.cuh -- FP32 fused projection with point-owning threads (Sec. III-A;
+// Appendix eqs. lagrange, comp_alpha .. comp_zeta, lag, affine_trans /
+// matrix_vec / comp_zeta), the hot path of the FP32 solver.
+//
+// Same iteration as project_kernel.cuh (phases A: trajectory and velocity /
+// acceleration / workspace residuals, B: obstacle pairs, C: g = F^T (F xi_bar
+// - e) and the multiplier step, D: the shared-inverse step), organised so the
+// per-point work never leaves registers:
+//   * a CTA holds S samples of one problem; thread (s, j) owns the R time
+//     stamps j, j + TPS, ..., TPS = ceil(n_p / R), of sample s for all K
+//     iterations, with its rows of the free-column basis (P, Pd, Pdd) and of
+//     the fixed-coefficient part in registers (loaded once per launch);
+//   * phase B tests the thread's points against every obstacle (no obstacle
+//     chunks): static obstacles four at a time from "quad" records (one f32x2
+//     FMA evaluates a point against two obstacles), moving ones two at a time;
+//     a running three-input minimum and one warp vote per batch find the rare
+//     candidates, which are recomputed with the same operations and tested
+//     exactly; residuals S_o accumulate in registers;
+//   * phase C forms each thread's share of g on the free columns and reduces
+//     it over the sample's threads with a segmented warp reduction (a warp may
+//     hold the end of one sample and the start of the next), one partial per
+//     (sample, warp) in shared memory, summed in a fixed order;
+//   * phase D: one lane per (sample, axis, free column) applies the multiplier
+//     and shared-inverse steps.
+// Two CTA barriers per iteration.  The multipliers of the fixed columns
+// (returned only on request) follow from the linearity of eq. lag:
+// lambda_B^K = lambda_B^0 - rho P_B^T sum_k r^k, so the per-point residual rows
+// are summed over the iterations and reduced once at the end.
+#pragma once
+
+#include "project_kernel.cuh"
+
+namespace priest {
+namespace pts {
+
+using detail::ffma2;
+using detail::fmin3;
+using detail::fmul2;
+using detail::kFull;
+
+// Shared-memory layout (float units; every block 32-byte aligned).
+//   obs   [n_obs][12 | 16]  obstacle records (copied from the tables)
+//   srec  [nq][12 | 20]     static quads: {m2x x4} {m2y x4} [{m2z x4} {kap x4}] {nthr x4}
+//   mrec  [nm2][12 | 16]    moving pairs (layout of project_kernel.cuh)
+//   W     [nf][nf]
+//   cd    [S][dims][cds]    free coefficients, each stored twice (c_f, c_f)
+//   lam, xi, u [S][dims][8] multipliers, sample, shared-inverse argument (free columns)
+//   part  [S][maxw][dims*nv] per-(sample, warp) partial sums
+//   part2 [S][maxw][2]      (doubles) residual / cost partials of the final pass
+struct PtsLayout {
+    int tps, nq, nm2, maxw, cds;
+    size_t obs, srec, mrec, W, cd, lam, xi, u, part, part2, total;
+};
+
+__host__ __device__ inline int pts_tps(int n_p, int R) { return (n_p + R - 1) / R; }
+
+__host__ __device__ inline PtsLayout pts_layout(int dims, int nf, int nv, int n_p, int n_obs, int n_static, int S,
+                                                int R)
+{
+    PtsLayout L;
+    L.tps = pts_tps(n_p, R);
+    L.nq = (n_static + 3) / 4;
+    L.nm2 = (n_obs - n_static + 1) / 2;
+    L.maxw = (L.tps + 31) / 32 + 1;
+    L.cds = ((2 * nf + 3) / 4) * 4;
+    size_t o = 0;
+    L.obs = o;
+    o = align8(o + size_t(n_obs) * (dims == 2 ? 12 : 16));
+    L.srec = o;
+    o = align8(o + size_t(L.nq) * (dims == 2 ? 12 : 20));
+    L.mrec = o;
+    o = align8(o + size_t(L.nm2) * (dims == 2 ? 12 : 16));
+    L.W = o;
+    o = align8(o + size_t(nf) * nf);
+    L.cd = o;
+    o = align8(o + size_t(S) * dims * L.cds);
+    L.lam = o;
+    o = align8(o + size_t(S) * dims * 8);
+    L.xi = o;
+    o = align8(o + size_t(S) * dims * 8);
+    L.u = o;
+    o = align8(o + size_t(S) * dims * 8);
+    L.part = o;
+    o = align8(o + size_t(S) * L.maxw * dims * nv);
+    L.part2 = o;
+    o = align8(o + size_t(S) * L.maxw * 4);
+    L.total = o;
+    return L;
+}
+
+// Segmented warp sum: lanes [lane, send] of one segment (send = the last lane
+// of the calling lane's segment in this warp); afterwards the first lane of
+// each segment holds its segment's in-warp sum.
+template <typename T>
+__device__ __forceinline__ T seg_sum(T v, int lane, int send)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T o = __shfl_down_sync(kFull, v, d);
+        if (lane + d <= send) v += o;
+    }
+    return v;
+}
+
+// Residual contribution of an active pair into registers (the arithmetic of
+// project_kernel.cuh's active_pair): so[] += Delta (1 - 1/rho_s), or in the
+// final pass so[0] += |Delta (1 - 1/rho_s)|^2.
+template <int DIMS>
+__device__ __forceinline__ void active_add(float dx, float dy, float dz, float q, float a, float b, bool fin,
+                                           float (&so)[DIMS])
+{
+    if (q > 0.f) {
+        const float rs = rsqrtf(q);
+        const float w = 1.f - rs;
+        if (!fin) {
+            so[0] = fmaf(a * w, dx, so[0]);
+            so[1] = fmaf(a * w, dy, so[1]);
+            if constexpr (DIMS == 3) so[DIMS - 1] = fmaf(b * w, dz, so[DIMS - 1]);
+        } else {
+            const float d2 = (DIMS == 3) ? a * a * fmaf(dx, dx, dy * dy) + b * b * dz * dz : a * a * q;
+            so[0] = fmaf(w * w, d2, so[0]);
+        }
+    } else {
+        // at the centre the target is o + (a, 0) (2-D) / o + (0, 0, b) (3-D)
+        const float s = (DIMS == 3) ? b : a;
+        if (!fin)
+            so[DIMS == 3 ? DIMS - 1 : 0] -= s;
+        else
+            so[0] = fmaf(s, s, so[0]);
+    }
+}
+
+template <int DIMS>
+__device__ __forceinline__ void exact_static(const float *sObs, int j, float x, float y, float z, bool fin,
+                                             float (&so)[DIMS])
+{
+    constexpr int ST = DIMS == 2 ? 12 : 16;
+    const float *o = sObs + size_t(j) * ST;
+    float ia, nox, noy, noz = 0.f, ib = 0.f, a, b = 0.f, d0, d1;
+    if constexpr (DIMS == 2) {
+        a = o[3];
+        detail::ld4(o + 4, ia, nox, noy, d0);
+    } else {
+        detail::ld4(o + 4, d0, a, b, d1);
+        detail::ld4(o + 8, ia, nox, noy, noz);
+        ib = o[12];
+    }
+    const float dx = fmaf(x, ia, nox), dy = fmaf(y, ia, noy);
+    const float dz = (DIMS == 3) ? fmaf(z, ib, noz) : 0.f;
+    const float q = (DIMS == 3) ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
+    if (q < 1.f) active_add<DIMS>(dx, dy, dz, q, a, b, fin, so);
+}
+
+// Pre-filter values of one static quad against one point (obstacles 0-1 and
+// 2-3): the expanded test without |p|^2, compared with -|p|^2.
+template <int DIMS>
+__device__ __forceinline__ void quad_values(const float *q, float2 xd, float2 yd, float2 zd, float2 zzd, float2 &v01,
+                                            float2 &v23)
+{
+    const float4 A = *reinterpret_cast<const float4 *>(q);
+    const float4 B = *reinterpret_cast<const float4 *>(q + 4);
+    const float4 Cc = *reinterpret_cast<const float4 *>(q + 8);
+    if constexpr (DIMS == 2) {
+        v01 = ffma2(xd, make_float2(A.x, A.y), ffma2(yd, make_float2(B.x, B.y), make_float2(Cc.x, Cc.y)));
+        v23 = ffma2(xd, make_float2(A.z, A.w), ffma2(yd, make_float2(B.z, B.w), make_float2(Cc.z, Cc.w)));
+    } else {
+        const float4 Dd = *reinterpret_cast<const float4 *>(q + 12);
+        const float4 E = *reinterpret_cast<const float4 *>(q + 16);
+        v01 = ffma2(xd, make_float2(A.x, A.y),
+                    ffma2(yd, make_float2(B.x, B.y),
+                          ffma2(zd, make_float2(Cc.x, Cc.y), ffma2(zzd, make_float2(Dd.x, Dd.y), make_float2(E.x, E.y)))));
+        v23 = ffma2(xd, make_float2(A.z, A.w),
+                    ffma2(yd, make_float2(B.z, B.w),
+                          ffma2(zd, make_float2(Cc.z, Cc.w), ffma2(zzd, make_float2(Dd.z, Dd.w), make_float2(E.z, E.w)))));
+    }
+}
+
+// Quads [k0, k0 + nb): exact tests of the flagged points' candidates, in
+// obstacle order.
+template <int DIMS, int R>
+__device__ __forceinline__ void quad_rescan(const float *rec, const float *sObs, int k0, int nb,
+                                            const detail::PackedPoints<DIMS, R> &P, const float (&m)[R], bool fin,
+                                            float (&so)[R][DIMS])
+{
+    constexpr int QS = DIMS == 2 ? 12 : 20;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (m[r] < P.npq[r]) {
+            for (int b = k0; b < k0 + nb; ++b) {
+                float2 v01, v23;
+                quad_values<DIMS>(rec + size_t(b) * QS, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
+                const float vv[4] = {v01.x, v01.y, v23.x, v23.y};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (vv[i] < P.npq[r]) exact_static<DIMS>(sObs, 4 * b + i, P.x[r].x, P.y[r].x, P.z[r].x, fin, so[r]);
+            }
+        }
+    }
+}
+
+template <int DIMS, int R>
+__device__ __forceinline__ void moving_rescan(const float *rec, const float *sObs, int k0, int nb, int j0,
+                                              const detail::PackedPoints<DIMS, R> &P, const float (&m)[R], bool fin,
+                                              float (&so)[R][DIMS])
+{
+    constexpr int RM = DIMS == 2 ? 12 : 16;
+    constexpr int ST = DIMS == 2 ? 12 : 16;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (m[r] < 1.f) {
+            for (int b = k0; b < k0 + nb; ++b) {
+                float2 dx, dy, dz;
+                const float2 q =
+                    detail::moving_value<DIMS>(rec + size_t(b) * RM, P.x[r], P.y[r], P.z[r], P.t[r], dx, dy, dz);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float qh = h ? q.y : q.x;
+                    if (qh < 1.f) {
+                        const float *o = sObs + size_t(j0 + 2 * b + h) * ST;
+                        const float a = (DIMS == 2) ? o[3] : o[5], bb = (DIMS == 2) ? o[3] : o[6];
+                        active_add<DIMS>(h ? dx.y : dx.x, h ? dy.y : dy.x, h ? dz.y : dz.x, qh, a, bb, fin, so[r]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Every obstacle against the thread's R points; all lanes of the CTA run the
+// same trip counts, so the votes use the full warp.
+template <int DIMS, int R, int NQB>
+__device__ __forceinline__ void all_pairs(const float *srec, const float *mrec, const float *sObs, int nq, int nm2,
+                                          int ns, const detail::PackedPoints<DIMS, R> &P, bool fin,
+                                          float (&so)[R][DIMS])
+{
+    constexpr int QS = DIMS == 2 ? 12 : 20;
+    constexpr int RM = DIMS == 2 ? 12 : 16;
+    int k = 0;
+    for (; k + NQB <= nq; k += NQB) {
+        float m[R];
+#pragma unroll
+        for (int b = 0; b < NQB; ++b) {
+            const float *q = srec + size_t(k + b) * QS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 v01, v23;
+                quad_values<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
+                const float m01 = (b == 0) ? fminf(v01.x, v01.y) : fmin3(m[r], v01.x, v01.y);
+                m[r] = fmin3(m01, v23.x, v23.y);
+            }
+        }
+        bool f = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f |= m[r] < P.npq[r];
+        if (__any_sync(kFull, f)) quad_rescan<DIMS, R>(srec, sObs, k, NQB, P, m, fin, so);
+    }
+    if (k < nq) {
+        float m[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) m[r] = INFINITY;
+        for (int b = k; b < nq; ++b) {
+            const float *q = srec + size_t(b) * QS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 v01, v23;
+                quad_values<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
+                m[r] = fmin3(fmin3(m[r], v01.x, v01.y), v23.x, v23.y);
+            }
+        }
+        bool f = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f |= m[r] < P.npq[r];
+        if (__any_sync(kFull, f)) quad_rescan<DIMS, R>(srec, sObs, k, nq - k, P, m, fin, so);
+    }
+    // moving obstacles: the batch minimum is the exact squared scaled distance
+    constexpr int NPM = 2;
+    for (k = 0; k < nm2; k += NPM) {
+        const int nb = min(NPM, nm2 - k);
+        float m[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) m[r] = INFINITY;
+#pragma unroll
+        for (int b = 0; b < NPM; ++b) {
+            if (b < nb) {
+                const float *q = mrec + size_t(k + b) * RM;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float2 dx, dy, dz;
+                    const float2 v = detail::moving_value<DIMS>(q, P.x[r], P.y[r], P.z[r], P.t[r], dx, dy, dz);
+                    m[r] = fmin3(m[r], v.x, v.y);
+                }
+            }
+        }
+        bool f = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f |= m[r] < 1.f;
+        if (__any_sync(kFull, f)) moving_rescan<DIMS, R>(mrec, sObs, k, nb, ns, P, m, fin, so);
+    }
+}
+
+// The projection of samples [s0, s0 + S) of one problem by the calling CTA
+// (blockDim.x >= S * TPS, a multiple of 32; all threads call it).
+// WL: also return the multipliers of the fixed columns.
+template <int DIMS, int R, int NF, bool WL>
+__device__ void pts_body(const ProjParams<float> &p, int s0)
+{
+    static_assert(R % 2 == 0, "points are paired for the f32x2 basis products");
+    constexpr int H = R / 2;
+    constexpr int ST = DIMS == 2 ? 12 : 16;
+    constexpr int QS = DIMS == 2 ? 12 : 20;
+    constexpr int RM = DIMS == 2 ? 12 : 16;
+    constexpr int NB = 11 - NF;  // fixed columns (degree 10: 11 coefficients per axis)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sm = reinterpret_cast<float *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    const int np_ = p.n_p, nv = p.nv, D = DIMS * nv, nobs = p.n_obs, ns = p.n_static;
+    const int S = p.S;
+    const int S_act = min(S, p.N - s0);
+    if (S_act <= 0) return;
+    const PtsLayout L = pts_layout(DIMS, NF, nv, np_, nobs, ns, S, R);
+    const int TPS = L.tps, CDS = L.cds, PD = DIMS * nv;
+    const int s = tid / TPS, j = tid - s * TPS;
+    const bool act = s < S_act;
+    const int sc = act ? s : 0;  // a valid sample index for idle threads' reads
+    const int fw = (sc * TPS) >> 5;
+    // last lane of this thread's segment in the warp (idle threads form one segment)
+    const int send = act ? min(31, (sc + 1) * TPS - 1 - 32 * warp) : 31;
+    const bool head = act && (lane == 0 || j == 0);
+    float *sObs = sm + L.obs, *sW = sm + L.W, *sCd = sm + L.cd, *sLam = sm + L.lam, *sXi = sm + L.xi,
+          *sU = sm + L.u, *sPart = sm + L.part;
+    double *sPart2 = reinterpret_cast<double *>(sm + L.part2);
+    const float rho = p.rho, vmax = p.vmax, amax = p.amax, vmax2 = vmax * vmax, amax2 = amax * amax;
+
+    // ---- obstacle records and W -> shared memory; a1/a2 sample set-up
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(p.tab + p.lay.obs);
+        float4 *dst = reinterpret_cast<float4 *>(sObs);
+        for (int i = tid; i < nobs * ST / 4; i += T) dst[i] = src[i];
+        for (int i = tid; i < NF * NF; i += T) sW[i] = p.tab[p.lay.W + i];
+    }
+    for (int e = tid; e < S_act * D; e += T) {
+        const int ss = e / D, d = e - ss * D;
+        const int ax = d / nv, col = d - ax * nv;
+        const size_t gi = size_t(s0 + ss) * D + d;
+        const int f = col - kFree0;
+        if (f < 0 || f >= NF) continue;
+        double x;
+        if (p.mode == 0) {
+            x = p.xi_in[gi];
+        } else {
+            const size_t seg = p.seg_len > 0 ? size_t((s0 + ss) / p.seg_len) : 0;  // D-PRIEST distribution
+            const double *Lrow = p.Lc + (seg * D + d) * D;
+            const double *zi = p.z + size_t(s0 + ss) * D;
+            x = p.mu[seg * D + d];
+            for (int q = 0; q <= d; ++q) x = fma(Lrow[q], zi[q], x);
+        }
+        const int ro = ss * DIMS + ax;
+        sXi[ro * 8 + f] = float(x);
+        sCd[ro * CDS + 2 * f] = float(x);
+        sCd[ro * CDS + 2 * f + 1] = float(x);
+        sLam[ro * 8 + f] = p.lam_in ? float(p.lam_in[gi]) : 0.f;
+    }
+    // per-thread constants: basis rows (pairs of points), fixed part, time stamps
+    float2 bf[3][NF][H], bs[3][DIMS][H];
+    float tt[R];
+    bool ok[R];
+    {
+        const int fbs = fb_stride(NF), nfp = nf_padded(NF);
+        const float *fb = p.tab + p.lay.fb, *bas = p.tab + p.lay.base, *tv = p.tab + p.lay.tval;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int t = j + TPS * r;
+            ok[r] = act && t < np_;
+            tt[r] = ok[r] ? tv[t] : 0.f;
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int t0 = j + TPS * (2 * h), t1 = t0 + TPS;
+            const bool o0 = ok[2 * h], o1 = ok[2 * h + 1];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    bf[q][f][h] = make_float2(o0 ? fb[size_t(t0) * fbs + q * nfp + f] : 0.f,
+                                              o1 ? fb[size_t(t1) * fbs + q * nfp + f] : 0.f);
+#pragma unroll
+                for (int ax = 0; ax < DIMS; ++ax) {
+                    // padding points: far from every obstacle, at rest
+                    const float pad = q == 0 ? 1e15f : 0.f;
+                    bs[q][ax][h] = make_float2(o0 ? bas[(q * DIMS + ax) * np_ + t0] : pad,
+                                               o1 ? bas[(q * DIMS + ax) * np_ + t1] : pad);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // ---- pair records of the obstacle loop
+    for (int q = tid; q < L.nq; q += T) {
+        float *d = sm + L.srec + size_t(q) * QS;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int jo = 4 * q + i;
+            const bool okj = jo < ns;
+            const float *o = sObs + size_t(okj ? jo : 0) * ST;
+            d[i] = okj ? o[0] : 0.f;
+            d[4 + i] = okj ? o[1] : 0.f;
+            if constexpr (DIMS == 2) {
+                d[8 + i] = okj ? -o[2] : 3e38f;  // padding: never below -|p|^2
+            } else {
+                d[8 + i] = okj ? o[2] : 0.f;
+                d[12 + i] = okj ? o[4] : 0.f;
+                d[16 + i] = okj ? -o[3] : 3e38f;
+            }
+        }
+    }
+    for (int q = tid; q < L.nm2; q += T) {
+        float *d = sm + L.mrec + size_t(q) * RM;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jo = ns + 2 * q + h;
+            const bool okj = jo < nobs;
+            const float *o = sObs + size_t(okj ? jo : 0) * ST;
+            // padding: scaled offset (4, 4[, 4]) at every time, never active
+            if constexpr (DIMS == 2) {
+                d[h] = okj ? o[4] : 0.f;
+                d[2 + h] = okj ? o[5] : 4.f;
+                d[4 + h] = okj ? o[6] : 4.f;
+                d[6 + h] = okj ? o[8] : 0.f;
+                d[8 + h] = okj ? o[9] : 0.f;
+                d[10 + h] = 0.f;
+            } else {
+                d[h] = okj ? o[8] : 0.f;
+                d[2 + h] = okj ? o[12] : 0.f;
+                d[4 + h] = okj ? o[9] : 4.f;
+                d[6 + h] = okj ? o[10] : 4.f;
+                d[8 + h] = okj ? o[11] : 4.f;
+                d[10 + h] = okj ? o[13] : 0.f;
+                d[12 + h] = okj ? o[14] : 0.f;
+                d[14 + h] = okj ? o[15] : 0.f;
+            }
+        }
+    }
+    __syncthreads();
+
+    float smin[DIMS], smax[DIMS];
+#pragma unroll
+    for (int ax = 0; ax < DIMS; ++ax) {
+        smin[ax] = p.smin[ax] - p.tab[p.lay.origin + ax];
+        smax[ax] = p.smax[ax] - p.tab[p.lay.origin + ax];
+    }
+    float rsum[WL ? R : 1][3][DIMS];  // WL: per-point residual rows summed over the iterations
+#pragma unroll
+    for (int r = 0; r < (WL ? R : 1); ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax) rsum[r][q][ax] = 0.f;
+
+    for (int k = 0; k <= p.K; ++k) {
+        const bool fin = (k == p.K);
+        // ---- A: trajectory (pairs of points share one f32x2 FMA per term)
+        float pos[R][DIMS], vel[R][DIMS], acc[R][DIMS];
+        {
+            const float *cds = sCd + sc * DIMS * CDS;
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax) {
+                float2 cf[NF];
+#pragma unroll
+                for (int f = 0; f < NF; f += 2) {
+                    const float4 c4 = *reinterpret_cast<const float4 *>(cds + ax * CDS + 2 * f);
+                    cf[f] = make_float2(c4.x, c4.y);
+                    if (f + 1 < NF) cf[f + 1] = make_float2(c4.z, c4.w);
+                }
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    float2 P2 = bs[0][ax][h], V2 = bs[1][ax][h], A2 = bs[2][ax][h];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        P2 = ffma2(bf[0][f][h], cf[f], P2);
+                        V2 = ffma2(bf[1][f][h], cf[f], V2);
+                        A2 = ffma2(bf[2][f][h], cf[f], A2);
+                    }
+                    pos[2 * h][ax] = P2.x;
+                    pos[2 * h + 1][ax] = P2.y;
+                    vel[2 * h][ax] = V2.x;
+                    vel[2 * h + 1][ax] = V2.y;
+                    acc[2 * h][ax] = A2.x;
+                    acc[2 * h + 1][ax] = A2.y;
+                }
+            }
+        }
+        float rv[R][DIMS], ra[R][DIMS], rb[R][DIMS], fvv[R], faa[R], v2v[R], a2v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float v2 = 0.f, a2 = 0.f;
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax) {
+                v2 = fmaf(vel[r][ax], vel[r][ax], v2);
+                a2 = fmaf(acc[r][ax], acc[r][ax], a2);
+            }
+            const float fv = (v2 > vmax2) ? 1.f - vmax * rsqrtf(v2) : 0.f;
+            const float fa = (a2 > amax2) ? 1.f - amax * rsqrtf(a2) : 0.f;
+            fvv[r] = fv;
+            faa[r] = fa;
+            v2v[r] = v2;
+            a2v[r] = a2;
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax) {
+                rv[r][ax] = fv * vel[r][ax];
+                ra[r][ax] = fa * acc[r][ax];
+                rb[r][ax] = (p.use_bounds && ok[r])
+                                ? fmaxf(0.f, pos[r][ax] - smax[ax]) - fmaxf(0.f, smin[ax] - pos[r][ax])
+                                : 0.f;
+            }
+        }
+        // ---- B: every obstacle against the thread's points
+        float so[R][DIMS];
+        {
+            detail::PackedPoints<DIMS, R> P;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float x = pos[r][0], y = pos[r][1], z = DIMS == 3 ? pos[r][DIMS - 1] : 0.f;
+                P.x[r] = make_float2(x, x);
+                P.y[r] = make_float2(y, y);
+                P.z[r] = make_float2(z, z);
+                P.zz[r] = make_float2(z * z, z * z);
+                P.t[r] = make_float2(tt[r], tt[r]);
+                P.npq[r] = -fmaf(x, x, y * y);
+#pragma unroll
+                for (int ax = 0; ax < DIMS; ++ax) so[r][ax] = 0.f;
+            }
+            all_pairs<DIMS, R, 2>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
+        }
+        if (fin) {
+            // ---- a9: r = sqrt(sum of squared residual rows), c_1
+            double r2 = 0.0, c1 = 0.0;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (ok[r]) {
+                    float rq = v2v[r] * fvv[r] * fvv[r] + a2v[r] * faa[r] * faa[r];
+                    if (p.use_bounds) {
+#pragma unroll
+                        for (int ax = 0; ax < DIMS; ++ax) {
+                            const float hi = fmaxf(0.f, pos[r][ax] - smax[ax]);
+                            const float lo = fmaxf(0.f, smin[ax] - pos[r][ax]);
+                            rq = fmaf(hi, hi, fmaf(lo, lo, rq));
+                        }
+                    }
+                    r2 += double(rq) + double(so[r][0]);
+                    c1 += double(point_cost<float, DIMS>(p.cost, pos[r], vel[r], acc[r], a2v[r]));
+                }
+            }
+            r2 = seg_sum(r2, lane, send);
+            c1 = seg_sum(c1, lane, send);
+            if (head) {
+                double *dst = sPart2 + (size_t(sc) * L.maxw + (warp - fw)) * 2;
+                dst[0] = r2;
+                dst[1] = c1;
+            }
+            break;
+        }
+        // ---- C: this thread's share of g on the free columns, reduced per sample
+        float g[DIMS][NF];
+#pragma unroll
+        for (int ax = 0; ax < DIMS; ++ax) {
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const float2 rp = make_float2(so[2 * h][ax] + rb[2 * h][ax], so[2 * h + 1][ax] + rb[2 * h + 1][ax]);
+                    const float2 r1 = make_float2(rv[2 * h][ax], rv[2 * h + 1][ax]);
+                    const float2 r2v = make_float2(ra[2 * h][ax], ra[2 * h + 1][ax]);
+                    acc2 = ffma2(bf[0][f][h], rp, ffma2(bf[1][f][h], r1, ffma2(bf[2][f][h], r2v, acc2)));
+                }
+                g[ax][f] = seg_sum(acc2.x + acc2.y, lane, send);
+            }
+        }
+        if constexpr (WL) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int ax = 0; ax < DIMS; ++ax) {
+                    rsum[r][0][ax] += so[r][ax] + rb[r][ax];
+                    rsum[r][1][ax] += rv[r][ax];
+                    rsum[r][2][ax] += ra[r][ax];
+                }
+        }
+        if (head) {
+            float *dst = sPart + (size_t(sc) * L.maxw + (warp - fw)) * PD;
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) dst[ax * nv + kFree0 + f] = g[ax][f];
+        }
+        __syncthreads();
+        // ---- D: multiplier step (eq. lag) and shared-inverse step, one lane per
+        //      (sample, axis, free column); groups of NF lanes never straddle a warp
+        {
+            constexpr int GPW = 32 / NF;
+            const int f = lane - (lane / NF) * NF;
+            for (int vw = warp; vw * GPW < S_act * DIMS; vw += T >> 5) {  // uniform per warp
+                const int gi = vw * GPW + lane / NF;
+                const bool dact = lane < GPW * NF && gi < S_act * DIMS;
+                const int ss = dact ? gi / DIMS : 0, ax = dact ? gi - ss * DIMS : 0, ro = ss * DIMS + ax;
+                float cv = 0.f, lnew = 0.f;
+                if (dact) {
+                    const int nw = (((ss + 1) * TPS - 1) >> 5) - ((ss * TPS) >> 5) + 1;
+                    float gs = 0.f;
+                    for (int w = 0; w < nw; ++w) gs += sPart[(size_t(ss) * L.maxw + w) * PD + ax * nv + kFree0 + f];
+                    cv = sCd[ro * CDS + 2 * f];
+                    lnew = sLam[ro * 8 + f] - rho * gs;
+                    sU[ro * 8 + f] = sXi[ro * 8 + f] + lnew - rho * gs - cv;
+                }
+                __syncwarp();
+                if (dact) {
+                    float du = 0.f;
+#pragma unroll
+                    for (int fi = 0; fi < NF; ++fi) du = fmaf(sW[f * NF + fi], sU[ro * 8 + fi], du);
+                    sLam[ro * 8 + f] = lnew;
+                    sCd[ro * CDS + 2 * f] = cv + du;
+                    sCd[ro * CDS + 2 * f + 1] = cv + du;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- fixed-column multipliers: P_B^T of the summed residual rows
+    if constexpr (WL) {
+        const float *bas = p.tab + p.lay.basis;
+        for (int cb = 0; cb < NB; ++cb) {
+            const int col = cb < kFree0 ? cb : cb + NF;
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax) {
+                float v = 0.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (ok[r]) {
+                        const int t = j + TPS * r;
+                        v = fmaf(bas[(size_t(0) * np_ + t) * nv + col], rsum[r][0][ax],
+                                 fmaf(bas[(size_t(1) * np_ + t) * nv + col], rsum[r][1][ax],
+                                      fmaf(bas[(size_t(2) * np_ + t) * nv + col], rsum[r][2][ax], v)));
+                    }
+                }
+                v = seg_sum(v, lane, send);
+                if (head) sPart[(size_t(sc) * L.maxw + (warp - fw)) * PD + ax * nv + col] = v;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- outputs: r, c_1; xi_bar (boundary coefficients from the closed form), lambda
+    for (int ss = tid; ss < S_act; ss += T) {
+        const int nw = (((ss + 1) * TPS - 1) >> 5) - ((ss * TPS) >> 5) + 1;
+        double r2 = 0.0, c1 = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            r2 += sPart2[(size_t(ss) * L.maxw + w) * 2];
+            c1 += sPart2[(size_t(ss) * L.maxw + w) * 2 + 1];
+        }
+        p.r_out[s0 + ss] = sqrt(r2);
+        p.c1_out[s0 + ss] = c1;
+    }
+    for (int e = tid; e < S_act * D; e += T) {
+        const int ss = e / D, d = e - ss * D;
+        const int ax = d / nv, cl = d - ax * nv, f = cl - kFree0;
+        const size_t gi = size_t(s0 + ss) * D + d;
+        const int ro = ss * DIMS + ax;
+        const bool free_col = f >= 0 && f < NF;
+        p.xi_bar[gi] = free_col ? double(sCd[ro * CDS + 2 * f]) : p.cB[ax * kMaxNv + cl];
+        if (p.lam_out) {
+            float lv;
+            if (free_col) {
+                lv = sLam[ro * 8 + f];
+            } else {
+                float gsum = 0.f;
+                if constexpr (WL) {
+                    const int nw = (((ss + 1) * TPS - 1) >> 5) - ((ss * TPS) >> 5) + 1;
+                    for (int w = 0; w < nw; ++w) gsum += sPart[(size_t(ss) * L.maxw + w) * PD + ax * nv + cl];
+                }
+                lv = (p.lam_in ? float(p.lam_in[gi]) : 0.f) - rho * gsum;
+            }
+            p.lam_out[gi] = double(lv);
+        }
+    }
+}
+
+// Largest CTA of each variant: more points per thread need more registers.
+template <int R>
+constexpr int pts_max_threads() { return R <= 2 ? 512 : 256; }
+
+template <int DIMS, int R, int NF, bool WL>
+__global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const ProjParams<float> p)
+{
+    pts_body<DIMS, R, NF, WL>(p, blockIdx.x * p.S);
+}
+
+}  // namespace pts
+}  // namespace priest
