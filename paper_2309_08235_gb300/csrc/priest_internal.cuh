@@ -223,6 +223,7 @@ struct Tiling {
 
 // FP32 point-owner kernel (project_pts.cu): degree 10 with 5 free coefficients.
 bool pts_supported(const Shape &sh);
+bool pts_span_ok(const Shape &sh, int R);
 size_t pts_smem_bytes(const Shape &sh, int S, int R);
 int pts_threads(const Shape &sh, int S, int R);
 int pts_max_threads(int R);

@@ -68,12 +68,14 @@ Tiling pts_tiling(const Shape &sh, int S, int R)
     t.ws = 0;
     t.threads = pts_threads(sh, S, R);
     t.smem = pts_smem_bytes(sh, S, R);
-    if (t.threads > pts_max_threads(R) || t.smem > kSmemCap) t.smem = 0;
+    if (t.threads > pts_max_threads(R) || t.smem > kSmemCap || !pts_span_ok(sh, R)) t.smem = 0;
     return t;
 }
 
-// Point-owner candidates: two or four points per thread, the samples of one
-// wave over the SMs (or the most that fit one CTA), and half that.
+// Point-owner candidates: two or four points per thread; the samples of one
+// wave over the SMs in one CTA (or the most that fit one CTA), half that, and
+// one to three samples per CTA (several CTAs per SM, whose phases then
+// overlap).
 std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
 {
     std::vector<Tiling> out;
@@ -82,9 +84,11 @@ std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
         const int tps = (sh.n_p + R - 1) / R;
         const int s_max = std::max(1, pts_max_threads(R) / tps);
         const int s1 = std::min(s_max, std::max(1, (n_samples + n_sm - 1) / n_sm));
-        const int s2 = (s1 + 1) / 2;
-        for (int S : {s1, s2}) {
-            if (S == s2 && s2 == s1) continue;
+        std::vector<int> ss = {s1, (s1 + 1) / 2, 1, 2, 3};
+        std::sort(ss.begin(), ss.end());
+        ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
+        for (int S : ss) {
+            if (S > s1) continue;
             const Tiling t = pts_tiling(sh, S, R);
             if (t.smem > 0) out.push_back(t);
         }
@@ -98,7 +102,7 @@ std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm)
 {
-    if (sizeof(Real) == 4 && pts_supported(sh)) {
+    if (sizeof(Real) == 4 && pts_supported(sh) && pts_span_ok(sh, 2)) {
         const int tps = (sh.n_p + 1) / 2;
         const int S = std::min(std::max(1, pts_max_threads(2) / tps), std::max(1, (n_samples + n_sm - 1) / n_sm));
         const Tiling p = pts_tiling(sh, S, 2);

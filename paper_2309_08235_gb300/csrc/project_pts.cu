@@ -16,6 +16,12 @@ int pts_max_threads(int R) { return R <= 2 ? pts::pts_max_threads<2>() : pts::pt
 
 bool pts_supported(const Shape &sh) { return sh.nf == 5 && sh.nv == 11 && (sh.dims == 2 || sh.dims == 3); }
 
+// Every sample a warp touches needs dims * nf state lanes in that warp.
+bool pts_span_ok(const Shape &sh, int R)
+{
+    return pts::pts_span(pts::pts_tps(sh.n_p, R)) * sh.dims * sh.nf <= 32;
+}
+
 namespace {
 
 template <int DIMS, int R, bool WL>
@@ -43,6 +49,7 @@ cudaError_t launch_project_pts(const ProjParams<float> &p, const Tiling &t, cuda
     if (p.nf != 5 || p.nv != 11) return cudaErrorInvalidValue;
     const int tps = pts::pts_tps(p.n_p, t.R);
     if (t.S * tps > t.threads || t.threads % 32 != 0 || t.threads > pts_max_threads(t.R)) return cudaErrorInvalidValue;
+    if (pts::pts_span(tps) * p.dims * p.nf > 32) return cudaErrorInvalidValue;
     if (p.dims == 2) {
         if (t.R == 2) return launch_pts_wl<2, 2>(p, t, st);
         if (t.R == 4) return launch_pts_wl<2, 4>(p, t, st);

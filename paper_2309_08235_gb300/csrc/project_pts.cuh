@@ -20,9 +20,14 @@
 //     it over the sample's threads with a segmented warp reduction (a warp may
 //     hold the end of one sample and the start of the next), one partial per
 //     (sample, warp) in shared memory, summed in a fixed order;
-//   * phase D: one lane per (sample, axis, free column) applies the multiplier
-//     and shared-inverse steps.
-// Two CTA barriers per iteration.  The multipliers of the fixed columns
+//   * phase D: every warp holds, for each sample it touches, the free
+//     coefficients c, multipliers lambda_F and sample xi_F in registers of
+//     dims * nf "state lanes" (one per axis and free column); after the single
+//     CTA barrier of the iteration those lanes read their sample's partial
+//     sums, apply the multiplier and shared-inverse steps (the W products by
+//     warp shuffles), and the warp's threads take the new c by shuffles.
+//     Warps sharing a sample repeat the same arithmetic, so they agree.
+// One CTA barrier per iteration.  The multipliers of the fixed columns
 // (returned only on request) follow from the linearity of eq. lag:
 // lambda_B^K = lambda_B^0 - rho P_B^T sum_k r^k, so the per-point residual rows
 // are summed over the iterations and reduced once at the end.
@@ -44,15 +49,21 @@ using detail::kFull;
 //   mrec  [nm2][12 | 16]    moving pairs (layout of project_kernel.cuh)
 //   W     [nf][nf]
 //   cd    [S][dims][cds]    free coefficients, each stored twice (c_f, c_f)
-//   lam, xi, u [S][dims][8] multipliers, sample, shared-inverse argument (free columns)
-//   part  [S][maxw][dims*nv] per-(sample, warp) partial sums
+//   lam, xi, u [S][dims][8] multipliers, sample (free columns; set-up and output only)
+//   part  [2][S][maxw][dims*nv] per-(sample, warp) partial sums, double-buffered by
+//                           iteration parity
 //   part2 [S][maxw][2]      (doubles) residual / cost partials of the final pass
 struct PtsLayout {
     int tps, nq, nm2, maxw, cds;
-    size_t obs, srec, mrec, W, cd, lam, xi, u, part, part2, total;
+    size_t obs, srec, mrec, W, cd, lam, xi, part, part2, total;
 };
 
 __host__ __device__ inline int pts_tps(int n_p, int R) { return (n_p + R - 1) / R; }
+
+// Most samples one warp can touch (its 32 consecutive threads cover TPS-thread
+// blocks); every warp keeps the multiplier and coefficient state of each of
+// its samples in dims * nf lanes, so dims * nf * span must fit in 32 lanes.
+__host__ __device__ inline int pts_span(int tps) { return (31 + tps - 1) / tps + 1; }
 
 __host__ __device__ inline PtsLayout pts_layout(int dims, int nf, int nv, int n_p, int n_obs, int n_static, int S,
                                                 int R)
@@ -78,10 +89,8 @@ __host__ __device__ inline PtsLayout pts_layout(int dims, int nf, int nv, int n_
     o = align8(o + size_t(S) * dims * 8);
     L.xi = o;
     o = align8(o + size_t(S) * dims * 8);
-    L.u = o;
-    o = align8(o + size_t(S) * dims * 8);
     L.part = o;
-    o = align8(o + size_t(S) * L.maxw * dims * nv);
+    o = align8(o + size_t(2) * S * L.maxw * dims * nv);
     L.part2 = o;
     o = align8(o + size_t(S) * L.maxw * 4);
     L.total = o;
@@ -100,6 +109,23 @@ __device__ __forceinline__ T seg_sum(T v, int lane, int send)
         if (lane + d <= send) v += o;
     }
     return v;
+}
+
+// The same for N values at once, step by step across the values so the
+// shuffles of one step are independent of each other.
+template <int N>
+__device__ __forceinline__ void seg_sum_n(float (&v)[N], int lane, int send)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        float o[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) o[i] = __shfl_down_sync(kFull, v[i], d);
+        if (lane + d <= send) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) v[i] += o[i];
+        }
+    }
 }
 
 // Residual contribution of an active pair into registers (the arithmetic of
@@ -327,7 +353,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
     const int send = act ? min(31, (sc + 1) * TPS - 1 - 32 * warp) : 31;
     const bool head = act && (lane == 0 || j == 0);
     float *sObs = sm + L.obs, *sW = sm + L.W, *sCd = sm + L.cd, *sLam = sm + L.lam, *sXi = sm + L.xi,
-          *sU = sm + L.u, *sPart = sm + L.part;
+          *sPart = sm + L.part;
     double *sPart2 = reinterpret_cast<double *>(sm + L.part2);
     const float rho = p.rho, vmax = p.vmax, amax = p.amax, vmax2 = vmax * vmax, amax2 = amax * amax;
 
@@ -448,6 +474,26 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
         smin[ax] = p.smin[ax] - p.tab[p.lay.origin + ax];
         smax[ax] = p.smax[ax] - p.tab[p.lay.origin + ax];
     }
+    // state lanes: lane = q * DIMS * NF + ax * NF + f serves the warp's q-th
+    // sample (sw0 + q), axis ax, free column f
+    constexpr int SL = DIMS * NF;
+    const int sw0 = (32 * warp) / TPS;               // first sample the warp touches
+    const int dq = lane / SL, dax = (lane % SL) / NF, df = lane % NF;
+    const int ds = sw0 + dq;
+    const bool dact = lane < (32 / SL) * SL && ds < S_act && ds * TPS < 32 * (warp + 1);
+    float stC = 0.f, stLam = 0.f, stXi = 0.f, wrow[NF];
+    {
+        const int ro = (dact ? ds : 0) * DIMS + dax;
+        if (dact) {
+            stC = sCd[ro * CDS + 2 * df];
+            stLam = sLam[ro * 8 + df];
+            stXi = sXi[ro * 8 + df];
+        }
+#pragma unroll
+        for (int fi = 0; fi < NF; ++fi) wrow[fi] = sW[df * NF + fi];
+    }
+    // the state lane holding (my sample, axis, column 0)
+    const int cbase = act ? (sc - sw0) * SL : 0;
     float rsum[WL ? R : 1][3][DIMS];  // WL: per-point residual rows summed over the iterations
 #pragma unroll
     for (int r = 0; r < (WL ? R : 1); ++r)
@@ -461,16 +507,16 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
         // ---- A: trajectory (pairs of points share one f32x2 FMA per term)
         float pos[R][DIMS], vel[R][DIMS], acc[R][DIMS];
         {
-            const float *cds = sCd + sc * DIMS * CDS;
+            float cfs[DIMS][NF];
+#pragma unroll
+            for (int ax = 0; ax < DIMS; ++ax)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) cfs[ax][f] = __shfl_sync(kFull, stC, (cbase + ax * NF + f) & 31);
 #pragma unroll
             for (int ax = 0; ax < DIMS; ++ax) {
                 float2 cf[NF];
 #pragma unroll
-                for (int f = 0; f < NF; f += 2) {
-                    const float4 c4 = *reinterpret_cast<const float4 *>(cds + ax * CDS + 2 * f);
-                    cf[f] = make_float2(c4.x, c4.y);
-                    if (f + 1 < NF) cf[f + 1] = make_float2(c4.z, c4.w);
-                }
+                for (int f = 0; f < NF; ++f) cf[f] = make_float2(cfs[ax][f], cfs[ax][f]);
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
                     float2 P2 = bs[0][ax][h], V2 = bs[1][ax][h], A2 = bs[2][ax][h];
@@ -560,7 +606,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
             break;
         }
         // ---- C: this thread's share of g on the free columns, reduced per sample
-        float g[DIMS][NF];
+        float g[DIMS * NF];
 #pragma unroll
         for (int ax = 0; ax < DIMS; ++ax) {
 #pragma unroll
@@ -573,9 +619,10 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                     const float2 r2v = make_float2(ra[2 * h][ax], ra[2 * h + 1][ax]);
                     acc2 = ffma2(bf[0][f][h], rp, ffma2(bf[1][f][h], r1, ffma2(bf[2][f][h], r2v, acc2)));
                 }
-                g[ax][f] = seg_sum(acc2.x + acc2.y, lane, send);
+                g[ax * NF + f] = acc2.x + acc2.y;
             }
         }
+        seg_sum_n<DIMS * NF>(g, lane, send);
         if constexpr (WL) {
 #pragma unroll
             for (int r = 0; r < R; ++r)
@@ -586,44 +633,35 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                     rsum[r][2][ax] += ra[r][ax];
                 }
         }
+        float *part = sPart + size_t(k & 1) * S * L.maxw * PD;
         if (head) {
-            float *dst = sPart + (size_t(sc) * L.maxw + (warp - fw)) * PD;
+            float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD;
 #pragma unroll
             for (int ax = 0; ax < DIMS; ++ax)
 #pragma unroll
-                for (int f = 0; f < NF; ++f) dst[ax * nv + kFree0 + f] = g[ax][f];
+                for (int f = 0; f < NF; ++f) dst[ax * nv + kFree0 + f] = g[ax * NF + f];
         }
         __syncthreads();
-        // ---- D: multiplier step (eq. lag) and shared-inverse step, one lane per
-        //      (sample, axis, free column); groups of NF lanes never straddle a warp
+        // ---- D: multiplier step (eq. lag) and shared-inverse step in the state
+        //      lanes: lambda^{k+1} = lambda^k - rho g, u = xi + lambda^{k+1} - rho g - c,
+        //      c += W u (the u of the lane's sample and axis gathered by shuffles)
         {
-            constexpr int GPW = 32 / NF;
-            const int f = lane - (lane / NF) * NF;
-            for (int vw = warp; vw * GPW < S_act * DIMS; vw += T >> 5) {  // uniform per warp
-                const int gi = vw * GPW + lane / NF;
-                const bool dact = lane < GPW * NF && gi < S_act * DIMS;
-                const int ss = dact ? gi / DIMS : 0, ax = dact ? gi - ss * DIMS : 0, ro = ss * DIMS + ax;
-                float cv = 0.f, lnew = 0.f;
-                if (dact) {
-                    const int nw = (((ss + 1) * TPS - 1) >> 5) - ((ss * TPS) >> 5) + 1;
-                    float gs = 0.f;
-                    for (int w = 0; w < nw; ++w) gs += sPart[(size_t(ss) * L.maxw + w) * PD + ax * nv + kFree0 + f];
-                    cv = sCd[ro * CDS + 2 * f];
-                    lnew = sLam[ro * 8 + f] - rho * gs;
-                    sU[ro * 8 + f] = sXi[ro * 8 + f] + lnew - rho * gs - cv;
-                }
-                __syncwarp();
-                if (dact) {
-                    float du = 0.f;
+            float gs = 0.f;
+            if (dact) {
+                const int nw = (((ds + 1) * TPS - 1) >> 5) - ((ds * TPS) >> 5) + 1;
+                for (int w = 0; w < nw; ++w) gs += part[(size_t(ds) * L.maxw + w) * PD + dax * nv + kFree0 + df];
+            }
+            const float lnew = stLam - rho * gs;
+            const float u = stXi + lnew - rho * gs - stC;
+            const int ub = lane - df;  // lane of (sample, axis, column 0)
+            float du = 0.f;
 #pragma unroll
-                    for (int fi = 0; fi < NF; ++fi) du = fmaf(sW[f * NF + fi], sU[ro * 8 + fi], du);
-                    sLam[ro * 8 + f] = lnew;
-                    sCd[ro * CDS + 2 * f] = cv + du;
-                    sCd[ro * CDS + 2 * f + 1] = cv + du;
-                }
+            for (int fi = 0; fi < NF; ++fi) du = fmaf(wrow[fi], __shfl_sync(kFull, u, (ub + fi) & 31), du);
+            if (dact) {
+                stLam = lnew;
+                stC = stC + du;
             }
         }
-        __syncthreads();
     }
 
     // ---- fixed-column multipliers: P_B^T of the summed residual rows
@@ -644,9 +682,15 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                     }
                 }
                 v = seg_sum(v, lane, send);
-                if (head) sPart[(size_t(sc) * L.maxw + (warp - fw)) * PD + ax * nv + col] = v;
+                if (head) sPart[(size_t(p.K & 1) * S * L.maxw + size_t(sc) * L.maxw + (warp - fw)) * PD + ax * nv + col] = v;
             }
         }
+    }
+    // free coefficients and multipliers of each sample from its first warp's state lanes
+    if (dact && (ds * TPS) >> 5 == warp) {
+        const int ro = ds * DIMS + dax;
+        sCd[ro * CDS + 2 * df] = stC;
+        sLam[ro * 8 + df] = stLam;
     }
     __syncthreads();
     // ---- outputs: r, c_1; xi_bar (boundary coefficients from the closed form), lambda
@@ -675,7 +719,8 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                 float gsum = 0.f;
                 if constexpr (WL) {
                     const int nw = (((ss + 1) * TPS - 1) >> 5) - ((ss * TPS) >> 5) + 1;
-                    for (int w = 0; w < nw; ++w) gsum += sPart[(size_t(ss) * L.maxw + w) * PD + ax * nv + cl];
+                    for (int w = 0; w < nw; ++w)
+                        gsum += sPart[(size_t(p.K & 1) * S * L.maxw + size_t(ss) * L.maxw + w) * PD + ax * nv + cl];
                 }
                 lv = (p.lam_in ? float(p.lam_in[gi]) : 0.f) - rho * gsum;
             }
@@ -686,7 +731,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
 
 // Largest CTA of each variant: more points per thread need more registers.
 template <int R>
-constexpr int pts_max_threads() { return R <= 2 ? 512 : 256; }
+constexpr int pts_max_threads() { return R <= 2 ? 384 : 256; }
 
 template <int DIMS, int R, int NF, bool WL>
 __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const ProjParams<float> p)
