@@ -511,8 +511,9 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
     }
     std::vector<Tiling> cands = tiling_candidates<Real>(sh, N, ctx->n_sm);
     cands.push_back(model);
-    // marginal cost per iteration: time K = 2 and K = 10 and take the difference
-    const int k_lo = 2, k_hi = 10;
+    // marginal cost per iteration: the fastest of two launches at K = 2 and at
+    // K = 22, differenced (a warm-up launch first)
+    const int k_lo = 2, k_hi = 22;
     p.lam_out = nullptr;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -526,8 +527,9 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
         p.WS = t.ws;
         float t_k[2] = {1e30f, 1e30f};
         bool ok = true;
-        for (int rep = 0; rep < 3 && ok; ++rep) {
-            p.K = (rep == 0 || rep == 1) ? k_lo : k_hi;  // rep 0 warms up
+        for (int rep = 0; rep < 5 && ok; ++rep) {
+            const int slot = rep == 0 ? -1 : (rep - 1) & 1;  // rep 0 warms up
+            p.K = slot == 1 ? k_hi : k_lo;
             cudaEventRecord(e0, st);
             cudaError_t e = launch_project<Real>(p, t, st);
             cudaEventRecord(e1, st);
@@ -539,9 +541,10 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
             }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) t_k[rep - 1] = ms;
+            if (slot >= 0) t_k[slot] = std::min(t_k[slot], ms);
         }
-        const float ms = ok ? (t_k[1] - t_k[0]) / float(k_hi - k_lo) : 1e30f;
+        float ms = ok ? (t_k[1] - t_k[0]) / float(k_hi - k_lo) : 1e30f;
+        if (!(ms > 0.f)) ms = ok ? t_k[1] / float(k_hi + 1) : 1e30f;  // timing noise: fall back to the plain ratio
         if (const char *lv = getenv("PRIEST_AUTOTUNE_LOG"))
             if (atoi(lv) >= 2)
                 fprintf(stderr, "priest autotune candidate: kind=%d S=%d C=%d R=%d threads=%d ws=%d smem=%zu -> %.2f us / iteration\n",

@@ -201,27 +201,72 @@ __device__ __forceinline__ void quad_values(const float *q, float2 xd, float2 yd
     }
 }
 
-// Quads [k0, k0 + nb): exact tests of the flagged points' candidates, in
-// obstacle order.
-template <int DIMS, int R>
-__device__ __forceinline__ void quad_rescan(const float *rec, const float *sObs, int k0, int nb,
-                                            const detail::PackedPoints<DIMS, R> &P, const float (&m)[R], bool fin,
-                                            float (&so)[R][DIMS])
+// Contribution of static obstacle j to one point (zero when the exact test
+// fails): x - e (or its squared norm in the final pass) as in active_add.
+template <int DIMS>
+__device__ __forceinline__ float3 static_contrib(const float *sObs, int j, float x, float y, float z, bool fin)
+{
+    float so[DIMS];
+#pragma unroll
+    for (int ax = 0; ax < DIMS; ++ax) so[ax] = 0.f;
+    exact_static<DIMS>(sObs, j, x, y, z, fin, so);
+    return make_float3(so[0], so[1], DIMS == 3 ? so[DIMS - 1] : 0.f);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ T pick(const T (&a)[R], int r)
+{
+    T v = a[0];
+#pragma unroll
+    for (int i = 1; i < R; ++i)
+        if (r == i) v = a[i];
+    return v;
+}
+
+// Exact tests of the candidates of a batch of quads [k, k + NB): bit r * NB + i
+// of `cand` flags point r against quad k + i.  Candidates are visited point by
+// point in obstacle order; the four obstacles of a flagged quad are
+// re-evaluated with the same operations and the ones below the threshold
+// tested exactly.
+template <int DIMS, int R, int NB>
+__device__ __forceinline__ void quad_candidates(unsigned cand, const float *srec, const float *sObs, int k,
+                                                const detail::PackedPoints<DIMS, R> &P, bool fin,
+                                                float (&so)[R][DIMS])
 {
     constexpr int QS = DIMS == 2 ? 12 : 20;
+    while (cand) {
+        const int bit = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int r = bit / NB, i = bit - r * NB;
+        const float2 xd = pick(P.x, r), yd = pick(P.y, r), zd = pick(P.z, r), zzd = pick(P.zz, r);
+        const float npq = pick(P.npq, r);
+        float2 v01, v23;
+        quad_values<DIMS>(srec + size_t(k + i) * QS, xd, yd, zd, zzd, v01, v23);
+        unsigned hb = (v01.x < npq ? 1u : 0u) | (v01.y < npq ? 2u : 0u) | (v23.x < npq ? 4u : 0u) |
+                      (v23.y < npq ? 8u : 0u);
+        while (hb) {
+            const int h = __ffs(hb) - 1;
+            hb &= hb - 1;
+            const float3 c = static_contrib<DIMS>(sObs, 4 * (k + i) + h, xd.x, yd.x, zd.x, fin);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (m[r] < P.npq[r]) {
-            for (int b = k0; b < k0 + nb; ++b) {
-                float2 v01, v23;
-                quad_values<DIMS>(rec + size_t(b) * QS, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
-                const float vv[4] = {v01.x, v01.y, v23.x, v23.y};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (vv[i] < P.npq[r]) exact_static<DIMS>(sObs, 4 * b + i, P.x[r].x, P.y[r].x, P.z[r].x, fin, so[r]);
+            for (int rr = 0; rr < R; ++rr) {
+                if (rr == r) {
+                    so[rr][0] += c.x;
+                    so[rr][1] += c.y;
+                    if constexpr (DIMS == 3) so[rr][DIMS - 1] += c.z;
+                }
             }
         }
     }
+}
+
+// Per-point minimum of the pre-filter values over one quad.
+template <int DIMS>
+__device__ __forceinline__ float quad_min(const float *q, float2 xd, float2 yd, float2 zd, float2 zzd)
+{
+    float2 v01, v23;
+    quad_values<DIMS>(q, xd, yd, zd, zzd, v01, v23);
+    return fmin3(v01.x, v01.y, fminf(v23.x, v23.y));
 }
 
 template <int DIMS, int R>
@@ -253,50 +298,52 @@ __device__ __forceinline__ void moving_rescan(const float *rec, const float *sOb
 }
 
 // Every obstacle against the thread's R points; all lanes of the CTA run the
-// same trip counts, so the votes use the full warp.
+// same trip counts, so the votes use the full warp.  Static quads go in
+// batches of NQB: one minimum per (point, quad) kept in registers, their
+// minimum per point and one vote; when it fires, the (point, quad) candidate
+// bits come from the kept minima and the candidates are tested exactly.
 template <int DIMS, int R, int NQB>
 __device__ __forceinline__ void all_pairs(const float *srec, const float *mrec, const float *sObs, int nq, int nm2,
                                           int ns, const detail::PackedPoints<DIMS, R> &P, bool fin,
                                           float (&so)[R][DIMS])
 {
+    static_assert(R * NQB <= 32, "candidate bits");
     constexpr int QS = DIMS == 2 ? 12 : 20;
     constexpr int RM = DIMS == 2 ? 12 : 16;
     int k = 0;
     for (; k + NQB <= nq; k += NQB) {
-        float m[R];
+        // screening: one minimum per (point, quad), their minimum per point, one vote
+        float mq[R][NQB];
 #pragma unroll
-        for (int b = 0; b < NQB; ++b) {
-            const float *q = srec + size_t(k + b) * QS;
+        for (int i = 0; i < NQB; ++i) {
+            const float *q = srec + size_t(k + i) * QS;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 v01, v23;
-                quad_values<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
-                const float m01 = (b == 0) ? fminf(v01.x, v01.y) : fmin3(m[r], v01.x, v01.y);
-                m[r] = fmin3(m01, v23.x, v23.y);
-            }
+            for (int r = 0; r < R; ++r) mq[r][i] = quad_min<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r]);
         }
         bool f = false;
 #pragma unroll
-        for (int r = 0; r < R; ++r) f |= m[r] < P.npq[r];
-        if (__any_sync(kFull, f)) quad_rescan<DIMS, R>(srec, sObs, k, NQB, P, m, fin, so);
+        for (int r = 0; r < R; ++r) {
+            float m = mq[r][0];
+#pragma unroll
+            for (int i = 1; i < NQB; i += 2) m = (i + 1 < NQB) ? fmin3(m, mq[r][i], mq[r][i + 1]) : fminf(m, mq[r][i]);
+            f |= m < P.npq[r];
+        }
+        if (__any_sync(kFull, f)) {
+            // (point, quad) candidate bits of the batch, then the exact tests
+            unsigned cand = 0u;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int i = 0; i < NQB; ++i) cand |= (mq[r][i] < P.npq[r] ? 1u : 0u) << (r * NQB + i);
+            quad_candidates<DIMS, R, NQB>(cand, srec, sObs, k, P, fin, so);
+        }
     }
-    if (k < nq) {
-        float m[R];
+    for (; k < nq; ++k) {
+        unsigned cand = 0u;
 #pragma unroll
-        for (int r = 0; r < R; ++r) m[r] = INFINITY;
-        for (int b = k; b < nq; ++b) {
-            const float *q = srec + size_t(b) * QS;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 v01, v23;
-                quad_values<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
-                m[r] = fmin3(fmin3(m[r], v01.x, v01.y), v23.x, v23.y);
-            }
-        }
-        bool f = false;
-#pragma unroll
-        for (int r = 0; r < R; ++r) f |= m[r] < P.npq[r];
-        if (__any_sync(kFull, f)) quad_rescan<DIMS, R>(srec, sObs, k, nq - k, P, m, fin, so);
+        for (int r = 0; r < R; ++r)
+            cand |= (quad_min<DIMS>(srec + size_t(k) * QS, P.x[r], P.y[r], P.z[r], P.zz[r]) < P.npq[r] ? 1u : 0u) << r;
+        if (__any_sync(kFull, cand != 0u)) quad_candidates<DIMS, R, 1>(cand, srec, sObs, k, P, fin, so);
     }
     // moving obstacles: the batch minimum is the exact squared scaled distance
     constexpr int NPM = 2;
@@ -575,7 +622,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
 #pragma unroll
                 for (int ax = 0; ax < DIMS; ++ax) so[r][ax] = 0.f;
             }
-            all_pairs<DIMS, R, 2>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
+            all_pairs<DIMS, R, (DIMS == 3 ? 2 : 4)>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
         }
         if (fin) {
             // ---- a9: r = sqrt(sum of squared residual rows), c_1
