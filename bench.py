@@ -66,16 +66,31 @@ def workload_desc(p, cem, precision="fp32", name="clutter2d"):
 
 
 def flops_per_sample_iter(p, nf=5):
-    """Algorithmic FP32 flops of one projected sample-iteration (FMA = 2):
-    7 per (point, obstacle) pair (2 differences, scaled squared distance,
-    activity test; the work of the rare active pairs is not counted), plus per
-    point the trajectory evaluation and the transposed basis product on the
-    free coefficients (2 x 3 x dims x nf FMA) and the velocity / acceleration
-    tests (~10), plus the shared-inverse step (2 nf^2 FMA per axis)."""
+    """Algorithmic FP32 flops of one projected sample-iteration, the per-unit
+    figure of the hot-path scope: per (point, obstacle) pair the direct polar
+    test (offset, scaled squared distance, activity test: 14 flops in 2-D, 22
+    in 3-D; the rare active pairs' rsqrt is not counted), the velocity /
+    acceleration blocks (12 flops per point and block), the two basis products
+    of the affine map over all n_v columns (2 x dims x 2 x 3 n_p n_v) and the
+    shared-inverse step (2 x dims x n_v^2)."""
     dims, n_p, n_o = p["dims"], p["n_p"], p["n_obs"]
-    pair = 7 if dims == 2 else 11
-    per_point = 2 * (2 * 3 * dims * nf) + 10
-    return n_p * n_o * pair + n_p * per_point + dims * 2 * 2 * nf * nf
+    nv = p.get("degree", 10) + 1
+    pair = 14 if dims == 2 else 22
+    return n_p * n_o * pair + 2 * n_p * 12 + 2 * dims * (2 * 3 * n_p * nv) + 2 * dims * nv * nv
+
+
+def fma_pipe_flops_per_sample_iter(p, nf=5):
+    """FP32 flops the kernel itself issues per projected sample-iteration on
+    the FMA pipe (FMA = 2): the expanded pre-filter (2 FMA per static pair,
+    4 in 3-D), the moving-obstacle scaled offsets (6 FMA per pair, 9 in 3-D),
+    the trajectory and transposed products on the nf free columns (2 x 3 x
+    dims x nf FMA per point), ~10 per point for the velocity / acceleration
+    blocks and the shared-inverse step (dims x nf^2 FMA)."""
+    dims, n_p, n_o = p["dims"], p["n_p"], p["n_obs"]
+    n_mov = int(np.count_nonzero(np.abs(np.asarray(p["vel"])).sum(1))) if n_o else 0
+    st, mv = (4, 12) if dims == 2 else (8, 18)
+    return (n_p * ((n_o - n_mov) * st + n_mov * mv) + n_p * (2 * (2 * 3 * dims * nf) + 10)
+            + 2 * dims * nf * nf)
 
 
 def fp32_peak_tflops():
@@ -259,19 +274,25 @@ def run_ours(args):
     flops_launch = flops_per_sample_iter(p) * N * K
     achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
     peak = fp32_peak_tflops()
+    pipe_tflops = fma_pipe_flops_per_sample_iter(p) * N * K / (avg_proj_ms / 1e3) / 1e12
     traffic = None
     prof_path = os.path.join(ROOT, "profiles", "traffic.txt")
-    kname = ("project_kernel (FP32, %d-D)" % p["dims"] if args.precision == "fp32" else
+    kname = ("pts_kernel (FP32 point-owner projection, %d-D)" % p["dims"] if args.precision == "fp32" else
              "project_tc_kernel (tcgen05 pair tests, %d-D)" % p["dims"])
-    if os.path.exists(prof_path) and args.precision == "fp32" and p["dims"] == 2:
+    if os.path.exists(prof_path) and args.precision == "fp32" and p["dims"] == 2 and args.workload == "clutter2d":
         for ln in open(prof_path):
-            if ln.startswith("project_kernel_bytes_per_launch:"):
+            if ln.startswith("pts_kernel_bytes_per_launch:"):
                 traffic = int(ln.split(":", 1)[1])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
                 "flops_per_launch": flops_launch,
-                "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
+                "flops_note": "algorithmic: direct polar pair test 14 (2-D) / 22 (3-D) flops per pair, "
+                              "vel/acc blocks, both basis products over all n_v columns, shared-inverse step",
+                "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+                "fma_pipe": {"achieved": pipe_tflops, "frac": pipe_tflops / peak,
+                             "note": "flops the kernel issues on the FMA pipe (expanded 2-FMA pair pre-filter, "
+                                     "free-column basis products)"}}
 
     # ---- end to end through the host-pointer C ABI (pinned z in, result out)
     res = P.priest_result()

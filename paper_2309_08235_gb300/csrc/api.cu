@@ -40,6 +40,7 @@ struct BatchPlan {
     int2 *items_dev = nullptr;
     int *counters_dev = nullptr;    // L
     int dims = 0, nf = 0, nv = 0, dbl = 0;
+    int kind = 0, R = 4;            // projection kernel of the batch (Tiling::kind) and its points per item
 };
 }  // namespace priest
 
@@ -893,7 +894,8 @@ void free_batch(BatchPlan *b)
 // present, bounds), every candidate tiling is timed on a representative
 // problem of the batch.  The trial launch is the batched kernel itself over
 // that problem's items, repeated until they fill the GPU twice, so the
-// measure is throughput (per-iteration marginal time: K = 10 minus K = 2).
+// measure is throughput (per-iteration marginal time: K = 22 minus K = 2,
+// the fastest of two launches each).
 std::vector<int> batch_class(const Shape &sh, int dbl)
 {
     return {-1, dbl, sh.dims, sh.nv, sh.nf, sh.bc_mask, sh.n_p, (sh.n_obs + 31) / 32, sh.n_obs > sh.n_static,
@@ -907,7 +909,7 @@ Tiling batch_tiling_for(priest_ctx *ctx, const Shape &sh)
     if (it == ctx->tuned.end()) return batch_tiling<Real>(sh);
     Tiling t = it->second;
     t.S = std::max(1, std::min(t.S, sh.N));
-    t.smem = project_smem_bytes<Real>(sh, t.S, t.C);
+    t.smem = t.kind == 1 ? pts_smem_bytes(sh, t.S, t.R) : project_smem_bytes<Real>(sh, t.S, t.C);
     if (t.smem > size_t(227) * 1024) return batch_tiling<Real>(sh);
     return t;
 }
@@ -977,25 +979,27 @@ priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
             }
             ProjParams<Real> pk[2] = {p, p};
             pk[0].K = 2;
-            pk[1].K = 10;
+            pk[1].K = 22;
             char *d = static_cast<char *>(dbuf);
             int *cnt = reinterpret_cast<int *>(d);
             ProjParams<Real> *dp = reinterpret_cast<ProjParams<Real> *>(d + 256);
             int2 *di = reinterpret_cast<int2 *>(d + 256 + 2 * sizeof(ProjParams<Real>));
             e = cudaMemcpyAsync(dp, pk, sizeof(pk), cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(di, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice, st);
-            float ms[2] = {0.f, 0.f};
-            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-                const int k = rep == 0 ? 0 : rep - 1;  // rep 0 warms up
+            float ms[2] = {1e30f, 1e30f};
+            for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+                const int k = rep == 0 ? 0 : (rep - 1) & 1;  // rep 0 warms up; then the fastest of two each
                 e = cudaMemsetAsync(cnt, 0, sizeof(int), st);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, st);
                 if (e == cudaSuccess)
-                    e = launch_project_batch<Real>(dp + k, di, int(it.size()), cnt, sh.dims, 4, 0, sh.nf, sh.nv, 0,
-                                                   t.smem, 0, st);
+                    e = launch_project_batch<Real>(dp + k, di, int(it.size()), cnt, sh.dims, t.R, 0, sh.nf, sh.nv, 0,
+                                                   t.smem, 0, st, t.kind);
                 ctx->launches++;
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                if (e == cudaSuccess && rep > 0) cudaEventElapsedTime(&ms[k], e0, e1);
+                float t_ms = 0.f;
+                if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&t_ms, e0, e1) == cudaSuccess)
+                    ms[k] = std::min(ms[k], t_ms);
             }
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -1003,7 +1007,12 @@ priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
                 continue;
             }
             // marginal time per iteration per sample processed
-            const float us = 1e3f * (ms[1] - ms[0]) / 8.f / float(it.size() * t.S);
+            float us = 1e3f * (ms[1] - ms[0]) / 20.f / float(it.size() * t.S);
+            if (!(us > 0.f)) us = 1e3f * ms[1] / 23.f / float(it.size() * t.S);  // timing noise
+            if (const char *lv = getenv("PRIEST_AUTOTUNE_LOG"))
+                if (atoi(lv) >= 2)
+                    fprintf(stderr, "priest batch autotune candidate: n_p=%d n_obs=%d kind=%d S=%d C=%d ws=%d -> %.5f us\n",
+                            sh.n_p, sh.n_obs, t.kind, t.S, t.C, t.ws, us);
             if (us < best_us) {
                 best_us = us;
                 best = t;
@@ -1011,8 +1020,8 @@ priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
         }
         ctx->tuned[batch_class(sh, sizeof(Real) == 8)] = best;
         if (getenv("PRIEST_AUTOTUNE_LOG"))
-            fprintf(stderr, "priest batch autotune: n_p=%d n_obs=%d -> S=%d C=%d ws=%d (%.4f us / sample-iteration)\n",
-                    sh.n_p, sh.n_obs, best.S, best.C, best.ws, best_us);
+            fprintf(stderr, "priest batch autotune: n_p=%d n_obs=%d -> kind=%d S=%d C=%d ws=%d (%.4f us / sample-iteration)\n",
+                    sh.n_p, sh.n_obs, best.kind, best.S, best.C, best.ws, best_us);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1046,12 +1055,31 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
     std::vector<SetupParams> setups(n), setups_ready(n);
     std::vector<CemArgs> cem(n);
     std::vector<std::pair<double, int2>> items;
+    // one projection kernel for the whole launch: the point-owner kernel when
+    // every problem's tiling uses it, the chunked one otherwise
+    std::vector<Tiling> tiles(n);
+    bool all_pts = true;
+    for (int i = 0; i < n; ++i) {
+        tiles[i] = batch_tiling_for<Real>(ctx, probs[i]->sh);
+        all_pts = all_pts && tiles[i].kind == 1;
+    }
+    for (int i = 0; i < n && !all_pts; ++i)
+        if (tiles[i].kind == 1) {
+            Shape sh = probs[i]->sh;
+            for (const Tiling &c : batch_candidates<Real>(sh))
+                if (c.kind == 0) {
+                    tiles[i] = c;
+                    break;
+                }
+        }
+    b->kind = all_pts ? 1 : 0;
+    b->R = all_pts ? tiles[0].R : 4;
     for (int i = 0; i < n; ++i) {
         priest_loaded *h = probs[i];
         const Shape &sh = h->sh;
         if (sh.dims != s0.dims || sh.nv != s0.nv || sh.bc_mask != s0.bc_mask)
             return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
-        const Tiling t = batch_tiling_for<Real>(ctx, sh);
+        const Tiling t = tiles[i];
         if (t.smem == 0) return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
         b->smem_proj = std::max(b->smem_proj, t.smem);
         ProjParams<Real> p = proj_params<Real>(ctx, h, t);
@@ -1135,7 +1163,7 @@ priest_status batch_enqueue(priest_ctx *ctx, BatchPlan *b, bool shape_ready, cud
     const ProjParams<Real> *params = static_cast<const ProjParams<Real> *>(b->params_dev);
     for (int l = 0; l < b->L && e == cudaSuccess; ++l) {
         e = launch_project_batch<Real>(params + size_t(l) * b->n, b->items_dev, b->n_items, b->counters_dev + l,
-                                       b->dims, 4, 0, b->nf, b->nv, 0, b->smem_proj, 0, st);
+                                       b->dims, b->R, 0, b->nf, b->nv, 0, b->smem_proj, 0, st, b->kind);
         if (e == cudaSuccess) e = launch_select_batch(b->cem_dev, b->n, b->smem_select, st);
         if (e == cudaSuccess) e = launch_refit_batch(b->cem_dev, b->n, b->D_max, b->smem_refit, st);
         ctx->launches += 3;

@@ -224,6 +224,7 @@ struct Tiling {
 // FP32 point-owner kernel (project_pts.cu): degree 10 with 5 free coefficients.
 bool pts_supported(const Shape &sh);
 bool pts_span_ok(const Shape &sh, int R);
+bool pts_batch_ok(const Shape &sh);
 size_t pts_smem_bytes(const Shape &sh, int S, int R);
 int pts_threads(const Shape &sh, int S, int R);
 int pts_max_threads(int R);
@@ -291,11 +292,12 @@ cudaError_t launch_refit_batch(const CemArgs *args_dev, int n, int D_max, size_t
 size_t select_smem_bytes(int N);
 size_t refit_smem_bytes(int D, int n_elite);
 
-// Persistent batched projection over the (problem, first sample) items.
+// Persistent batched projection over the (problem, first sample) items; kind
+// selects the chunked (0) or point-owner FP32 (1) kernel.
 template <typename Real>
 cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 *items_dev, int n_items,
                                  int *counter_dev, int dims, int R, int threads, int nf, int nv, int want_lambda,
-                                 size_t smem, int grid, cudaStream_t st);
+                                 size_t smem, int grid, cudaStream_t st, int kind = 0);
 
 
 template <typename Real>
@@ -304,6 +306,8 @@ size_t project_smem_bytes(const Shape &sh, int S, int C);
 template <typename Real>
 cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st);
 cudaError_t launch_project_pts(const ProjParams<float> &p, const Tiling &t, cudaStream_t st);
+cudaError_t launch_project_pts_batch(const ProjParams<float> *params, const int2 *items, int n_items, int *counter,
+                                     int dims, int R, int want_lambda, size_t smem, int grid, cudaStream_t st);
 
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm);

@@ -2,6 +2,8 @@
 // (project_kernel.cuh): a cost model for the default tiling and the list of
 // compiled (points per item, CTA size) variants the autotuner times.
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "project_kernel.cuh"
@@ -56,6 +58,8 @@ int samples_per_cta(int n_samples, int n_sm, int threads, int ws)
     return std::max(1, S);
 }
 
+bool pts_allowed();
+
 // Point-owner tiling (FP32, project_pts.cuh): S samples per CTA with R points
 // per thread; smem == 0 when the CTA does not fit.
 Tiling pts_tiling(const Shape &sh, int S, int R)
@@ -79,7 +83,7 @@ Tiling pts_tiling(const Shape &sh, int S, int R)
 std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
 {
     std::vector<Tiling> out;
-    if (!pts_supported(sh)) return out;
+    if (!pts_supported(sh) || !pts_allowed()) return out;
     for (int R : {2, 4}) {
         const int tps = (sh.n_p + R - 1) / R;
         const int s_max = std::max(1, pts_max_threads(R) / tps);
@@ -102,7 +106,7 @@ std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm)
 {
-    if (sizeof(Real) == 4 && pts_supported(sh) && pts_span_ok(sh, 2)) {
+    if (sizeof(Real) == 4 && pts_supported(sh) && pts_span_ok(sh, 2) && pts_allowed()) {
         const int tps = (sh.n_p + 1) / 2;
         const int S = std::min(std::max(1, pts_max_threads(2) / tps), std::max(1, (n_samples + n_sm - 1) / n_sm));
         const Tiling p = pts_tiling(sh, S, 2);
@@ -160,9 +164,39 @@ std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm)
     return out;
 }
 
+// Point-owner tiling of one problem inside a persistent launch: two points
+// per thread, the samples that fill the variant's CTA (at most N).
+Tiling pts_batch_tiling(const Shape &sh, int S)
+{
+    Tiling t = pts_tiling(sh, std::max(1, std::min(S, sh.N)), 2);
+    t.threads = pts_max_threads(2);
+    if (pts_threads(sh, t.S, 2) > t.threads) t.smem = 0;
+    return t;
+}
+
+// PRIEST_PROJECT_KERNEL=chunked in the environment keeps the FP32 projection
+// on the chunked kernel (comparisons; the autotuner otherwise picks).
+bool pts_allowed()
+{
+    static const bool allowed = [] {
+        const char *v = getenv("PRIEST_PROJECT_KERNEL");
+        return !(v && std::string(v) == "chunked");
+    }();
+    return allowed;
+}
+
+bool pts_batch_ok(const Shape &sh)
+{
+    return pts_allowed() && pts_supported(sh) && pts_span_ok(sh, 2) && pts_batch_tiling(sh, 1).smem > 0;
+}
+
 template <typename Real>
 Tiling batch_tiling(const Shape &sh)
 {
+    if (sizeof(Real) == 4 && pts_batch_ok(sh)) {
+        const Tiling p = pts_batch_tiling(sh, pts_max_threads(2) / ((sh.n_p + 1) / 2));
+        if (p.smem > 0) return p;
+    }
     Tiling t;
     t.R = sizeof(Real) == 8 ? 4 : 5;
     t.threads = sizeof(Real) == 8 ? 256 : 512;
@@ -183,6 +217,13 @@ template <typename Real>
 std::vector<Tiling> batch_candidates(const Shape &sh)
 {
     std::vector<Tiling> out;
+    if (sizeof(Real) == 4 && pts_batch_ok(sh)) {
+        const int s_full = pts_max_threads(2) / ((sh.n_p + 1) / 2);
+        for (int S : {s_full, (s_full + 1) / 2}) {
+            const Tiling t = pts_batch_tiling(sh, S);
+            if (t.smem > 0 && (out.empty() || out.back().S != t.S)) out.push_back(t);
+        }
+    }
     const int threads = sizeof(Real) == 8 ? 256 : 512;
     for (int ws = 1; ws <= 4; ws *= 2) {
         Tiling t;
@@ -233,11 +274,15 @@ cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStrea
 template <typename Real>
 cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 *items_dev, int n_items,
                                  int *counter_dev, int dims, int R, int threads, int nf, int nv, int want_lambda,
-                                 size_t smem, int grid, cudaStream_t st)
+                                 size_t smem, int grid, cudaStream_t st, int kind)
 {
-    (void)R;
     (void)threads;
     if (n_items <= 0) return cudaSuccess;
+    if constexpr (sizeof(Real) == 4) {
+        if (kind == 1)
+            return launch_project_pts_batch(params_dev, items_dev, n_items, counter_dev, dims, R, want_lambda, smem,
+                                            grid, st);
+    }
     if constexpr (sizeof(Real) == 8) {
         if (dims == 2)
             return launch_variant_batch<Real, 2, 4, 256>(params_dev, items_dev, n_items, counter_dev, nf, nv,
@@ -254,9 +299,9 @@ cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 
 }
 
 template cudaError_t launch_project_batch<float>(const ProjParams<float> *, const int2 *, int, int *, int, int, int,
-                                                 int, int, int, size_t, int, cudaStream_t);
+                                                 int, int, int, size_t, int, cudaStream_t, int);
 template cudaError_t launch_project_batch<double>(const ProjParams<double> *, const int2 *, int, int *, int, int,
-                                                  int, int, int, int, size_t, int, cudaStream_t);
+                                                  int, int, int, int, size_t, int, cudaStream_t, int);
 template size_t project_smem_bytes<float>(const Shape &, int, int);
 template size_t project_smem_bytes<double>(const Shape &, int, int);
 template Tiling choose_tiling<float>(const Shape &, int, int);

@@ -1,6 +1,8 @@
 // project_pts.cu -- launch of the FP32 point-owner projection kernel
 // (project_pts.cuh): shared-memory size and dispatch over the compiled
 // (dims, points per thread, fixed-column multipliers) variants.
+#include <algorithm>
+
 #include "project_pts.cuh"
 
 namespace priest {
@@ -41,7 +43,42 @@ cudaError_t launch_pts_wl(const ProjParams<float> &p, const Tiling &t, cudaStrea
     return p.want_lambda ? launch_pts_one<DIMS, R, true>(p, t, st) : launch_pts_one<DIMS, R, false>(p, t, st);
 }
 
+template <int DIMS, int R, bool WL>
+cudaError_t launch_pts_batch_one(const ProjParams<float> *params, const int2 *items, int n_items, int *counter,
+                                 size_t smem, int grid, cudaStream_t st)
+{
+    static size_t granted = 0;
+    auto kern = pts::pts_batch_kernel<DIMS, R, 5, WL>;
+    cudaError_t e = reserve_smem(kern, smem, granted);
+    if (e != cudaSuccess) return e;
+    constexpr int threads = pts::pts_max_threads<R>();
+    if (grid <= 0) {
+        int per_sm = 0, dev = 0, n_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        grid = std::max(1, per_sm) * n_sm;
+    }
+    kern<<<grid, threads, smem, st>>>(params, items, n_items, counter);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+// Persistent point-owner launch over (problem, first sample) items; every
+// problem's p.S * TPS fits the variant's CTA (pts_max_threads(R)).
+cudaError_t launch_project_pts_batch(const ProjParams<float> *params, const int2 *items, int n_items, int *counter,
+                                     int dims, int R, int want_lambda, size_t smem, int grid, cudaStream_t st)
+{
+    if (n_items <= 0) return cudaSuccess;
+    if (dims == 2 && R == 2)
+        return want_lambda ? launch_pts_batch_one<2, 2, true>(params, items, n_items, counter, smem, grid, st)
+                           : launch_pts_batch_one<2, 2, false>(params, items, n_items, counter, smem, grid, st);
+    if (dims == 3 && R == 2)
+        return want_lambda ? launch_pts_batch_one<3, 2, true>(params, items, n_items, counter, smem, grid, st)
+                           : launch_pts_batch_one<3, 2, false>(params, items, n_items, counter, smem, grid, st);
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_project_pts(const ProjParams<float> &p, const Tiling &t, cudaStream_t st)
 {

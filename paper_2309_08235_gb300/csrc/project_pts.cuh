@@ -622,7 +622,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
 #pragma unroll
                 for (int ax = 0; ax < DIMS; ++ax) so[r][ax] = 0.f;
             }
-            all_pairs<DIMS, R, (DIMS == 3 ? 2 : 4)>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
+            all_pairs<DIMS, R, (DIMS == 3 ? 2 : (R >= 4 ? 8 : 4))>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
         }
         if (fin) {
             // ---- a9: r = sqrt(sum of squared residual rows), c_1
@@ -784,6 +784,26 @@ template <int DIMS, int R, int NF, bool WL>
 __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const ProjParams<float> p)
 {
     pts_body<DIMS, R, NF, WL>(p, blockIdx.x * p.S);
+}
+
+// Persistent form over many problems: CTAs take (problem, first sample)
+// items (each problem's p.S samples per item, p.S * TPS <= blockDim.x) through
+// an atomic counter until none is left.  *next must be zero at launch.
+template <int DIMS, int R, int NF, bool WL>
+__global__ void __launch_bounds__(pts_max_threads<R>(), 1)
+    pts_batch_kernel(const ProjParams<float> *params, const int2 *items, int n_items, int *next)
+{
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int2 w = items[it];
+        const ProjParams<float> p = params[w.x];
+        pts_body<DIMS, R, NF, WL>(p, w.y);
+        __syncthreads();
+    }
 }
 
 }  // namespace pts

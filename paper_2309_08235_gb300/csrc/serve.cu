@@ -37,6 +37,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -300,9 +301,10 @@ cudaError_t Server::enqueue_step(std::vector<Slot *> &active, const std::vector<
 template <typename Real>
 cudaError_t Server::enqueue_step_t(std::vector<Slot *> &active, const std::vector<Slot *> &fresh, Stage &sg)
 {
-    // ---- groups of the projection launch: same dims and free-coefficient count
-    std::map<std::pair<int, int>, std::vector<Slot *>> groups;
-    for (Slot *s : active) groups[{s->h.sh.dims, s->h.sh.nf}].push_back(s);
+    // ---- groups of the projection launch: same dims, free-coefficient count
+    //      and projection kernel
+    std::map<std::tuple<int, int, int>, std::vector<Slot *>> groups;
+    for (Slot *s : active) groups[{s->h.sh.dims, s->h.sh.nf, s->t.kind}].push_back(s);
     // ---- layout of the staging block
     StepLayout lay;
     size_t o = 0;
@@ -370,13 +372,14 @@ cudaError_t Server::enqueue_step_t(std::vector<Slot *> &active, const std::vecto
     ProjParams<Real> *pp = reinterpret_cast<ProjParams<Real> *>(H + lay.proj);
     int2 *items = reinterpret_cast<int2 *>(H + lay.items);
     struct GroupLaunch {
-        int dims, nf, nv, want_lambda;
+        int dims, nf, nv, want_lambda, kind, R;
         size_t first_param, first_item, n_items, smem;
     };
     std::vector<GroupLaunch> launches;
     size_t np = 0, ni = 0;
     for (auto &g : groups) {
-        GroupLaunch gl{g.first.first, g.first.second, g.second.front()->h.sh.nv, 0, np, ni, 0, 0};
+        GroupLaunch gl{std::get<0>(g.first), std::get<1>(g.first), g.second.front()->h.sh.nv, 0, std::get<2>(g.first),
+                       g.second.front()->t.R, np, ni, 0, 0};
         std::vector<std::pair<double, int2>> its;
         for (Slot *s : g.second) {
             const Shape &sh = s->h.sh;
@@ -451,7 +454,7 @@ cudaError_t Server::enqueue_step_t(std::vector<Slot *> &active, const std::vecto
     for (size_t gi = 0; gi < launches.size(); ++gi) {
         const GroupLaunch &gl = launches[gi];
         e = launch_project_batch<Real>(ppd + gl.first_param, itd + gl.first_item, int(gl.n_items), cnt + gi, gl.dims,
-                                       4, 0, gl.nf, gl.nv, gl.want_lambda, gl.smem, 0, st);
+                                       gl.R, 0, gl.nf, gl.nv, gl.want_lambda, gl.smem, 0, st, gl.kind);
         ctx->launches++;
         if (e != cudaSuccess) return e;
     }
