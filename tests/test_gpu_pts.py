@@ -1,0 +1,72 @@
+"""GPU parity of the FP32 point-owner projection kernel (threads own time
+stamps of one sample for all iterations; segmented reductions, state lanes)
+against the FP64 oracle, through the C ABI.  The autotuner is off, so the
+default tiling runs: the point-owner kernel with two time stamps per thread
+for every shape here (degree 10, at rest at both ends, enough time stamps).
+Cases: warm-start multipliers over many iterations (the fixed-column
+multipliers come from the summed residual rows), workspace bounds, moving
+obstacles, 2-D and 3-D, a ragged last CTA and samples of several CTAs
+whose warps straddle two samples."""
+import numpy as np
+import pytest
+
+from gpu_common import TOL_FP32, rel_err, samples, scale_of, scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2309_08235_gb300 import build, priest
+
+    build.build()
+    return priest
+
+
+def project(P, p, xi, K, lam0):
+    with P.Context(p, {"proj_iters": K}, precision=P.PRIEST_FP32, autotune=0) as ctx:
+        return ctx.project(p, xi, lam=lam0)
+
+
+@pytest.mark.parametrize("dims,bounds,n_dyn", [(2, False, 4), (3, False, 3), (2, True, 2)])
+def test_k_steps_with_warm_multipliers(P, oracle, dims, bounds, n_dyn):
+    p = scene(dims=dims, n_obs=40, n_p=100, n_dyn=n_dyn, bounds=bounds)
+    xi = samples(oracle, p, 300, seed=11 + dims)
+    lam0 = np.random.default_rng(3).normal(0.0, 0.2, xi.shape)
+    K = 30
+    xb, lam, r, c1 = project(P, p, xi, K, lam0)
+    xb_o, lam_o = oracle.project(p, xi, K, lam=lam0)
+    r_o, c1_o = oracle.residual_cost(p, xb_o)
+    assert rel_err(xb, xb_o, scale_of(p)) < TOL_FP32
+    # every column, the fixed ones included
+    assert rel_err(lam, lam_o, 1.0) < TOL_FP32
+    assert rel_err(r, r_o, 1.0) < TOL_FP32
+    assert rel_err(c1, c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
+    assert np.count_nonzero(r_o > 1e-6) > 10  # obstacles are active
+
+
+def test_ragged_last_cta_sampled(P, oracle):
+    """1003 samples (seven per CTA, the last CTA holds two): every 59th
+    sample and the last one against the oracle."""
+    p = scene(dims=2, n_obs=30, n_p=100, n_dyn=3)
+    xi = samples(oracle, p, 1003, seed=21)
+    K = 20
+    xb, lam, r, c1 = project(P, p, xi, K, None)
+    idx = np.r_[np.arange(0, 1003, 59), 1001, 1002]
+    xb_o, _ = oracle.project(p, xi[idx], K)
+    r_o, c1_o = oracle.residual_cost(p, xb_o)
+    assert rel_err(xb[idx], xb_o, scale_of(p)) < TOL_FP32
+    assert rel_err(r[idx], r_o, 1.0) < TOL_FP32
+    assert rel_err(c1[idx], c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
+
+
+def test_same_result_alone_and_in_a_larger_launch(P, oracle):
+    """A sample's result does not depend on which CTA or warp position holds
+    it: the first 7 samples alone (one per CTA) and inside 700 (five per CTA,
+    warps shared by two samples) agree to well within the FP32 tolerance."""
+    p = scene(dims=2, n_obs=25, n_p=100, n_dyn=2)
+    xi = samples(oracle, p, 700, seed=31)
+    a = project(P, p, xi[:7], 25, None)
+    b = project(P, p, xi, 25, None)
+    assert rel_err(a[0], b[0][:7], scale_of(p)) < TOL_FP32 / 10
+    assert rel_err(a[2], b[2][:7], 1.0) < TOL_FP32 / 10
