@@ -43,6 +43,7 @@ SM_MAX_MHZ = 2070.0
 
 
 WORKLOADS = {"clutter2d": "clutter2d_fp32", "ellipsoid3d": "ellipsoid3d_mixed", "p2p2d": "p2p2d", "p2p3d": "p2p3d",
+             "clutter2d_bounds": "clutter2d_bounds",
              "dynamic2d": "dynamic2d"}
 
 
@@ -54,6 +55,10 @@ def workload_desc(p, cem, precision="fp32", name="clutter2d"):
                 f"K={cem['proj_iters']}, L={cem['cem_iters']} CEM iters (the paper's N_b = 110, N = 13), "
                 f"{cem['n_elite']} elites, cost {'BARN-style' if p.get('cost_kind', 0) == 1 else 'sum |acc|^2'}, "
                 f"{prec}")
+    if name == "clutter2d_bounds":
+        return (f"2-D clutter with workspace rows (box [0, 30]^2) and the paper's four boundary rows per axis "
+                f"(end position only): {p['n_obs']} circles (10 moving), N={cem['n_samples']} samples, "
+                f"n_p={p['n_p']}, K={cem['proj_iters']}, L={cem['cem_iters']}, {cem['n_elite']} elites, {prec}")
     if p["dims"] == 3:
         return (f"3-D point-to-point: {p['n_obs']} static ellipsoids in 20x20x8 m, N={cem['n_samples']} samples, "
                 f"n_p={p['n_p']}, degree {p['degree']}, K={cem['proj_iters']} projection iters, "
@@ -79,7 +84,14 @@ def flops_per_sample_iter(p, nf=5):
     return n_p * n_o * pair + 2 * n_p * 12 + 2 * dims * (2 * 3 * n_p * nv) + 2 * dims * nv * nv
 
 
-def fma_pipe_flops_per_sample_iter(p, nf=5):
+def free_coefficients(p):
+    """Free Bernstein coefficients per axis: n_v minus the three start
+    conditions minus the end conditions of the final mask."""
+    fixed_end = {7: 3, 3: 2, 1: 1, 0: 0}[int(p.get("bc_final_mask", 7))]
+    return p.get("degree", 10) + 1 - 3 - fixed_end
+
+
+def fma_pipe_flops_per_sample_iter(p, nf=None):
     """FP32 flops the kernel itself issues per projected sample-iteration on
     the FMA pipe (FMA = 2): the expanded pre-filter (2 FMA per static pair,
     4 in 3-D), the moving-obstacle scaled offsets (6 FMA per pair, 9 in 3-D),
@@ -87,6 +99,7 @@ def fma_pipe_flops_per_sample_iter(p, nf=5):
     dims x nf FMA per point), ~10 per point for the velocity / acceleration
     blocks and the shared-inverse step (dims x nf^2 FMA)."""
     dims, n_p, n_o = p["dims"], p["n_p"], p["n_obs"]
+    nf = free_coefficients(p) if nf is None else nf
     n_mov = int(np.count_nonzero(np.abs(np.asarray(p["vel"])).sum(1))) if n_o else 0
     st, mv = (4, 12) if dims == 2 else (8, 18)
     return (n_p * ((n_o - n_mov) * st + n_mov * mv) + n_p * (2 * (2 * 3 * dims * nf) + 10)
@@ -277,8 +290,12 @@ def run_ours(args):
     pipe_tflops = fma_pipe_flops_per_sample_iter(p) * N * K / (avg_proj_ms / 1e3) / 1e12
     traffic = None
     prof_path = os.path.join(ROOT, "profiles", "traffic.txt")
-    kname = ("pts_kernel (FP32 point-owner projection, %d-D)" % p["dims"] if args.precision == "fp32" else
-             "project_tc_kernel (tcgen05 pair tests, %d-D)" % p["dims"])
+    if args.precision != "fp32":
+        kname = "project_tc_kernel (tcgen05 pair tests, %d-D)" % p["dims"]
+    elif p.get("degree", 10) == 10 and (free_coefficients(p) == 5 or (free_coefficients(p) == 7 and p["dims"] == 2)):
+        kname = "pts_kernel (FP32 point-owner projection, %d-D)" % p["dims"]
+    else:
+        kname = "project_kernel (FP32 chunked projection, %d-D, %d free coefficients)" % (p["dims"], free_coefficients(p))
     if os.path.exists(prof_path) and args.precision == "fp32" and p["dims"] == 2 and args.workload == "clutter2d":
         for ln in open(prof_path):
             if ln.startswith("pts_kernel_bytes_per_launch:"):
@@ -600,7 +617,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["clutter2d", "ellipsoid3d", "p2p2d", "p2p3d", "dynamic2d", "batched",
+    ap.add_argument("--workload", choices=["clutter2d", "clutter2d_bounds", "ellipsoid3d", "p2p2d", "p2p3d", "dynamic2d",
+                                           "batched",
                                            "serving", "dpriest"],
                     default="clutter2d",
                     help="clutter2d: the default bench line; batched: 256 uneven problems; serving: Poisson "

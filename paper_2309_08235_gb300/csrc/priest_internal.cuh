@@ -221,7 +221,8 @@ struct Tiling {
     int kind = 0; // 0: chunked kernel (project_kernel.cuh); 1: point-owner FP32 kernel (project_pts.cuh)
 };
 
-// FP32 point-owner kernel (project_pts.cu): degree 10 with 5 free coefficients.
+// FP32 point-owner kernel (project_pts.cu): degree 10 with 5 free coefficients
+// (2-D, 3-D) or 7 (2-D).
 bool pts_supported(const Shape &sh);
 bool pts_span_ok(const Shape &sh, int R);
 bool pts_batch_ok(const Shape &sh);
@@ -307,7 +308,7 @@ template <typename Real>
 cudaError_t launch_project(const ProjParams<Real> &p, const Tiling &t, cudaStream_t st);
 cudaError_t launch_project_pts(const ProjParams<float> &p, const Tiling &t, cudaStream_t st);
 cudaError_t launch_project_pts_batch(const ProjParams<float> *params, const int2 *items, int n_items, int *counter,
-                                     int dims, int R, int want_lambda, size_t smem, int grid, cudaStream_t st);
+                                     int dims, int nf, int R, int want_lambda, size_t smem, int grid, cudaStream_t st);
 
 template <typename Real>
 Tiling choose_tiling(const Shape &sh, int n_samples, int n_sm);

@@ -85,6 +85,7 @@ std::vector<Tiling> pts_candidates(const Shape &sh, int n_samples, int n_sm)
     std::vector<Tiling> out;
     if (!pts_supported(sh) || !pts_allowed()) return out;
     for (int R : {2, 4}) {
+        if (R == 4 && sh.nf != 5) continue;  // compiled for five free coefficients only
         const int tps = (sh.n_p + R - 1) / R;
         const int s_max = std::max(1, pts_max_threads(R) / tps);
         const int s1 = std::min(s_max, std::max(1, (n_samples + n_sm - 1) / n_sm));
@@ -280,8 +281,8 @@ cudaError_t launch_project_batch(const ProjParams<Real> *params_dev, const int2 
     if (n_items <= 0) return cudaSuccess;
     if constexpr (sizeof(Real) == 4) {
         if (kind == 1)
-            return launch_project_pts_batch(params_dev, items_dev, n_items, counter_dev, dims, R, want_lambda, smem,
-                                            grid, st);
+            return launch_project_pts_batch(params_dev, items_dev, n_items, counter_dev, dims, nf, R, want_lambda,
+                                            smem, grid, st);
     }
     if constexpr (sizeof(Real) == 8) {
         if (dims == 2)

@@ -305,6 +305,13 @@ def workload(name: str):
     if name == "ellipsoid3d_mixed":
         p = scene_ellipsoids_3d()
         return p, cem_settings(2000, 100, 4, n_elite=200, dims=3)
+    if name == "clutter2d_bounds":
+        # the 2-D clutter workload with the workspace rows G = [-P; P] on
+        # (tau = [-s_min; s_max], the 30 x 30 m box) and the paper's four
+        # boundary rows per axis (end position only: final mask 1)
+        p = dict(scene_clutter_2d())
+        p.update(use_bounds=True, smin=np.zeros(2), smax=np.full(2, 30.0), bc_final_mask=1)
+        return p, cem_settings(1000, 100, 5, n_elite=100, dims=2)
     c = PAPER_CEM
     if name == "p2p2d":
         return scene_p2p_2d(), cem_settings(c["n_samples"], c["proj_iters"], c["cem_iters"], c["n_proj"],

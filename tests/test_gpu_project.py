@@ -145,3 +145,17 @@ def test_invalid_inputs_are_rejected(P, oracle):
         xi_nan[1, 4] = np.nan
         with pytest.raises(P.PriestError):
             ctx.project(p, xi_nan)
+
+
+def test_fp32_bounded_four_row_workload(P, oracle):
+    """The measured bounded workload's shape (workspace rows on, the paper's
+    four boundary rows per axis: end position only), 2-D clutter scene, FP32
+    against the oracle on 150 samples over 20 iterations."""
+    from paper_2309_08235_gb300 import workloads as W
+
+    p, _ = W.workload("clutter2d_bounds")
+    xi = samples(oracle, p, 150, seed=41, std=2.0)
+    (xb, lam, r, c1), (xb_o, lam_o, r_o, c1_o) = run_both(P, oracle, p, xi, 20, P.PRIEST_FP32)
+    assert rel_err(xb, xb_o, scale_of(p)) < TOL_FP32
+    assert rel_err(r, r_o, 1.0) < TOL_FP32
+    assert rel_err(c1, c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32

@@ -2,7 +2,8 @@
 stamps of one sample for all iterations; segmented reductions, state lanes)
 against the FP64 oracle, through the C ABI.  The autotuner is off, so the
 default tiling runs: the point-owner kernel with two time stamps per thread
-for every shape here (degree 10, at rest at both ends, enough time stamps).
+for every shape here (degree 10, at rest at both ends or, in 2-D, the end
+position only; enough time stamps).
 Cases: warm-start multipliers over many iterations (the fixed-column
 multipliers come from the summed residual rows), workspace bounds, moving
 obstacles, 2-D and 3-D, a ragged last CTA and samples of several CTAs
@@ -28,9 +29,9 @@ def project(P, p, xi, K, lam0):
         return ctx.project(p, xi, lam=lam0)
 
 
-@pytest.mark.parametrize("dims,bounds,n_dyn", [(2, False, 4), (3, False, 3), (2, True, 2)])
-def test_k_steps_with_warm_multipliers(P, oracle, dims, bounds, n_dyn):
-    p = scene(dims=dims, n_obs=40, n_p=100, n_dyn=n_dyn, bounds=bounds)
+@pytest.mark.parametrize("dims,bounds,n_dyn,mask", [(2, False, 4, 7), (3, False, 3, 7), (2, True, 2, 7), (2, True, 2, 1)])
+def test_k_steps_with_warm_multipliers(P, oracle, dims, bounds, n_dyn, mask):
+    p = scene(dims=dims, n_obs=40, n_p=100, n_dyn=n_dyn, bounds=bounds, mask=mask)
     xi = samples(oracle, p, 300, seed=11 + dims)
     lam0 = np.random.default_rng(3).normal(0.0, 0.2, xi.shape)
     K = 30
