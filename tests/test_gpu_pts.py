@@ -71,3 +71,35 @@ def test_same_result_alone_and_in_a_larger_launch(P, oracle):
     b = project(P, p, xi, 25, None)
     assert rel_err(a[0], b[0][:7], scale_of(p)) < TOL_FP32 / 10
     assert rel_err(a[2], b[2][:7], 1.0) < TOL_FP32 / 10
+
+
+@pytest.mark.parametrize("case", ["no_obstacles", "moving_only", "one_sample", "long_horizon"])
+def test_edge_shapes(P, oracle, case):
+    """Degenerate and extreme shapes through the point-owner kernel: no
+    obstacles (the projection is the equality projection at every iteration),
+    moving obstacles only (no static quads), a single sample (one CTA with
+    one partial warp), and 400 time stamps (200 threads per sample)."""
+    if case == "no_obstacles":
+        p = scene(dims=2, n_obs=0, n_dyn=0, n_p=100, vmax=1e6, amax=1e6)
+        n, K = 64, 15
+    elif case == "moving_only":
+        p = scene(dims=2, n_obs=8, n_dyn=8, n_p=100)
+        n, K = 64, 15
+    elif case == "one_sample":
+        p = scene(dims=3, n_obs=20, n_dyn=2, n_p=100)
+        n, K = 1, 15
+    else:
+        p = scene(dims=2, n_obs=30, n_dyn=3, n_p=400, horizon=12.0)
+        n, K = 40, 15
+    xi = samples(oracle, p, n, seed=51)
+    # zero multipliers without obstacles (the equality-projection pin), warm ones otherwise
+    lam0 = np.zeros_like(xi) if case == "no_obstacles" else np.random.default_rng(5).normal(0.0, 0.1, xi.shape)
+    xb, lam, r, c1 = project(P, p, xi, K, lam0)
+    xb_o, lam_o = oracle.project(p, xi, K, lam=lam0)
+    r_o, c1_o = oracle.residual_cost(p, xb_o)
+    assert rel_err(xb, xb_o, scale_of(p)) < TOL_FP32
+    assert rel_err(lam, lam_o, 1.0) < TOL_FP32
+    assert rel_err(r, r_o, 1.0) < TOL_FP32
+    assert rel_err(c1, c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
+    if case == "no_obstacles":
+        assert rel_err(xb, oracle.project_eq(p, xi), scale_of(p)) < TOL_FP32
