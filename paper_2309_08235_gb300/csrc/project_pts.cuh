@@ -299,9 +299,11 @@ __device__ __forceinline__ void moving_rescan(const float *rec, const float *sOb
 
 // Every obstacle against the thread's R points; all lanes of the CTA run the
 // same trip counts, so the votes use the full warp.  Static quads go in
-// batches of NQB: one minimum per (point, quad) kept in registers, their
-// minimum per point and one vote; when it fires, the (point, quad) candidate
-// bits come from the kept minima and the candidates are tested exactly.
+// batches of NQB: one minimum per (point, quad) kept in registers and their
+// minimum per point; a thread with a candidate records the batch's (point,
+// quad) bits, and after the loop each thread tests its recorded candidates
+// exactly, oldest first (all lanes with candidates in one pass instead of one
+// warp-wide detour per batch).
 template <int DIMS, int R, int NQB>
 __device__ __forceinline__ void all_pairs(const float *srec, const float *mrec, const float *sObs, int nq, int nm2,
                                           int ns, const detail::PackedPoints<DIMS, R> &P, bool fin,
@@ -310,9 +312,22 @@ __device__ __forceinline__ void all_pairs(const float *srec, const float *mrec, 
     static_assert(R * NQB <= 32, "candidate bits");
     constexpr int QS = DIMS == 2 ? 12 : 20;
     constexpr int RM = DIMS == 2 ? 12 : 16;
+    // candidate batches of this thread, processed after the screening loop
+    // (oldest first, so each point still sees its obstacles in order)
+    constexpr int MAXE = 3;
+    int ek0 = 0, ek1 = 0, ek2 = 0, ne = 0;
+    unsigned ec0 = 0u, ec1 = 0u, ec2 = 0u;
+    auto flush = [&]() {
+        for (int e = 0; e < ne; ++e) {
+            const int ke = e == 0 ? ek0 : (e == 1 ? ek1 : ek2);
+            const unsigned ce = e == 0 ? ec0 : (e == 1 ? ec1 : ec2);
+            quad_candidates<DIMS, R, NQB>(ce, srec, sObs, ke, P, fin, so);
+        }
+        ne = 0;
+    };
     int k = 0;
     for (; k + NQB <= nq; k += NQB) {
-        // screening: one minimum per (point, quad), their minimum per point, one vote
+        // screening: one minimum per (point, quad), their minimum per point
         float mq[R][NQB];
 #pragma unroll
         for (int i = 0; i < NQB; ++i) {
@@ -328,16 +343,28 @@ __device__ __forceinline__ void all_pairs(const float *srec, const float *mrec, 
             for (int i = 1; i < NQB; i += 2) m = (i + 1 < NQB) ? fmin3(m, mq[r][i], mq[r][i + 1]) : fminf(m, mq[r][i]);
             f |= m < P.npq[r];
         }
-        if (__any_sync(kFull, f)) {
-            // (point, quad) candidate bits of the batch, then the exact tests
+        if (f) {
+            // record the (point, quad) candidate bits of the batch
             unsigned cand = 0u;
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int i = 0; i < NQB; ++i) cand |= (mq[r][i] < P.npq[r] ? 1u : 0u) << (r * NQB + i);
-            quad_candidates<DIMS, R, NQB>(cand, srec, sObs, k, P, fin, so);
+            if (ne == MAXE) flush();
+            if (ne == 0) {
+                ek0 = k;
+                ec0 = cand;
+            } else if (ne == 1) {
+                ek1 = k;
+                ec1 = cand;
+            } else {
+                ek2 = k;
+                ec2 = cand;
+            }
+            ++ne;
         }
     }
+    flush();
     for (; k < nq; ++k) {
         unsigned cand = 0u;
 #pragma unroll
