@@ -1,7 +1,7 @@
 // cem.cu -- the CEM stages of Alg. 1 around the projection:
 //   a10 ConstraintEliteSet (N_proj least r) and EliteSet (N_elite least
-//       c_aug = c_1 + r among them), ties to the lower sample index, by a
-//       bitonic sort whose short-stride stages run inside a warp on shuffles;
+//       c_aug = c_1 + r among them), ties to the lower sample index, by two
+//       bitonic sorts whose short-stride stages run inside a warp on shuffles;
 //   a11 MPPI-like refit (eqs. update_mean, update_covariance) in FP64 with
 //       weights exp(-(c_aug - delta)/gamma), delta = min c_aug;
 //   a12 the next sampling factor chol(Sigma' + eps I), eps = chol_eps tr(Sigma')/D,
@@ -17,7 +17,6 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSelectThreads = 1024;
 constexpr int kRefitThreads = 256;
-constexpr int kMaxEliteSort = PRIEST_MAX_ELITE;  // elites sorted in static shared memory
 
 // Order-preserving map of an FP64 key to uint64 (NaN sorts after +inf).
 __device__ __forceinline__ unsigned long long order_key(double x)
@@ -84,140 +83,41 @@ __device__ void bitonic_sort(unsigned long long *key, int *idx, int n2)
     }
 }
 
-// k-th smallest (1-based) composite key (key, index) among the elements with
-// member[i] != 0, by most-significant-digit radix select: 8 passes over the
-// 64-bit key and 2 over the index (indices are below 2^16), each pass a
-// 256-bin histogram of the surviving candidates (warp-aggregated atomics)
-// and a scan by one warp.  Composite keys are distinct, so the result is the
-// unique element with exactly k - 1 smaller ones.
-__device__ void radix_select(const unsigned long long *key, const unsigned char *member, int N, int k,
-                             unsigned *hist, unsigned long long *out_key, int *out_idx, int *s_k)
+__host__ __device__ inline int pow2_at_least(int n)
 {
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
-    unsigned long long pkey = 0ull;  // decided high bits of the key
-    unsigned pidx = 0u;              // decided high bits of the index
-    if (tid == 0) *s_k = k;
-    for (int pass = 0; pass < 10; ++pass) {
-        for (int b = tid; b < 256; b += T) hist[b] = 0u;
-        __syncthreads();
-        const bool on_key = pass < 8;
-        const int shift = on_key ? 56 - 8 * pass : 8 - 8 * (pass - 8);
-        for (int base = 0; base < N; base += T) {
-            const int i = base + tid;
-            int digit = -1;
-            if (i < N && member[i]) {
-                const unsigned long long kk = key[i];
-                bool match;
-                if (on_key) {
-                    match = (pass == 0) || ((kk >> (shift + 8)) == pkey);
-                    if (match) digit = int((kk >> shift) & 0xffull);
-                } else {
-                    match = (kk == pkey) && (pass == 8 || (unsigned(i) >> (shift + 8)) == pidx);
-                    if (match) digit = (i >> shift) & 0xff;
-                }
-            }
-            const unsigned grp = __match_any_sync(kFull, digit);
-            if (digit >= 0 && lane == __ffs(grp) - 1) atomicAdd(&hist[digit], unsigned(__popc(grp)));
-        }
-        __syncthreads();
-        if (tid < 32) {
-            // find the bin holding the k-th candidate: scan 256 bins, 8 per lane
-            unsigned c[8], sum = 0u;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                c[q] = hist[lane * 8 + q];
-                sum += c[q];
-            }
-            unsigned incl = sum;
-            for (int off = 1; off < 32; off <<= 1) {
-                const unsigned v = __shfl_up_sync(kFull, incl, off);
-                if (lane >= off) incl += v;
-            }
-            const unsigned excl = incl - sum;
-            const unsigned kk = unsigned(*s_k);
-            int found = -1;
-            unsigned before = 0u;
-            if (kk > excl && kk <= incl) {
-                unsigned run = excl;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (found < 0 && kk <= run + c[q]) {
-                        found = lane * 8 + q;
-                        before = run;
-                    }
-                    run += c[q];
-                }
-            }
-            const unsigned owner = __ballot_sync(kFull, found >= 0);
-            const int src = __ffs(owner) - 1;
-            const int digit = __shfl_sync(kFull, found, src);
-            const unsigned bef = __shfl_sync(kFull, before, src);
-            if (lane == 0) {
-                *s_k = int(kk - bef);
-                hist[256] = unsigned(digit);
-            }
-        }
-        __syncthreads();
-        const unsigned digit = hist[256];
-        if (on_key)
-            pkey = (pkey << 8) | digit;
-        else
-            pidx = (pidx << 8) | digit;
-        __syncthreads();
-    }
-    *out_key = pkey;
-    *out_idx = int(pidx);
-}
-
-__device__ __forceinline__ bool le_composite(unsigned long long ka, int ia, unsigned long long kb, int ib)
-{
-    return ka < kb || (ka == kb && ia <= ib);
+    int n2 = 32;
+    while (n2 < n) n2 <<= 1;
+    return n2;
 }
 
 // ConstraintEliteSet: the n_proj least (r, index); EliteSet: the n_elite least
-// (c_aug, index) among them, written in ascending order.
+// (c_aug, index) among them, written in ascending order.  Two bitonic sorts of
+// composite (key, index) pairs: all N samples by r, then the first n_proj by
+// c_aug; padding entries carry the largest key and index, so they sort last.
 __device__ void select_body(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long *kr = reinterpret_cast<unsigned long long *>(smem_raw);  // N
-    unsigned long long *kc = kr + N;                                             // N
-    unsigned char *member = reinterpret_cast<unsigned char *>(kc + N);           // N
-    __shared__ unsigned hist[257];
-    __shared__ int s_k, s_cnt;
-    __shared__ unsigned long long s_tkey;
-    __shared__ int s_tidx;
-    __shared__ unsigned long long s_ek[kMaxEliteSort];
-    __shared__ int s_ei[kMaxEliteSort];
+    const int n2 = pow2_at_least(N);
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(smem_raw);  // n2
+    int *idx = reinterpret_cast<int *>(key + n2);                                // n2
     const int tid = threadIdx.x, T = blockDim.x;
-    for (int i = tid; i < N; i += T) {
-        kr[i] = order_key(r[i]);
-        kc[i] = order_key(c1[i] + r[i]);
-        member[i] = 1;
+    for (int i = tid; i < n2; i += T) {
+        key[i] = i < N ? order_key(r[i]) : ~0ull;
+        idx[i] = i < N ? i : 0x7fffffff;
     }
-    if (tid == 0) s_cnt = 0;
-    __syncthreads();
-    unsigned long long tk;
-    int ti;
-    radix_select(kr, member, N, n_proj, hist, &tk, &ti, &s_k);
-    for (int i = tid; i < N; i += T) member[i] = le_composite(kr[i], i, tk, ti) ? 1 : 0;
-    __syncthreads();
-    radix_select(kc, member, N, n_elite, hist, &tk, &ti, &s_k);
-    // gather the elites, then order them by (c_aug, index)
-    int n2 = 32;
-    while (n2 < n_elite) n2 <<= 1;
-    for (int i = tid; i < N; i += T)
-        if (member[i] && le_composite(kc[i], i, tk, ti)) {
-            const int slot = atomicAdd(&s_cnt, 1);
-            s_ek[slot] = kc[i];
-            s_ei[slot] = i;
+    bitonic_sort(key, idx, n2);
+    const int n2p = pow2_at_least(n_proj);
+    for (int e = tid; e < n2p; e += T) {
+        if (e < n_proj) {
+            const int i = idx[e];
+            key[e] = order_key(c1[i] + r[i]);
+        } else {
+            key[e] = ~0ull;
+            idx[e] = 0x7fffffff;
         }
-    __syncthreads();
-    for (int e = n_elite + tid; e < n2; e += T) {
-        s_ek[e] = ~0ull;
-        s_ei[e] = 0x7fffffff;
     }
-    bitonic_sort(s_ek, s_ei, n2);
-    for (int e = tid; e < n_elite; e += T) elite_idx[e] = s_ei[e];
+    bitonic_sort(key, idx, n2p);
+    for (int e = tid; e < n_elite; e += T) elite_idx[e] = idx[e];
 }
 
 __global__ void __launch_bounds__(kSelectThreads)
@@ -386,7 +286,7 @@ size_t refit_smem(int D, int n_elite)
 
 }  // namespace
 
-size_t select_smem_bytes(int N) { return size_t(N) * (2 * sizeof(unsigned long long) + 1) + 16; }
+size_t select_smem_bytes(int N) { return size_t(pow2_at_least(N)) * (sizeof(unsigned long long) + sizeof(int)) + 16; }
 size_t refit_smem_bytes(int D, int n_elite) { return refit_smem(D, n_elite); }
 
 cudaError_t launch_select_batch(const CemArgs *args_dev, int n, size_t smem, cudaStream_t st)
@@ -410,7 +310,7 @@ cudaError_t launch_refit_batch(const CemArgs *args_dev, int n, int D_max, size_t
 cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx,
                           cudaStream_t st)
 {
-    const size_t smem = size_t(N) * (2 * sizeof(unsigned long long) + 1) + 16;
+    const size_t smem = select_smem_bytes(N);
     static size_t granted = 0;
     cudaError_t e = reserve_smem(select_kernel, smem, granted);
     if (e != cudaSuccess) return e;
