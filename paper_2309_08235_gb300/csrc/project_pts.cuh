@@ -696,7 +696,47 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                 g[ax * NF + f] = acc2.x + acc2.y;
             }
         }
-        seg_sum_n<DIMS * NF>(g, lane, send);
+        // reduce g over the sample's threads.  2-D with an even TPS: the lanes
+        // 2i, 2i+1 always share a sample, so one exchange leaves the x-axis
+        // values on even lanes and the y-axis values on odd lanes, and the
+        // segmented sum runs over stride-2 lanes on half the values.
+        float *part = sPart + size_t(k & 1) * S * L.maxw * PD;
+        if (DIMS == 2 && (TPS & 1) == 0) {
+            const bool odd = (lane & 1) != 0;
+            float h[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const float other = __shfl_xor_sync(kFull, odd ? g[f] : g[NF + f], 1);
+                h[f] = (odd ? g[NF + f] : g[f]) + other;
+            }
+#pragma unroll
+            for (int d = 2; d < 32; d <<= 1) {
+                float o[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) o[f] = __shfl_down_sync(kFull, h[f], d);
+                if (lane + d <= send) {
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) h[f] += o[f];
+                }
+            }
+            // the segment's first two lanes hold its x and y sums
+            const bool hx = act && !odd && (lane == 0 || j == 0);
+            const bool hy = act && odd && (lane == 1 || j == 1);
+            if (hx || hy) {
+                float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD + (hy ? nv : 0) + kFree0;
+#pragma unroll
+                for (int f = 0; f < NF; ++f) dst[f] = h[f];
+            }
+        } else {
+            seg_sum_n<DIMS * NF>(g, lane, send);
+            if (head) {
+                float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD;
+#pragma unroll
+                for (int ax = 0; ax < DIMS; ++ax)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) dst[ax * nv + kFree0 + f] = g[ax * NF + f];
+            }
+        }
         if constexpr (WL) {
 #pragma unroll
             for (int r = 0; r < R; ++r)
@@ -706,14 +746,6 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                     rsum[r][1][ax] += rv[r][ax];
                     rsum[r][2][ax] += ra[r][ax];
                 }
-        }
-        float *part = sPart + size_t(k & 1) * S * L.maxw * PD;
-        if (head) {
-            float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD;
-#pragma unroll
-            for (int ax = 0; ax < DIMS; ++ax)
-#pragma unroll
-                for (int f = 0; f < NF; ++f) dst[ax * nv + kFree0 + f] = g[ax * NF + f];
         }
         __syncthreads();
         // ---- D: multiplier step (eq. lag) and shared-inverse step in the state
