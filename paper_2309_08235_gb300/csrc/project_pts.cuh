@@ -58,7 +58,9 @@ struct PtsLayout {
     size_t obs, srec, mrec, W, cd, lam, xi, part, part2, total;
 };
 
-__host__ __device__ inline int pts_tps(int n_p, int R) { return (n_p + R - 1) / R; }
+// Threads per sample, rounded up to an even count so the lanes 2i, 2i + 1 of
+// a warp always hold the same sample (the paired reduction of phase C).
+__host__ __device__ inline int pts_tps(int n_p, int R) { return (((n_p + R - 1) / R) + 1) & ~1; }
 
 // Most samples one warp can touch (its 32 consecutive threads cover TPS-thread
 // blocks); every warp keeps the multiplier and coefficient state of each of
@@ -109,23 +111,6 @@ __device__ __forceinline__ T seg_sum(T v, int lane, int send)
         if (lane + d <= send) v += o;
     }
     return v;
-}
-
-// The same for N values at once, step by step across the values so the
-// shuffles of one step are independent of each other.
-template <int N>
-__device__ __forceinline__ void seg_sum_n(float (&v)[N], int lane, int send)
-{
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        float o[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) o[i] = __shfl_down_sync(kFull, v[i], d);
-        if (lane + d <= send) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) v[i] += o[i];
-        }
-    }
 }
 
 // Residual contribution of an active pair into registers (the arithmetic of
@@ -696,45 +681,41 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                 g[ax * NF + f] = acc2.x + acc2.y;
             }
         }
-        // reduce g over the sample's threads.  2-D with an even TPS: the lanes
-        // 2i, 2i+1 always share a sample, so one exchange leaves the x-axis
-        // values on even lanes and the y-axis values on odd lanes, and the
-        // segmented sum runs over stride-2 lanes on half the values.
+        // reduce g over the sample's threads: the lanes 2i, 2i + 1 always share
+        // a sample (TPS is even), so one exchange leaves the first half of the
+        // values on even lanes and the second half on odd lanes, and the
+        // segmented sum runs over stride-2 lanes on half the values
+        constexpr int V = DIMS * NF, VH = (V + 1) / 2;
         float *part = sPart + size_t(k & 1) * S * L.maxw * PD;
-        if (DIMS == 2 && (TPS & 1) == 0) {
+        {
             const bool odd = (lane & 1) != 0;
-            float h[NF];
+            float h[VH];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                const float other = __shfl_xor_sync(kFull, odd ? g[f] : g[NF + f], 1);
-                h[f] = (odd ? g[NF + f] : g[f]) + other;
+            for (int i = 0; i < VH; ++i) {
+                const float hi = VH + i < V ? g[VH + i] : 0.f;
+                const float other = __shfl_xor_sync(kFull, odd ? g[i] : hi, 1);
+                h[i] = (odd ? hi : g[i]) + other;
             }
 #pragma unroll
             for (int d = 2; d < 32; d <<= 1) {
-                float o[NF];
+                float o[VH];
 #pragma unroll
-                for (int f = 0; f < NF; ++f) o[f] = __shfl_down_sync(kFull, h[f], d);
+                for (int i = 0; i < VH; ++i) o[i] = __shfl_down_sync(kFull, h[i], d);
                 if (lane + d <= send) {
 #pragma unroll
-                    for (int f = 0; f < NF; ++f) h[f] += o[f];
+                    for (int i = 0; i < VH; ++i) h[i] += o[i];
                 }
             }
-            // the segment's first two lanes hold its x and y sums
-            const bool hx = act && !odd && (lane == 0 || j == 0);
-            const bool hy = act && odd && (lane == 1 || j == 1);
-            if (hx || hy) {
-                float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD + (hy ? nv : 0) + kFree0;
+            // the segment's first two lanes hold the sums of the two halves
+            const bool h0 = act && !odd && (lane == 0 || j == 0);
+            const bool h1 = act && odd && (lane == 1 || j == 1);
+            if (h0 || h1) {
+                float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD + kFree0;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) dst[f] = h[f];
-            }
-        } else {
-            seg_sum_n<DIMS * NF>(g, lane, send);
-            if (head) {
-                float *dst = part + (size_t(sc) * L.maxw + (warp - fw)) * PD;
-#pragma unroll
-                for (int ax = 0; ax < DIMS; ++ax)
-#pragma unroll
-                    for (int f = 0; f < NF; ++f) dst[ax * nv + kFree0 + f] = g[ax * NF + f];
+                for (int i = 0; i < VH; ++i) {
+                    const int v = (h1 ? VH : 0) + i;
+                    if (v < V) dst[(v / NF) * nv + (v % NF)] = h[i];
+                }
             }
         }
         if constexpr (WL) {
