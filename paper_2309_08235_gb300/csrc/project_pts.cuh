@@ -13,13 +13,14 @@
 //   * phase B tests the thread's points against every obstacle (no obstacle
 //     chunks): static obstacles four at a time from "quad" records (one f32x2
 //     FMA evaluates a point against two obstacles), moving ones two at a time;
-//     a running three-input minimum and one warp vote per batch find the rare
-//     candidates, which are recomputed with the same operations and tested
-//     exactly; residuals S_o accumulate in registers;
+//     three-input minima find the rare candidates, each thread records its
+//     candidate batches and, after the loop, recomputes them with the same
+//     operations and tests them exactly; residuals S_o accumulate in registers;
 //   * phase C forms each thread's share of g on the free columns and reduces
 //     it over the sample's threads with a segmented warp reduction (a warp may
-//     hold the end of one sample and the start of the next), one partial per
-//     (sample, warp) in shared memory, summed in a fixed order;
+//     hold the end of one sample and the start of the next; lanes 2i, 2i + 1
+//     always share a sample), one partial per (sample, warp) in shared memory,
+//     summed in a fixed order;
 //   * phase D: every warp holds, for each sample it touches, the free
 //     coefficients c, multipliers lambda_F and sample xi_F in registers of
 //     dims * nf "state lanes" (one per axis and free column); after the single
