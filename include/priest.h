@@ -318,6 +318,16 @@ priest_status priest_project_plain(priest_ctx *ctx, const priest_problem *prob, 
 priest_status priest_tc_selftest(int n, int k, int swap, const uint16_t *a_host, const uint16_t *b_host,
                                  float *d_host);
 
+/* Diagnostic of the Cholesky factor used for the sampling factor
+ * chol(Sigma + eps I) (Alg. 1, in the setup and after every refit): factors
+ * the D x D symmetric matrix a_host (row-major, host; the lower triangle is
+ * read) on one CTA of `threads` threads and writes L (row-major, host, strict
+ * upper triangle zero) to l_host.  1 <= D <= PRIEST_MAX_D; threads a multiple
+ * of 32 in [32, 1024].  PRIEST_ERR_NUMERIC if a pivot was not a positive
+ * normal number (that pivot is taken as 1 and l_host is still written).
+ * Allocates and synchronises; for tests. */
+priest_status priest_chol_selftest(int D, int threads, const double *a_host, double *l_host);
+
 /* Waits for the context stream and reports any kernel-side error status. */
 priest_status priest_sync(priest_ctx *ctx);
 

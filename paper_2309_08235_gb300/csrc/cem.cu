@@ -142,41 +142,49 @@ __device__ void refit_body(int D, int row, const double *xb, const double *r, co
                            double *mu_new, double *Lout, unsigned *counter, int *status, double *best_out)
 {
     extern __shared__ __align__(16) double s_dyn[];
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     const int chunk = max(1, min(n_elite, int(kRefitChunkBytes / (sizeof(double) * D))));
     double *w = s_dyn;                 // n_elite weights
-    double *mnew = w + n_elite;        // D
+    double *wr = w + n_elite;          // n_elite: w_m (x_m,row - mu'_row)
+    double *mnew = wr + n_elite;       // D
     double *part = mnew + D;           // T partial sums
     double *xe = part + T;             // chunk x D staged elite rows
     double *A = xe;                    // D x D (last CTA, reuses the staging area)
     __shared__ double s_red[kRefitThreads / 32];
-    __shared__ double s_sw, s_tr;
+    __shared__ double s_isw, s_eps;
     __shared__ int s_last, s_flag;
 
-    // weights: elites are sorted by c_aug, so delta = c_aug of the first
+    // elite rows m0 .. m0 + mc - 1 into xe, one warp per row
+    auto stage = [&](int m0, int mc) {
+        for (int m = warp; m < mc; m += nw) {
+            const double *src = xb + size_t(elite[m0 + m]) * D;
+            for (int q = lane; q < D; q += 32) xe[m * D + q] = src[q];
+        }
+    };
+    stage(0, min(chunk, n_elite));
+    // weights w_m = exp(-(c_aug_m - delta) / gamma); the elites are sorted by
+    // c_aug, so delta is the first one's
     const int e0 = elite[0];
-    const double delta = c1[e0] + r[e0];
-    __shared__ double s_ig;
-    if (tid == 0) s_ig = 1.0 / gamma;
-    __syncthreads();
-    const double ig = s_ig;
     double psum = 0.0;
-    for (int m = tid; m < n_elite; m += T) {
-        const int i = elite[m];
-        const double wm = exp(-((c1[i] + r[i]) - delta) * ig);
-        w[m] = wm;
-        psum += wm;
+    if (tid < n_elite) {
+        const double delta = c1[e0] + r[e0];
+        const double ig = rcp_any(gamma);
+        for (int m = tid; m < n_elite; m += T) {
+            const int i = elite[m];
+            const double wm = exp(-((c1[i] + r[i]) - delta) * ig);
+            w[m] = wm;
+            psum += wm;
+        }
     }
     for (int off = 16; off > 0; off >>= 1) psum += __shfl_xor_sync(kFull, psum, off);
     if (lane == 0) s_red[warp] = psum;
     __syncthreads();
-    if (tid == 0) {
-        double sw = 0.0;
-        for (int k = 0; k < T / 32; ++k) sw += s_red[k];
-        s_sw = sw;
+    // 1 / (sum of the weights) on warp 0, beside pass 1
+    if (warp == 0) {
+        double sw = lane < nw ? s_red[lane] : 0.0;
+        for (int off = kRefitThreads / 64; off > 0; off >>= 1) sw += __shfl_xor_sync(kFull, sw, off);
+        if (lane == 0) s_isw = rcp_any(sw);
     }
-    __syncthreads();
-    const double sw = s_sw;
     // thread (d, slice): column d, elites m = slice, slice + nslice, ...
     const int nslice = max(1, T / D);
     const int d = tid % D, slice = tid / D;
@@ -185,16 +193,15 @@ __device__ void refit_body(int D, int row, const double *xb, const double *r, co
     double acc = 0.0;
     for (int m0 = 0; m0 < n_elite; m0 += chunk) {
         const int mc = min(chunk, n_elite - m0);
-        __syncthreads();
-        for (int e = tid; e < mc * D; e += T) xe[e] = xb[size_t(elite[m0 + e / D]) * D + e % D];
-        __syncthreads();
+        if (m0 > 0) {
+            __syncthreads();
+            stage(m0, mc);
+            __syncthreads();
+        }
         if (worker)
             for (int m = slice; m < mc; m += nslice) acc = fma(w[m0 + m], xe[m * D + d], acc);
     }
     part[tid] = worker ? acc : 0.0;
-    __syncthreads();
-    __shared__ double s_isw;
-    if (tid == 0) s_isw = 1.0 / sw;
     __syncthreads();
     const double isw = s_isw;
     if (tid < D) {
@@ -203,21 +210,22 @@ __device__ void refit_body(int D, int row, const double *xb, const double *r, co
         mnew[tid] = (1.0 - sigma) * mu[tid] + sigma * (s * isw);
     }
     __syncthreads();
-    // pass 2: row `row` of the new covariance (eq. update_covariance, around the new mean)
+    // pass 2: row `row` of the new covariance (eq. update_covariance, around
+    // the new mean), with w_m (x_m,row - mu'_row) formed once per elite
     acc = 0.0;
     const double mrow = mnew[row], md = mnew[d];
     for (int m0 = 0; m0 < n_elite; m0 += chunk) {
         const int mc = min(chunk, n_elite - m0);
         if (m0 > 0 || chunk < n_elite) {
             __syncthreads();
-            for (int e = tid; e < mc * D; e += T) xe[e] = xb[size_t(elite[m0 + e / D]) * D + e % D];
+            stage(m0, mc);
             __syncthreads();
         }
+        for (int m = tid; m < mc; m += T) wr[m0 + m] = w[m0 + m] * (xe[m * D + row] - mrow);
+        __syncthreads();
         if (worker)
-            for (int m = slice; m < mc; m += nslice)
-                acc = fma(w[m0 + m], (xe[m * D + row] - mrow) * (xe[m * D + d] - md), acc);
+            for (int m = slice; m < mc; m += nslice) acc = fma(wr[m0 + m], xe[m * D + d] - md, acc);
     }
-    __syncthreads();
     part[tid] = worker ? acc : 0.0;
     __syncthreads();
     if (tid < D) {
@@ -234,15 +242,17 @@ __device__ void refit_body(int D, int row, const double *xb, const double *r, co
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int q = tid; q < D; q += T) mu[q] = mu_new[q];
-    if (tid == 0) {
+    for (int q = tid; q < D; q += T) mu[q] = mnew[q];  // every CTA formed the same mean
+    if (warp == 0) {
         double tr = 0.0;
-        for (int i = 0; i < D; ++i) tr += cov[i * D + i];
-        s_tr = chol_eps * tr / double(D);
+        for (int i = lane; i < D; i += 32) tr += __ldcg(cov + i * D + i);
+        for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(kFull, tr, off);
+        if (lane == 0) s_eps = chol_eps * tr * rcp_fast(double(D));
     }
     __syncthreads();
-    const double eps = s_tr;
-    for (int e = tid; e < D * D; e += T) A[e] = cov[e] + ((e / D == e % D) ? eps : 0.0);
+    const double eps = s_eps;
+    for (int i = warp; i < D; i += nw)
+        for (int k = lane; k < D; k += 32) A[i * D + k] = __ldcg(cov + i * D + k) + (i == k ? eps : 0.0);
     __syncthreads();
     const bool ok = block_cholesky(A, D, &s_flag);
     for (int e = tid; e < D * D; e += T) Lout[e] = A[e];
@@ -277,11 +287,24 @@ __global__ void __launch_bounds__(kRefitThreads) refit_batch_kernel(const CemArg
                a.mu_new, a.L, a.counter, a.status, a.best_out);
 }
 
+// Diagnostic: block_cholesky on one CTA of any width (the refit runs it on
+// 256 threads, the setup on 512).
+__global__ void chol_selftest_kernel(double *A, int D, int *ok)
+{
+    extern __shared__ __align__(16) double s_a[];
+    __shared__ int s_flag;
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) s_a[e] = A[e];
+    __syncthreads();
+    const bool good = block_cholesky(s_a, D, &s_flag);
+    for (int e = threadIdx.x; e < D * D; e += blockDim.x) A[e] = s_a[e];
+    if (threadIdx.x == 0) *ok = good ? 1 : 0;
+}
+
 size_t refit_smem(int D, int n_elite)
 {
-    const size_t chunk = std::max<size_t>(1, std::min<size_t>(n_elite, 96 * 1024 / (sizeof(double) * D)));
+    const size_t chunk = std::max<size_t>(1, std::min<size_t>(n_elite, kRefitChunkBytes / (sizeof(double) * D)));
     const size_t stage = std::max(chunk * D, size_t(D) * D);
-    return (size_t(n_elite) + D + kRefitThreads + stage) * sizeof(double);
+    return (2 * size_t(n_elite) + D + kRefitThreads + stage) * sizeof(double);
 }
 
 }  // namespace
@@ -323,9 +346,7 @@ cudaError_t launch_refit(int D, const double *xb, const double *r, const double 
                          double *mu_new, double *L, unsigned *counter, int *status, double *best_out,
                          cudaStream_t st)
 {
-    const size_t chunk = std::max<size_t>(1, std::min<size_t>(n_elite, 96 * 1024 / (sizeof(double) * D)));
-    const size_t stage = std::max(chunk * D, size_t(D) * D);
-    const size_t smem = (size_t(n_elite) + D + kRefitThreads + stage) * sizeof(double);
+    const size_t smem = refit_smem(D, n_elite);
     static size_t granted = 0;
     cudaError_t e = reserve_smem(refit_kernel, smem, granted);
     if (e != cudaSuccess) return e;
@@ -335,3 +356,33 @@ cudaError_t launch_refit(int D, const double *xb, const double *r, const double 
 }
 
 }  // namespace priest
+
+using namespace priest;
+
+extern "C" priest_status priest_chol_selftest(int D, int threads, const double *a_host, double *l_host)
+{
+    if (D < 1 || D > PRIEST_MAX_D || threads < 32 || threads > 1024 || threads % 32 || !a_host || !l_host)
+        return PRIEST_ERR_INVALID;
+    const size_t bytes = sizeof(double) * D * D;
+    double *A = nullptr;
+    int *ok = nullptr;
+    cudaError_t e = cudaMalloc(&A, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ok, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(A, a_host, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(ok, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        chol_selftest_kernel<<<1, threads, bytes>>>(A, D, ok);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int hok = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(l_host, A, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&hok, ok, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(A);
+    cudaFree(ok);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PRIEST_ERR_CUDA;
+    }
+    return hok ? PRIEST_OK : PRIEST_ERR_NUMERIC;
+}

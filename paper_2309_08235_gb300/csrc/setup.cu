@@ -170,7 +170,7 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
         if (tid == 0) {
             const double piv = s_M[k][k];
             if (!(piv > 0.0)) s_flag = 0;
-            s_ipiv = (piv > 0.0) ? 1.0 / piv : 1.0;
+            s_ipiv = (piv > 0.0) ? rcp_any(piv) : 1.0;
         }
         __syncthreads();
         for (int j = tid; j < 2 * nf; j += T) s_M[k][j] *= s_ipiv;
@@ -230,10 +230,11 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
                 p.cov[e] = (e / D == e % D) ? p.init_std * p.init_std : 0.0;
         __syncthreads();
         __shared__ double s_tr;
-        if (tid == 0) {
+        if (tid < 32) {
             double tr = 0.0;
-            for (int i = 0; i < D; ++i) tr += p.cov[i * D + i];
-            s_tr = p.chol_eps * tr / double(D);
+            for (int i = tid; i < D; i += 32) tr += p.cov[i * D + i];
+            for (int off = 16; off > 0; off >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, off);
+            if (tid == 0) s_tr = p.chol_eps * tr * rcp_fast(double(D));
         }
         __syncthreads();
         const double eps = s_tr;

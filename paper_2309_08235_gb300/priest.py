@@ -34,7 +34,7 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
            "priest_project_noalloc", "priest_plan_batch", "priest_wait", "priest_serve_stats_get",
            "priest_rng_normal_device", "priest_plan_plain", "priest_plan_plain_device",
-           "priest_project_plain", "priest_tc_selftest", "priest_plan_multi"]
+           "priest_project_plain", "priest_tc_selftest", "priest_plan_multi", "priest_chol_selftest"]
 
 
 class PriestError(RuntimeError):
@@ -128,6 +128,7 @@ def lib():
             "priest_plan_plain_device": (C.c_int, [vp, vp, vp, vp]),
             "priest_project_plain": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P, _P, _P]),
             "priest_tc_selftest": (C.c_int, [C.c_int, C.c_int, C.c_int, vp, vp, vp]),
+            "priest_chol_selftest": (C.c_int, [C.c_int, C.c_int, vp, vp]),
             "priest_plan_multi": (C.c_int, [vp, C.POINTER(priest_problem), C.c_int, _P, _P, _P,
                                             C.POINTER(priest_result), C.POINTER(C.c_int), C.POINTER(priest_result)]),
         }
@@ -293,6 +294,17 @@ def priest_tc_selftest(a_bf16, b_bf16, swap=0):
     st = lib().priest_tc_selftest(int(n), int(k), int(swap), a.ctypes.data_as(C.c_void_p),
                                   b.ctypes.data_as(C.c_void_p), d.ctypes.data_as(C.c_void_p))
     return st, d
+
+
+def priest_chol_selftest(a, threads=256):
+    """The device Cholesky of the symmetric matrix a (D x D, FP64) on one CTA
+    of `threads` threads.  Returns (status, L)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    D = a.shape[0]
+    out = np.zeros((D, D), dtype=np.float64)
+    st = lib().priest_chol_selftest(int(D), int(threads), a.ctypes.data_as(C.c_void_p),
+                                    out.ctypes.data_as(C.c_void_p))
+    return st, out
 
 
 def priest_plan_multi(ctx, prob, M, mu0, cov0, z):

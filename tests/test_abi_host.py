@@ -61,3 +61,11 @@ def test_create_validates_config_before_touching_the_gpu(priest):
     with pytest.raises(priest.PriestError) as e:
         priest.priest_create(bad)
     assert e.value.status == priest.PRIEST_ERR_INVALID
+
+
+def test_chol_selftest_validates_arguments_before_touching_the_gpu(priest):
+    a = np.eye(4)
+    for D, threads in ((0, 256), (49, 256), (4, 0), (4, 48), (4, 2048)):
+        st = priest.lib().priest_chol_selftest(D, threads, a.ctypes.data_as(priest.C.c_void_p),
+                                               a.ctypes.data_as(priest.C.c_void_p))
+        assert st == priest.PRIEST_ERR_INVALID, (D, threads)
