@@ -18,7 +18,7 @@ def P():
     return priest
 
 
-@pytest.mark.parametrize("dims,N,n_proj,n_elite", [(2, 64, 45, 7), (3, 50, 50, 1), (2, 33, 20, 20)])
+@pytest.mark.parametrize("dims,N,n_proj,n_elite", [(2, 64, 45, 7), (3, 50, 50, 1), (2, 33, 20, 20), (2, 2500, 1300, 300)])
 def test_fp64_plan_matches_oracle(P, oracle, dims, N, n_proj, n_elite):
     p = scene(dims=dims, n_obs=10, n_dyn=2, n_p=40)
     cem = W.cem_settings(N, 15, 3, n_proj=n_proj, n_elite=n_elite, dims=dims)
