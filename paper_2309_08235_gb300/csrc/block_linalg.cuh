@@ -51,15 +51,15 @@ __device__ __forceinline__ bool positive_normal(double x)
 }
 
 // 1/x for positive_normal(x): the FP64 estimate of the PTX approximate
-// reciprocal, then two Newton-Raphson steps e = 1 - x y, y <- y + y e.
+// reciprocal (relative error below 2^-19 on this part), then one third-order
+// step: with e = 1 - x y, 1/x = y (1 + e + e^2 + ...), so y (1 + e + e^2)
+// leaves an error of e^3 < 2^-57 before the final rounding.
 __device__ __forceinline__ double rcp_fast(double x)
 {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // 1/sqrt(x) for positive_normal(x): the PTX approximate reciprocal square
@@ -91,9 +91,10 @@ constexpr int kCholMaxD = PRIEST_MAX_D;
 // rank-1 update of the textbook form (L[i][j] = A[i][j] / sqrt(A[j][j]))
 // without scaling column j first; L follows at the end in one pass,
 // L[i][k] = A[i][k] / sqrt(A[k][k]).  The thread that updates the next pivot
-// forms its reciprocal at once and column j + 1 is copied into a contiguous
-// buffer as it is written, so each column costs one barrier and the serial
-// chain per column is one update and one reciprocal.  Each thread keeps the
+// (a thread of its own) forms its reciprocal at once, column j + 1 is copied
+// into a contiguous buffer as it is written and the square of its entry in
+// row j + 2 is kept, so each column costs one barrier and the serial chain per
+// column is one fused multiply-add and one reciprocal.  Each thread keeps the
 // same elements at every step: the triangle is numbered by columns from the
 // last one back (column k holds rows k..D-1), so the elements of step j are
 // the first (D-1-j)(D-j)/2 numbers.
@@ -101,6 +102,7 @@ __device__ inline bool block_cholesky(double *A, int D, int *flag_smem)
 {
     __shared__ double s_col[2][kCholMaxD];  // column j (unscaled), by step parity
     __shared__ double s_rcp[kCholMaxD];     // 1 / pivot
+    __shared__ double s_sq[2];              // A[j+1][j]^2, by step parity
     __shared__ unsigned short s_tab[kCholMaxD * (kCholMaxD + 1) / 2];  // (i << 8) | k
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
     const int ntri = D * (D + 1) / 2;
@@ -123,28 +125,41 @@ __device__ inline bool block_cholesky(double *A, int D, int *flag_smem)
         *flag_smem = ok;
         s_rcp[0] = rcp_fast(v);
     }
-    for (int i = 1 + tid; i < D; i += T) s_col[0][i] = A[i * D];
+    for (int i = 1 + tid; i < D; i += T) {
+        const double v = A[i * D];
+        s_col[0][i] = v;
+        if (i == 1) s_sq[0] = v * v;
+    }
     __syncthreads();
+    // the next pivot and its reciprocal on lane 0 of the last warp, which
+    // takes no part in the update, so no other element waits behind the chain
+    const int Tw = nw > 1 ? T - 32 : T, tp = nw > 1 ? T - 32 : 0;
     for (int j = 0; j + 1 < D; ++j) {
         const int m = D - 1 - j, cnt = m * (m + 1) / 2;
         const double r = s_rcp[j];
         const double *col = s_col[j & 1];
         double *nxt = s_col[(j + 1) & 1];
-        for (int p = tid; p < cnt; p += T) {
-            const int ik = s_tab[p], i = ik >> 8, k = ik & 255;
-            double v = fma(-col[i], col[k] * r, A[i * D + k]);
-            if (k == j + 1) {
-                if (i == k) {
-                    if (!positive_normal(v)) {
-                        *flag_smem = 0;
-                        v = 1.0;
-                    }
-                    s_rcp[k] = rcp_fast(v);
-                }
-                nxt[i] = v;
+        if (tid == tp) {
+            const int q = (j + 1) * (D + 1);
+            double v = fma(-s_sq[j & 1], r, A[q]);
+            if (!positive_normal(v)) {
+                *flag_smem = 0;
+                v = 1.0;
             }
-            A[i * D + k] = v;
+            s_rcp[j + 1] = rcp_fast(v);
+            A[q] = v;
         }
+        if (tid < Tw)
+            for (int p = tid; p < cnt; p += Tw) {
+                const int ik = s_tab[p], i = ik >> 8, k = ik & 255;
+                if (i == k && k == j + 1) continue;  // the pivot, above
+                const double v = fma(-col[i], col[k] * r, A[i * D + k]);
+                if (k == j + 1) {
+                    nxt[i] = v;
+                    if (i == k + 1) s_sq[(j + 1) & 1] = v * v;
+                }
+                A[i * D + k] = v;
+            }
         __syncthreads();
     }
     double *rsq = s_col[0];  // free after the last step's barrier
