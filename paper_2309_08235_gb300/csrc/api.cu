@@ -412,8 +412,13 @@ priest_status scratch_for(priest_ctx *ctx, const Shape &sh, const priest_problem
         Shape s2 = sh;
         std::vector<double> c, v, s;
         order_obstacles(s2, pr->center, pr->vel, pr->semi, c, v, s, s2.n_static);
+        // the basis, time stamps and Gram blocks stay valid (and in place)
+        // while the table layout and the basis inputs are unchanged
+        const Shape &o = h->sh;
+        const bool same_tables = o.dims == s2.dims && o.degree == s2.degree && o.nf == s2.nf && o.n_p == s2.n_p &&
+                                 o.n_obs == s2.n_obs && o.horizon == s2.horizon;
+        h->shape_ready = h->shape_ready && same_tables;
         h->sh = s2;
-        h->shape_ready = false;
         carve_ptrs(h, b, k, fp32, z_iters, proj_buffers);
         const size_t ob = sizeof(double) * c.size();
         cudaError_t e = cudaMemcpyAsync(h->center, c.data(), ob, cudaMemcpyHostToDevice, ctx->stream);

@@ -256,6 +256,8 @@ __device__ void select_body(int N, const double *r, const double *c1, int n_proj
 __global__ void __launch_bounds__(kSelectThreads)
     select_kernel(int N, const double *r, const double *c1, int n_proj, int n_elite, int *elite_idx)
 {
+    pdl_trigger();
+    pdl_wait();
     select_body(N, r, c1, n_proj, n_elite, elite_idx);
 }
 
@@ -461,6 +463,8 @@ __global__ void __launch_bounds__(kRefitThreads)
                  double sigma, double gamma, double chol_eps, double *mu, double *cov, double *mu_new,
                  double *Lout, unsigned *counter, int *status, double *best_out)
 {
+    pdl_trigger();
+    pdl_wait();
     refit_body(D, blockIdx.x, xb, r, c1, elite, n_elite, sigma, gamma, chol_eps, mu, cov, mu_new, Lout, counter,
                status, best_out);
 }
@@ -526,8 +530,7 @@ cudaError_t launch_select(int N, const double *r, const double *c1, int n_proj, 
     static size_t granted = 0;
     cudaError_t e = reserve_smem(select_kernel, smem, granted);
     if (e != cudaSuccess) return e;
-    select_kernel<<<1, kSelectThreads, smem, st>>>(N, r, c1, n_proj, n_elite, elite_idx);
-    return cudaGetLastError();
+    return launch_pdl(select_kernel, dim3(1), dim3(kSelectThreads), smem, st, N, r, c1, n_proj, n_elite, elite_idx);
 }
 
 cudaError_t launch_refit(int D, const double *xb, const double *r, const double *c1, const int *elite,
@@ -539,9 +542,8 @@ cudaError_t launch_refit(int D, const double *xb, const double *r, const double 
     static size_t granted = 0;
     cudaError_t e = reserve_smem(refit_kernel, smem, granted);
     if (e != cudaSuccess) return e;
-    refit_kernel<<<D, kRefitThreads, smem, st>>>(D, xb, r, c1, elite, n_elite, sigma, gamma, chol_eps, mu, cov,
-                                                  mu_new, L, counter, status, best_out);
-    return cudaGetLastError();
+    return launch_pdl(refit_kernel, dim3(D), dim3(kRefitThreads), smem, st, D, xb, r, c1, elite, n_elite, sigma,
+                      gamma, chol_eps, mu, cov, mu_new, L, counter, status, best_out);
 }
 
 }  // namespace priest

@@ -6,6 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "priest.h"
@@ -240,6 +241,34 @@ inline cudaError_t reserve_smem(Kernel kernel, size_t bytes, size_t &granted)
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     if (e == cudaSuccess) granted = bytes;
     return e;
+}
+
+// Programmatic dependent launch along the solve's chain of kernels (setup ->
+// projection -> selection -> refit -> projection ...): a kernel launched with
+// launch_pdl may be scheduled while the previous kernel of the stream still
+// runs; it calls pdl_wait() before touching any memory, which returns once
+// that kernel has completed and its writes are visible, so the order of
+// memory accesses is that of plain stream order and only the launch latency
+// overlaps.  pdl_trigger() lets the next kernel be scheduled.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Arguments of the selection and refit stages of one problem (batched launches).

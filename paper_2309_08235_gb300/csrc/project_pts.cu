@@ -39,8 +39,7 @@ cudaError_t launch_pts_one(const ProjParams<float> &p, const Tiling &t, cudaStre
     cudaError_t e = reserve_smem(pts::pts_kernel<DIMS, R, NF, WL>, t.smem, granted);
     if (e != cudaSuccess) return e;
     const int grid = (p.N + t.S - 1) / t.S;
-    pts::pts_kernel<DIMS, R, NF, WL><<<grid, t.threads, t.smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(pts::pts_kernel<DIMS, R, NF, WL>, dim3(grid), dim3(t.threads), t.smem, st, p);
 }
 
 template <int DIMS, int R, int NF = 5>

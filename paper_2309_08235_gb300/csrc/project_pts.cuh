@@ -824,6 +824,8 @@ constexpr int pts_max_threads() { return R <= 2 ? 384 : 256; }
 template <int DIMS, int R, int NF, bool WL>
 __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const ProjParams<float> p)
 {
+    pdl_trigger();
+    pdl_wait();
     pts_body<DIMS, R, NF, WL>(p, blockIdx.x * p.S);
 }
 

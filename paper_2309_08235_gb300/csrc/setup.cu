@@ -254,7 +254,12 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
     }
 }
 
-__global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, double *tab64) { setup_body(p, tab64); }
+__global__ void __launch_bounds__(kSetupThreads) setup_kernel(SetupParams p, double *tab64)
+{
+    pdl_trigger();
+    pdl_wait();
+    setup_body(p, tab64);
+}
 
 // One CTA per problem.
 __global__ void __launch_bounds__(kSetupThreads) setup_batch_kernel(const SetupParams *ps)
