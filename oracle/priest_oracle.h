@@ -92,7 +92,11 @@ void orc_bound_polar(int dims, const double *v, double vmax,
 /* Projection of N samples (Sec. III-A, Appendix eqs. comp_alpha..comp_zeta):
  * xi_bar^0 = Pi_A(xi) (if xi_bar0 == NULL) else xi_bar0; lambda^0 =
  * lambda_io (NULL -> zeros); K alternating-minimisation iterations.
- * Outputs xi_bar (N x D); lambda_io updated in place if non-NULL. */
+ * Outputs xi_bar (N x D); lambda_io updated in place if non-NULL.
+ * Pinned per iteration (dense restatement, Lagrangian minimiser, zero
+ * obstacles = Pi_A, feasible fixed point) and, converged, on a two-variable
+ * case by brute force and the fixed-point identity xi_bar = Pi_A(xi + lambda);
+ * the converged multi-obstacle result in general: parity unpinned. */
 int orc_project(const orc_problem *pr, int K, int N, const double *xi, const double *xi_bar0,
                 double *lambda_io, double *xi_bar_out);
 

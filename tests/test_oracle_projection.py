@@ -203,3 +203,53 @@ def test_teaser_projection_pushes_samples_out(oracle):
     assert np.median(rs[0]) < np.median(r0)
     assert np.median(rs[2]) < np.median(rs[0])
     assert np.median(rs[2]) < 0.1 * np.median(r0)
+
+
+def test_converged_projection_on_a_two_variable_case(oracle):
+    """Degree 6 with both ends at rest leaves one free coefficient per axis
+    (c_3), so the projection of Sec. III-A is a two-variable problem that
+    brute force can check.  One circle of radius 1 at the middle of the
+    straight start-goal line (0, 0) -> (10, 0), horizon 4 s, 41 time stamps,
+    velocity / acceleration bounds inactive; the sample's free coefficients
+    are (5, 0.3).  At convergence the method fixes:
+      * feasibility at every time stamp, checked here from the basis and the
+        circle directly;
+      * the mirror symmetry of the scene (t -> T - t, x -> 10 - x): c_3,x
+        stays 5;
+      * xi_bar = Pi_A(xi + lambda): with r = 0 the targets equal F xi_bar, so
+        the minimiser of eq. lagrange under A xi_bar = b (eq. comp_zeta) is the
+        equality projection of xi + lambda.
+    The alpha / d steps (eqs. comp_alpha .. comp_d) do not involve lambda, so
+    every feasible xi_bar with that property is a fixed point: the method
+    stops at a feasible point, farther from xi than the Euclidean projection
+    found by brute force (distance 2.90 at c_3,y = 3.2; the method stops near
+    c_3,y = 3.94)."""
+    p = W.problem(2, 41, 4.0, [0, 0], [10, 0], [[5.0, 0.0]], None, [[1.0, 1.0]], vmax=1e6, amax=1e6, degree=6)
+    P, _, _ = oracle.basis(6, 41, 4.0)
+    xi = np.array([0, 0, 0, 5.0, 10, 10, 10, 0, 0, 0, 0.3, 0, 0, 0])
+    xb, lam = oracle.project(p, xi[None], 2000)
+    r, _ = oracle.residual_cost(p, xb)
+    xb, lam = xb[0], lam[0]
+    x, y = P @ xb[:7], P @ xb[7:]
+    assert r[0] == 0.0
+    assert ((x - 5.0) ** 2 + y ** 2).min() >= 1.0 - 1e-9
+    assert abs(xb[3] - 5.0) < 1e-9
+    assert np.abs(xb - oracle.project_eq(p, (xi + lam)[None])[0]).max() < 1e-10
+    # brute force: the nearest feasible (c_3,x, c_3,y) to (5, 0.3), coarse grid then fine
+    B3, xfix = P[:, 3], P[:, 4:] @ np.array([10.0, 10.0, 10.0])
+
+    def nearest(cx, cy):
+        CX, CY = np.meshgrid(cx, cy, indexing="ij")
+        X = np.multiply.outer(CX, B3) + xfix
+        Y = np.multiply.outer(CY, B3)
+        d2 = (CX - 5.0) ** 2 + (CY - 0.3) ** 2
+        d2[((X - 5.0) ** 2 + Y ** 2 < 1.0).any(axis=-1)] = np.inf
+        i = np.unravel_index(np.argmin(d2), d2.shape)
+        return CX[i], CY[i], np.sqrt(d2[i])
+
+    cx, cy, _ = nearest(np.arange(3.0, 7.0, 0.01), np.arange(0.0, 6.0, 0.01))
+    cx, cy, dmin = nearest(np.arange(cx - 0.01, cx + 0.01, 1e-4), np.arange(cy - 0.01, cy + 0.01, 1e-4))
+    assert abs(cy - 3.2) < 2e-4 and abs(dmin - 2.9) < 2e-4
+    d_am = np.hypot(xb[3] - 5.0, xb[10] - 0.3)
+    assert d_am >= dmin - 1e-3
+    assert d_am > dmin + 0.5
