@@ -270,13 +270,28 @@ __global__ void __launch_bounds__(kSelectThreads) select_batch_kernel(const CemA
 // Elite rows staged in shared memory per chunk (all of them when they fit).
 constexpr int kRefitChunkBytes = 96 * 1024;
 
+// Dynamic shared memory the refit plans for: the per-elite arrays (weights,
+// pre-weighted row entries: 8 + 8 bytes; indices: 4 bytes), the mean and
+// the partial sums, and a staging area for a chunk of elite rows.
+constexpr int kRefitSmemBudget = 200 * 1024;
+
+// Elite rows staged per chunk: all of them when they fit in kRefitChunkBytes
+// and in what the other arrays leave of kRefitSmemBudget.
+__host__ __device__ inline int refit_chunk(int D, int n_elite)
+{
+    const int row = int(sizeof(double)) * D;
+    const int room = (kRefitSmemBudget - 20 * n_elite - int(sizeof(double)) * (D + kRefitThreads)) / row;
+    int c = kRefitChunkBytes / row;
+    c = c < room ? c : room;
+    c = c < n_elite ? c : n_elite;
+    return c < 1 ? 1 : c;
+}
+
 // Doubles of the staging area: a chunk of elite rows, or the D x D matrix
 // the last CTA factors.
 __host__ __device__ inline int refit_stage_doubles(int D, int n_elite)
 {
-    const int chunk = n_elite < kRefitChunkBytes / int(sizeof(double) * D) ? n_elite
-                                                                            : kRefitChunkBytes / int(sizeof(double) * D);
-    const int c = chunk < 1 ? 1 : chunk;
+    const int c = refit_chunk(D, n_elite);
     return c * D > D * D ? c * D : D * D;
 }
 
@@ -293,7 +308,7 @@ __device__ void refit_body(int D, int row, const double *xb, const double *r, co
 {
     extern __shared__ __align__(16) double s_dyn[];
     const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    const int chunk = max(1, min(n_elite, int(kRefitChunkBytes / (sizeof(double) * D))));
+    const int chunk = refit_chunk(D, n_elite);
     double *w = s_dyn;                 // n_elite weights
     double *wr = w + n_elite;          // n_elite: w_m (x_m,row - mu'_row)
     double *mnew = wr + n_elite;       // D
