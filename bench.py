@@ -1,19 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the PRIEST hot path on GB300: projected sample-iterations per
 second of full solves (Alg. 1: sample, K projection iterations, residual and
-cost, elites, refit, Cholesky) on the 2-D clutter workload.
+cost, elites, refit, Cholesky).
 
-One step = one full solve of one problem: N = 1000 samples, n_p = 100 time
-stamps, 90 static + 10 moving circles in a 30 x 30 m box, degree 10,
-K = 100 projection iterations, L = 5 CEM iterations, 100 elites, FP32
-projection (FP64 sampling / refit / Cholesky / KKT block).  Units per step:
-N * K * L = 5e5 projected sample-iterations.
+Default line: the batched workload of 256 uneven 2-D problems (obstacles
+log-uniform in [10, 400], N in {256, 512, 1024, 2048}, n_p in {60, 100,
+150}, K = 60, L = 3) solved by priest_plan_batch: per CEM iteration one
+persistent projection launch over every problem's samples, one selection and
+one refit launch, replayed as a CUDA graph.  One step = one batched solve of
+all 256 problems; units per step = sum over problems of N K L.  The line also
+carries the single-problem 2-D clutter solve (N = 1000, n_p = 100, K = 100,
+L = 5) and the point-to-point solves (the paper's N_b = 110, 13 CEM
+iterations) as extra keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batched|clutter2d|...]
 
-Under torchrun each rank solves its own replica (no collective on the data
-path); rank 0 prints one JSON line.  ``--impl reference`` times the FP64 CPU
-oracle on a bounded sample of the same workload on this host's cores.
+Under torchrun each rank solves its own 256 problems (a disjoint share of a
+256 N problem set; no collective on the data path); rank 0 prints one JSON
+line.  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of
+the same workload on this host's cores.
 """
 from __future__ import annotations
 
@@ -25,6 +31,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -34,17 +41,13 @@ if ROOT not in sys.path:
 
 from paper_2309_08235_gb300 import replicas as R  # noqa: E402
 
-WORKLOAD = "clutter2d_fp32"
 METRIC = "projected sample-iters/s; solves/s & p99 latency vs plain GPU path, at oracle tol"
 UNIT = "sample-iters/s"
-N_SM = 152
 FP32_LANES = 128
-SM_MAX_MHZ = 2070.0
-
+BATCH_K, BATCH_L, BATCH_N = 60, 3, 256
 
 WORKLOADS = {"clutter2d": "clutter2d_fp32", "ellipsoid3d": "ellipsoid3d_mixed", "p2p2d": "p2p2d", "p2p3d": "p2p3d",
-             "clutter2d_bounds": "clutter2d_bounds",
-             "dynamic2d": "dynamic2d"}
+             "clutter2d_bounds": "clutter2d_bounds", "dynamic2d": "dynamic2d"}
 
 
 def workload_desc(p, cem, precision="fp32", name="clutter2d"):
@@ -68,6 +71,11 @@ def workload_desc(p, cem, precision="fp32", name="clutter2d"):
             f"N={cem['n_samples']} samples, n_p={p['n_p']}, degree {p['degree']}, "
             f"K={cem['proj_iters']} projection iters, L={cem['cem_iters']} CEM iters, "
             f"{cem['n_elite']} elites, {prec}")
+
+
+BATCH_DESC = ("batched: 256 uneven 2-D problems (obstacles log-uniform 10-400, 10 % moving; N in {256, 512, 1024, "
+              "2048}; n_p in {60, 100, 150}; degree 10), K=60 projection iters, L=3 CEM iters, N/10 elites, FP32 "
+              "projection; one persistent projection launch per CEM iteration over all problems, CUDA graph replay")
 
 
 def flops_per_sample_iter(p, nf=5):
@@ -106,8 +114,28 @@ def fma_pipe_flops_per_sample_iter(p, nf=None):
             + 2 * dims * nf * nf)
 
 
-def fp32_peak_tflops():
-    return N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+def sm_count(dev=None):
+    import torch
+
+    return int(torch.cuda.get_device_properties(dev if dev is not None else 0).multi_processor_count)
+
+
+def sm_max_mhz(clocks):
+    """The SM clock ceiling: nvidia-smi's maximum seen during the run, else
+    the measured peaks file, else the part's nominal 2070 MHz."""
+    if clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"])
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return float(json.load(open(path))["sm_max_mhz"])
+        except Exception:
+            pass
+    return 2070.0
+
+
+def fp32_peak_tflops(n_sm, mhz):
+    return n_sm * FP32_LANES * 2 * mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -167,20 +195,88 @@ def dist_env():
     return R.env()
 
 
-def cpu_oracle_rate(p, cem, n_samples, seed=0):
-    """Projected sample-iterations/s of the FP64 oracle (single thread) on
-    n_samples samples of the workload (K projection iterations + residual)."""
+def stored_traffic(key):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/traffic.txt), or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        if ln.startswith(key + ":"):
+            return int(float(ln.split(":", 1)[1]))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# The FP64 oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_projection_rate(jobs, threads):
+    """Projected sample-iterations/s of the FP64 oracle on `jobs`, a list of
+    (problem, samples, K): each job's K projection iterations + residual /
+    cost.  threads > 1 runs the jobs' rows in parallel (the oracle is plain
+    reentrant C called through ctypes, which releases the interpreter lock),
+    one chunk of rows per task."""
+    import oracle as O
+
+    O.build()
+    tasks = []
+    for p, xi, K in jobs:
+        step = max(1, int(np.ceil(len(xi) / max(1, threads))) if threads > 1 else len(xi))
+        for a in range(0, len(xi), step):
+            tasks.append((p, xi[a:a + step], K))
+
+    def run(t):
+        p, xi, K = t
+        xb, _ = O.project(p, xi, K)
+        O.residual_cost(p, xb)
+
+    units = sum(len(xi) * K for _, xi, K in jobs)
+    t0 = time.perf_counter()
+    if threads > 1:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, tasks))
+    else:
+        for t in tasks:
+            run(t)
+    dt = time.perf_counter() - t0
+    return units / dt, dt
+
+
+def batched_oracle_jobs(scale=8, n_sub=16, seed=0):
+    """The bounded sample of the batched workload: the first n_sub of its
+    seeded problems, scale * N_i / 256 rows of problem i (so the rows keep
+    the workload's weighting of problems by sample count), K = 60."""
+    import oracle as O
+    from paper_2309_08235_gb300 import workloads as W
+
+    O.build()
+    jobs = []
+    for i, (p, N) in enumerate(W.batched_problems(n_sub)):
+        m = max(1, scale * N // 256)
+        xi = O.default_mean(p) + 2.0 * W.normals(seed * 1000 + i, (m, 22))
+        jobs.append((p, xi, BATCH_K))
+    return jobs
+
+
+def single_oracle_jobs(p, cem, n_samples, seed=0):
     import oracle as O
     from paper_2309_08235_gb300 import workloads as W
 
     O.build()
     D = p["dims"] * (p["degree"] + 1)
     xi = O.default_mean(p) + cem["init_std"] * W.normals(seed, (n_samples, D))
-    t0 = time.perf_counter()
-    xb, _ = O.project(p, xi, cem["proj_iters"])
-    O.residual_cost(p, xb)
-    dt = time.perf_counter() - t0
-    return n_samples * cem["proj_iters"] / dt, dt
+    return [(p, xi, cem["proj_iters"])]
+
+
+def cpu_baselines(jobs, sample_desc):
+    """The oracle on all host cores and on one thread (same sample)."""
+    cores = os.cpu_count() or 1
+    rate_all, dt_all = oracle_projection_rate(jobs, cores)
+    rate_1, dt_1 = oracle_projection_rate(jobs, 1)
+    return {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_desc}; FP64 oracle, rows split over {cores} threads, {dt_all:.1f} s",
+            "single_thread": {"value": rate_1, "unit": UNIT, "cores": 1, "seconds": dt_1}}
 
 
 def run_reference(args):
@@ -189,56 +285,67 @@ def run_reference(args):
         return 0
     from paper_2309_08235_gb300 import workloads as W
 
-    p, cem = W.workload(WORKLOAD)
-    # calibrate, then size each step so the whole run stays within ~2 minutes
-    rate, _ = cpu_oracle_rate(p, dict(cem, proj_iters=10), 1)
-    per_step_s = 120.0 / max(1, args.steps + args.warmup)
-    m = max(1, int(per_step_s * rate / cem["proj_iters"]))
-    for _ in range(args.warmup):
-        cpu_oracle_rate(p, cem, m)
+    cores = os.cpu_count() or 1
+    if args.workload == "batched":
+        desc = BATCH_DESC
+        make = lambda k: batched_oracle_jobs(scale=args.ref_scale, seed=k)  # noqa: E731
+        sample = (f"rows {args.ref_scale} N_i / 256 of each of the first 16 seeded problems of the batched "
+                  f"workload (K=60 projection iterations + residual / cost) per step")
+    else:
+        p, cem = W.workload(WORKLOADS[args.workload])
+        desc = workload_desc(p, cem, name=args.workload)
+        # calibrate, then size each step so the whole run stays within ~2 minutes
+        rate, _ = oracle_projection_rate(single_oracle_jobs(p, dict(cem, proj_iters=10), cores), cores)
+        per_step_s = 120.0 / max(1, args.steps + args.warmup)
+        m = max(cores, int(per_step_s * rate / cem["proj_iters"]))
+        make = lambda k: single_oracle_jobs(p, cem, m, seed=k)  # noqa: E731
+        sample = f"{m} samples x {cem['proj_iters']} projection iterations (+ residual / cost) per step"
+    for k in range(args.warmup):
+        oracle_projection_rate(make(100 + k), cores)
+    units, secs = 0.0, 0.0
     times = []
     for k in range(args.steps):
-        _, dt = cpu_oracle_rate(p, cem, m, seed=k + 1)
+        jobs = make(k + 1)
+        rate, dt = oracle_projection_rate(jobs, cores)
+        units += rate * dt
+        secs += dt
         times.append(dt)
-    units = m * cem["proj_iters"]
-    value = units * len(times) / sum(times)
-    sample = (f"{m} samples x {cem['proj_iters']} projection iterations (+ residual/cost) of the "
-              f"{WORKLOAD} workload per step, FP64 oracle, 1 thread")
+    value = units / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": workload_desc(p, cem), "impl": "FP64 CPU oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": desc, "impl": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample + f", FP64 oracle, rows split over {cores} threads"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args):
+# ---------------------------------------------------------------------------
+# One problem per step (the 2-D clutter, 3-D, point-to-point workloads)
+# ---------------------------------------------------------------------------
+
+def measure_single(args, name, steps, warmup, precision="fp32", plain_steps=0, e2e=True, cpu=False, dist=None):
+    """Full solves of one problem per step on this rank's GPU: the device
+    timed rate, the projection kernel's roofline, optionally the end-to-end
+    rate through priest_plan_z with host buffers, the plain per-problem path
+    and the oracle's baseline.  Returns the line's dict."""
     import torch
 
-    from paper_2309_08235_gb300 import build as B
     from paper_2309_08235_gb300 import priest as P
     from paper_2309_08235_gb300 import workloads as W
 
     rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    B.build()
-    p, cem = W.workload(WORKLOADS.get(args.workload, WORKLOAD))
+    p, cem = W.workload(WORKLOADS[name])
     N, K, L = cem["n_samples"], cem["proj_iters"], cem["cem_iters"]
     D = p["dims"] * (p["degree"] + 1)
     units = N * K * L
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    prec = P.PRIEST_MIXED_BF16 if args.precision == "mixed" else P.PRIEST_FP32
+    prec = P.PRIEST_MIXED_BF16 if precision == "mixed" else P.PRIEST_FP32
     ctx = P.Context(p, cem, precision=prec, stream=stream.cuda_stream)
-    prob, keep = P.make_problem(p, cem)
+    prob, keep = P.make_problem(p, cem, per_problem_shape=True)
     h = P.priest_load(ctx.h, prob)
     z_host = torch.from_numpy(W.normals(1000 + rank, (L, N, D))).pin_memory()
     z_dev = z_host.to(dev)
@@ -249,7 +356,7 @@ def run_ours(args):
         P.priest_plan_device(ctx.h, h, z_dev.data_ptr(), out.data_ptr())
 
     with torch.cuda.stream(stream):
-        for _ in range(max(3, args.warmup)):
+        for _ in range(max(3, warmup)):
             step()
     stream.synchronize()
     P.priest_sync(ctx.h)
@@ -260,7 +367,7 @@ def run_ours(args):
     P.priest_profile_read(ctx.h)
     P.priest_profile_enable(ctx.h, 1)
     l0 = ctx.launches()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     R.barrier(dist)
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
@@ -275,68 +382,70 @@ def run_ours(args):
     clocks = sampler.stop()
     P.priest_profile_enable(ctx.h, 0)
     launches = ctx.launches() - l0
+    kind = P.priest_last_kernel(ctx.h)
     n_proj_launch, proj_ms = P.priest_profile_read(ctx.h)
     P.priest_sync(ctx.h)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    # whole job: all ranks' units over the slowest rank's device time
-    value, t_max, _ = R.job_rate(units * args.steps, sum(step_ms) / 1e3, dist, dev)
+    value, t_max, _ = R.job_rate(units * steps, sum(step_ms) / 1e3, dist, dev)
     total_ms = 1e3 * t_max
 
     # ---- roofline of the dominant kernel (the fused projection)
     avg_proj_ms = proj_ms / max(1, n_proj_launch)
     flops_launch = flops_per_sample_iter(p) * N * K
+    n_sm = sm_count(dev)
+    mhz = sm_max_mhz(clocks)
+    peak = fp32_peak_tflops(n_sm, mhz)
     achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
-    peak = fp32_peak_tflops()
-    pipe_tflops = fma_pipe_flops_per_sample_iter(p) * N * K / (avg_proj_ms / 1e3) / 1e12
-    traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if args.precision != "fp32":
-        kname = "project_tc_kernel (tcgen05 pair tests, %d-D)" % p["dims"]
-    elif p.get("degree", 10) == 10 and (free_coefficients(p) == 5 or (free_coefficients(p) == 7 and p["dims"] == 2)):
-        kname = "pts_kernel (FP32 point-owner projection, %d-D)" % p["dims"]
-    else:
-        kname = "project_kernel (FP32 chunked projection, %d-D, %d free coefficients)" % (p["dims"], free_coefficients(p))
-    if os.path.exists(prof_path) and args.precision == "fp32" and p["dims"] == 2 and args.workload == "clutter2d":
-        for ln in open(prof_path):
-            if ln.startswith("pts_kernel_bytes_per_launch:"):
-                traffic = int(ln.split(":", 1)[1])
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-                "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
-                "flops_per_launch": flops_launch,
+    pipe = fma_pipe_flops_per_sample_iter(p) * N * K / (avg_proj_ms / 1e3) / 1e12
+    kname = {0: "project_kernel (FP32 chunked projection)", 1: "pts_kernel (FP32 point-owner projection)",
+             2: "project_tc_kernel (tcgen05 pair tests)"}.get(kind, "projection kernel")
+    traffic = stored_traffic("pts_kernel_bytes_per_launch") if (name == "clutter2d" and kind == 1) else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": f"{kname}, {p['dims']}-D", "avg_launch_ms": avg_proj_ms,
+                "launches": n_proj_launch, "flops_per_launch": flops_launch,
                 "flops_note": "algorithmic: direct polar pair test 14 (2-D) / 22 (3-D) flops per pair, "
                               "vel/acc blocks, both basis products over all n_v columns, shared-inverse step",
-                "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-                "fma_pipe": {"achieved": pipe_tflops, "frac": pipe_tflops / peak,
+                "peak_note": f"FP32 FMA peak derived: {n_sm} SMs x 128 lanes x 2 flop x {mhz:g} MHz",
+                "traffic_note": ("dram bytes per launch from one ncu capture (profiles/traffic.txt), not measured "
+                                 "in this run") if traffic else None,
+                "fma_pipe": {"achieved": pipe, "frac": pipe / peak,
                              "note": "flops the kernel issues on the FMA pipe (expanded 2-FMA pair pre-filter, "
                                      "free-column basis products)"}}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(n_sm, clocks["sm_mhz"])
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(p, cem, precision, name),
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU", "units_per_step": units},
+            "solves_per_s": steps * world / (total_ms / 1e3),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
 
-    # ---- end to end through the host-pointer C ABI (pinned z in, result out)
-    res = P.priest_result()
-    z_np = z_host.numpy()
-    for _ in range(2):
-        P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
-    e2e_steps = max(3, min(args.steps, 50))
-    R.barrier(dist)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
-    e2e_rate, e2e_s, _ = R.job_rate(units * e2e_steps, time.perf_counter() - t0, dist, dev)
-    obs_bytes = 8 * (p["n_obs"] * (2 * p["dims"] + 2))
-    e2e = {"value": e2e_rate, "unit": UNIT,
-           "h2d_bytes_per_step": int(z_np.nbytes + obs_bytes),
-           "d2h_bytes_per_step": int(8 * (D + 4 + D)),
-           "api": "priest_plan_z (host buffers, blocking)"}
+    if e2e:
+        # ---- end to end through the host-pointer C ABI (pinned z in, result out)
+        res = P.priest_result()
+        z_np = z_host.numpy()
+        for _ in range(2):
+            P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
+        e2e_steps = max(3, min(steps, 50))
+        R.barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            P.priest_plan_z(ctx.h, prob, None, None, z_np, res)
+        e2e_rate, _, _ = R.job_rate(units * e2e_steps, time.perf_counter() - t0, dist, dev)
+        obs_bytes = 8 * (p["n_obs"] * (2 * p["dims"] + 2))
+        line["e2e"] = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(z_np.nbytes + obs_bytes),
+                       "d2h_bytes_per_step": int(8 * (D + 4 + D)), "api": "priest_plan_z (host buffers, blocking)"}
 
-    # ---- the plain per-problem FP32 GPU path on the same workload and draws
-    plain = None
-    if args.plain_steps > 0:
+    if plain_steps > 0:
+        # ---- the plain per-problem FP32 GPU path on the same workload and draws
         out_p = torch.zeros(D + 4, dtype=torch.float64, device=dev)
         with torch.cuda.stream(stream):
             P.priest_plan_plain_device(ctx.h, h, z_dev.data_ptr(), out_p.data_ptr())
         P.priest_sync(ctx.h)
-        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.plain_steps)]
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(plain_steps)]
         with torch.cuda.stream(stream):
             for e0, e1 in pev:
                 flush.zero_()
@@ -345,31 +454,34 @@ def run_ours(args):
                 e1.record(stream)
         P.priest_sync(ctx.h)
         pms = sum(a.elapsed_time(b) for a, b in pev) / len(pev)
-        ours = out.cpu().numpy()
-        theirs = out_p.cpu().numpy()
-        plain = {"value": units / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": len(pev),
-                 "speedup_of_fused": (units / (total_ms / args.steps / 1e3)) / (units / (pms / 1e3)),
-                 "c_aug": float(theirs[D + 2]), "c_aug_fused": float(ours[D + 2]),
-                 "path": "priest_plan_plain_device: one kernel per step, HBM trajectory / residual tiles"}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(p, cem, args.precision, args.workload),
-                       "l2": "flushed between timed steps (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "units_per_step": units},
-            "solves_per_s": args.steps * world / (total_ms / 1e3),
-            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "plain_gpu": plain}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt = cpu_oracle_rate(p, cem, args.cpu_samples)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{args.cpu_samples} samples x {K} projection iterations (+ residual/cost) "
-                                          f"of the same workload, FP64 oracle, 1 thread, {dt:.1f} s"}
+        line["plain_gpu"] = {"value": units / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": len(pev),
+                             "speedup_of_fused": pms / (total_ms / steps),
+                             "c_aug": float(out_p.cpu().numpy()[D + 2]), "c_aug_fused": float(out.cpu().numpy()[D + 2]),
+                             "path": "priest_plan_plain_device: one kernel per step, HBM trajectory / residual tiles"}
+    if cpu and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baselines(single_oracle_jobs(p, cem, args.cpu_samples),
+                                             f"{args.cpu_samples} samples x {K} projection iterations "
+                                             "(+ residual / cost) of the same workload")
     P.priest_unload(ctx.h, h)
     ctx.close()
+    return line
+
+
+def run_single(args):
+    import torch
+
+    from paper_2309_08235_gb300 import build as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    B.build()
+    line = measure_single(args, args.workload, args.steps, args.warmup, args.precision, args.plain_steps,
+                          e2e=True, cpu=not args.no_cpu_baseline, dist=dist)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -377,63 +489,198 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# The batched workload (the default line)
+# ---------------------------------------------------------------------------
+
 def run_batched(args):
-    """Batched workload: 256 uneven 2-D problems (obstacles log-uniform 10-400,
-    N in {256, 512, 1024, 2048}, n_p in {60, 100, 150}, K = 60, L = 3) solved
-    by priest_plan_batch (one persistent projection launch per CEM iteration,
-    CUDA graph replay).  Not the default bench line."""
+    """256 uneven 2-D problems per rank in shared launches (priest_plan_batch,
+    graph replay): device-timed rate, roofline of the persistent projection
+    kernel, end-to-end rate through priest_plan_batch_host, the plain
+    per-problem path on the same problems and draws, the oracle's baseline,
+    and the single-problem workloads as extra keys."""
     import torch
 
     from paper_2309_08235_gb300 import build as B
     from paper_2309_08235_gb300 import priest as P
     from paper_2309_08235_gb300 import workloads as W
 
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
     B.build()
-    dev = torch.device("cuda", 0)
-    probs = W.batched_problems(args.batch_problems)
-    K, L = 60, 3
+    dev = torch.device("cuda", local)
+    K, L, n = BATCH_K, BATCH_L, args.batch_problems
+    # this rank's share of an n x world problem set (weak scaling: n per rank)
+    share = R.shard(n * world, rank, world)
+    probs = W.batched_problems(len(share), seed0=100 + share.start)
     stream = torch.cuda.Stream(device=dev)
-    p0 = probs[0][0]
-    ctx = P.Context(p0, W.cem_settings(probs[0][1], K, L), precision=P.PRIEST_FP32, stream=stream.cuda_stream)
-    handles, zs, outs, keep = [], [], [], []
-    units = 0
-    pairs = 0
+    p0, n0 = probs[0]
+    ctx = P.Context(p0, W.cem_settings(n0, K, L), precision=P.PRIEST_FP32, stream=stream.cuda_stream)
+    handles, structs, keep, z_host, z_dev, outs = [], [], [], [], [], []
+    units = flops_launch = pipe_launch = pairs = 0
+    h2d_obs = 0
     for i, (p, N) in enumerate(probs):
         cem = W.cem_settings(N, K, L)
         prob, kp = P.make_problem(p, cem, per_problem_shape=True)
         keep.append(kp)
+        structs.append(prob)
         handles.append(P.priest_load(ctx.h, prob))
-        zs.append(torch.from_numpy(W.normals(2000 + i, (L, N, 22))).to(dev))
+        zh = torch.from_numpy(W.normals(2000 + share.start + i, (L, N, 22))).pin_memory()
+        z_host.append(zh)
+        z_dev.append(zh.to(dev))
         outs.append(torch.zeros(26, dtype=torch.float64, device=dev))
         units += N * K * L
         pairs += N * K * L * p["n_p"] * p["n_obs"]
-    zp = [z.data_ptr() for z in zs]
+        flops_launch += flops_per_sample_iter(p) * N * K
+        pipe_launch += fma_pipe_flops_per_sample_iter(p) * N * K
+        h2d_obs += 8 * (p["n_obs"] * (2 * p["dims"] + 2) + 18)
+    zp = [z.data_ptr() for z in z_dev]
     op = [o.data_ptr() for o in outs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    t_setup = time.perf_counter()
     with torch.cuda.stream(stream):
-        for _ in range(max(2, args.warmup)):
+        for _ in range(max(3, args.warmup)):  # the first call tunes tilings and records the graph
             P.priest_plan_batch(ctx.h, handles, zp, op)
     P.priest_sync(ctx.h)
+    t_setup = time.perf_counter() - t_setup
+    kind = P.priest_last_kernel(ctx.h)
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    P.priest_profile_read(ctx.h)
+    P.priest_profile_enable(ctx.h, 1)
+    l0 = ctx.launches()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    R.barrier(dist)
+    torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         for e0, e1 in evs:
+            flush.zero_()
             e0.record(stream)
             P.priest_plan_batch(ctx.h, handles, zp, op)
             e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    R.barrier(dist)
+    clocks = sampler.stop()
+    P.priest_profile_enable(ctx.h, 0)
+    launches = ctx.launches() - l0
+    n_proj_launch, proj_ms = P.priest_profile_read(ctx.h)
     P.priest_sync(ctx.h)
-    ms = [a.elapsed_time(b) for a, b in evs]
-    tot = sum(ms) / 1e3
-    line = {"metric": METRIC, "value": units * args.steps / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched: {len(probs)} uneven 2-D problems (n_obs 10-400, N 256-2048, "
-                                   f"n_p 60/100/150), K={K}, L={L}, one persistent launch per CEM iteration, "
-                                   "CUDA graph replay", "units_per_step": units, "pairs_per_step": pairs},
-            "solves_per_s": len(probs) * args.steps / tot,
-            "pair_tests_per_s": pairs * args.steps / tot}
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    value, t_max, _ = R.job_rate(units * args.steps, sum(step_ms) / 1e3, dist, dev)
+    total_ms = 1e3 * t_max
+
+    # ---- roofline of the persistent projection kernel
+    avg_proj_ms = proj_ms / max(1, n_proj_launch)
+    n_sm = sm_count(dev)
+    mhz = sm_max_mhz(clocks)
+    peak = fp32_peak_tflops(n_sm, mhz)
+    achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
+    pipe = pipe_launch / (avg_proj_ms / 1e3) / 1e12
+    kname = {0: "project_batch_kernel (FP32 chunked, persistent)",
+             1: "pts_batch_kernel (FP32 point-owner, persistent)"}.get(kind, "batched projection kernel")
+    traffic = stored_traffic("pts_batch_kernel_bytes_per_launch") if kind == 1 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
+                "flops_per_launch": flops_launch,
+                "flops_note": "algorithmic, summed over the launch's problems: N_i K x (n_p n_o x 14 flops per "
+                              "direct polar pair test + vel/acc blocks + both basis products over all n_v columns "
+                              "+ shared-inverse step)",
+                "peak_note": f"FP32 FMA peak derived: {n_sm} SMs x 128 lanes x 2 flop x {mhz:g} MHz",
+                "traffic_note": ("dram bytes per launch from one ncu capture of a smaller batch scaled by its "
+                                 "sample-iterations (profiles/traffic.txt), not measured in this run")
+                if traffic else None,
+                "fma_pipe": {"achieved": pipe, "frac": pipe / peak,
+                             "note": "flops the kernel issues on the FMA pipe (expanded 2-FMA pair pre-filter, "
+                                     "moving-obstacle offsets, free-column basis products)"}}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(n_sm, clocks["sm_mhz"])
+
+    # ---- end to end through the host-buffer C ABI: problems, pinned draws in, results out
+    res = (P.priest_result * len(probs))()
+    z_np = [z.numpy() for z in z_host]
+    for _ in range(2):  # the first call makes the resident set, tunes nothing new and records its graph
+        P.priest_plan_batch_host(ctx.h, structs, z_np, res)
+    e2e_steps = max(3, min(args.steps, 20))
+    R.barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.priest_plan_batch_host(ctx.h, structs, z_np, res)
+    e2e_rate, _, _ = R.job_rate(units * e2e_steps, time.perf_counter() - t0, dist, dev)
+    h2d_z = sum(z.nbytes for z in z_np)
+    e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(h2d_z + h2d_obs),
+           "d2h_bytes_per_step": int(8 * len(probs) * (30 + 22)),
+           "api": "priest_plan_batch_host (host problem structs and pinned draws in, results out, blocking)"}
+    ok = sum(1 for i in range(len(probs)) if res[i].status == 0)
+
+    # ---- the plain per-problem FP32 path: the same problems and draws, one at a time
+    plain = None
+    if args.plain_steps > 0:
+        outp = torch.zeros(26, dtype=torch.float64, device=dev)
+        with torch.cuda.stream(stream):
+            P.priest_plan_plain_device(ctx.h, handles[0], zp[0], outp.data_ptr())
+        P.priest_sync(ctx.h)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            for h, z in zip(handles, zp):
+                P.priest_plan_plain_device(ctx.h, h, z, outp.data_ptr())
+            e1.record(stream)
+        P.priest_sync(ctx.h)
+        pms = e0.elapsed_time(e1)
+        plain = {"value": units / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": 1,
+                 "speedup_of_fused": pms / (total_ms / args.steps),
+                 "path": "priest_plan_plain_device on each of the same problems in turn (one kernel per step, "
+                         "HBM trajectory / residual tiles), same draws"}
     for h in handles:
         P.priest_unload(ctx.h, h)
     ctx.close()
-    print(json.dumps(line), flush=True)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_DESC, "problems_per_gpu": len(probs), "units_per_step": units,
+                       "pair_tests_per_step": pairs,
+                       "l2": "flushed between timed steps (256 MB write); the draws alone are 130 MB",
+                       "parallelism": f"dp{world}: a disjoint share of {n * world} problems per GPU"
+                       if world > 1 else "single GPU"},
+            "solves_per_s": len(probs) * args.steps * world / (total_ms / 1e3),
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "note": "per batched solve of all problems"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "results_ok": ok, "first_call_s": t_setup, "plain_gpu": plain}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baselines(
+            batched_oracle_jobs(scale=args.ref_scale),
+            f"rows {args.ref_scale} N_i / 256 of each of the first 16 seeded problems of the batched workload "
+            "(K=60 projection iterations + residual / cost; the rows keep the workload's weighting by N_i)")
+    if not args.no_extra:
+        # the single-problem workloads on the same GPU, as extra keys
+        extra = {}
+        c2 = measure_single(args, "clutter2d", max(3, min(args.steps, 50)), 3, plain_steps=3, e2e=True, dist=dist)
+        extra["clutter2d"] = {k: c2[k] for k in ("value", "ms_per_step", "solves_per_s", "config", "e2e",
+                                                 "plain_gpu")}
+        extra["clutter2d"]["roofline"] = {k: c2["roofline"].get(k) for k in
+                                          ("kernel", "achieved", "peak", "frac", "avg_launch_ms", "traffic")}
+        extra["clutter2d"]["roofline"]["fma_pipe_frac"] = c2["roofline"]["fma_pipe"]["frac"]
+        for name in ("p2p2d", "p2p3d", "dynamic2d"):
+            r = measure_single(args, name, 20, 3, e2e=False, dist=dist)
+            extra[name] = {"ms_per_solve": r["ms_per_step"], "value": r["value"],
+                           "projection_launch_ms": r["roofline"]["avg_launch_ms"],
+                           "workload": r["config"]["workload"]}
+        line["extra_workloads"] = extra
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -556,7 +803,10 @@ def run_serving(args):
     seq_lat = np.array(fifo_latencies([r[0] for r in reqs], service)) * 1e3
     seq = {"service_ms_mean": 1e3 * mean_svc, "solves_per_s_capacity": 1.0 / mean_svc,
            "p50_ms": float(np.percentile(seq_lat, 50)), "p99_ms": float(np.percentile(seq_lat, 99)),
-           "sample": f"{len(idx)} requests timed one at a time, FIFO replay of all {len(reqs)} arrivals"}
+           "sample": f"{len(idx)} requests timed one at a time, FIFO replay of all {len(reqs)} arrivals",
+           "method": "replayed: the plain path's measured per-request service times (load, device draws, solve, "
+                     "result read, unload) fed to a single FIFO server over the same arrival times (Lindley's "
+                     "recursion), not a live run of the stream"}
     line = {"metric": METRIC, "value": served["sample_iters_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": len(warm), "ms_per_step": 1e3 * wall / max(1, steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -612,20 +862,22 @@ def run_dpriest(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-samples", type=int, default=160)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="batched: skip the single-problem extra keys")
+    ap.add_argument("--ref-scale", type=int, default=8,
+                    help="batched oracle sample: rows ref_scale * N_i / 256 of each of 16 problems")
     ap.add_argument("--workload", choices=["clutter2d", "clutter2d_bounds", "ellipsoid3d", "p2p2d", "p2p3d", "dynamic2d",
-                                           "batched",
-                                           "serving", "dpriest"],
-                    default="clutter2d",
-                    help="clutter2d: the default bench line; batched: 256 uneven problems; serving: Poisson "
-                         "request stream (both report only)")
-    ap.add_argument("--batch-problems", type=int, default=256)
+                                           "batched", "serving", "dpriest"],
+                    default="batched",
+                    help="batched: the default line (256 uneven problems); the single-problem workloads print "
+                         "their own line; serving: Poisson request stream; dpriest: distribution sweep")
+    ap.add_argument("--batch-problems", type=int, default=BATCH_N)
     ap.add_argument("--rate", type=float, default=500.0)
-    ap.add_argument("--duration", type=float, default=20.0)
+    ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--budget-gb", type=float, default=8.0)
     ap.add_argument("--seq-sample", type=int, default=300)
     ap.add_argument("--plain-steps", type=int, default=10, help="timed solves of the plain per-problem path")
@@ -634,6 +886,8 @@ def main():
     ap.add_argument("--dump", default=None, help="serving: save per-request arrival / latency / sizes (.npz)")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.workload in ("serving", "dpriest"):
+            args.workload = "batched"
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
@@ -641,7 +895,7 @@ def main():
         return run_serving(args)
     if args.workload == "dpriest":
         return run_dpriest(args)
-    return run_ours(args)
+    return run_single(args)
 
 
 if __name__ == "__main__":

@@ -291,6 +291,59 @@ priest_status priest_project_device(priest_ctx *ctx, priest_loaded *h, int n, co
 priest_status priest_plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs,
                                 const double *const *z_dev, double *const *out_dev);
 
+/* Batched solve through host buffers (Alg. 1 for every problem, in the shared
+ * launches of priest_plan_batch): probs (n host structs, obstacle arrays
+ * host memory), z[i] = L x N_i x D standard normals of problem i (host; the
+ * copies run as DMA when the caller's buffers are pinned), out[i] = problem
+ * i's result (host; xi_best, resid, cost, c_aug, best_index and the final
+ * mean; latency_ms 0).  Problems must share dims, degree and bc_final_mask;
+ * every problem starts from the default distribution (straight-line mean,
+ * init_std^2 I).  The context keeps the problems resident between calls:
+ * while every problem keeps its layout (dims, degree, mask, n_p, horizon,
+ * obstacle count and its static / moving split, sample counts, bounds flag)
+ * a call only uploads the obstacles, boundary values and draws, replays the
+ * recorded launches and copies the results back; a new layout replaces the
+ * resident set (device allocations, autotuning and graph recording on that
+ * call).  Blocks until done.  Errors: PRIEST_ERR_INVALID (as priest_plan,
+ * mixed dims / degree / mask, n < 1), PRIEST_ERR_NOMEM, PRIEST_ERR_NUMERIC
+ * (also written to every result's status), PRIEST_ERR_CUDA. */
+priest_status priest_plan_batch_host(priest_ctx *ctx, int n, const priest_problem *probs, const double *const *z,
+                                     priest_result *out);
+
+/* Batched projection (Sec. III-A, Appendix eqs. comp_alpha .. comp_zeta):
+ * for every loaded problem i, rows[i] caller-given samples (0 <= rows[i] <=
+ * its loaded sample count) are projected as priest_project_device does --
+ * xi_bar^0 = Pi_A(xi), lambda^0 from lambda_dev[i] (or 0), cfg.proj_iters
+ * iterations, then r and c_1 -- all problems in one persistent launch of the
+ * kernel and tilings the batched solves use (one setup launch for all
+ * problems first).  Device pointers per problem (caller-owned, row-major):
+ * xi_dev[i] (rows x D, read), lambda_dev[i] (rows x D, updated in place; the
+ * list or an entry may be NULL: lambda^0 = 0, not written), xi_bar_dev[i]
+ * (rows x D), resid_dev[i], cost_dev[i] (rows).  Problems must share dims,
+ * degree and bc_final_mask.  Asynchronous on the context stream (the first
+ * call of a new problem shape class blocks while the autotuner times its
+ * candidate tilings).  Errors: PRIEST_ERR_INVALID, PRIEST_ERR_NOMEM,
+ * PRIEST_ERR_CUDA. */
+priest_status priest_project_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const int *rows,
+                                   const double *const *xi_dev, double *const *lambda_dev,
+                                   double *const *xi_bar_dev, double *const *resid_dev, double *const *cost_dev);
+
+/* The selections of the last CEM iteration of a solve (Alg. 1,
+ * ConstraintEliteSet / EliteSet): h a loaded problem after priest_plan_device,
+ * or NULL for the context's last host-buffer solve (priest_plan,
+ * priest_plan_z, priest_plan_plain).  elite_out: the N_elite indices of the
+ * EliteSet in ascending (c_aug, index) order; resid_out, cost_out: r and c_1
+ * of all N projected samples of that iteration (the ConstraintEliteSet is the
+ * N_proj least (r, index)).  Host buffers, each may be NULL.  Waits for the
+ * context stream.  Errors: PRIEST_ERR_INVALID (no solve), PRIEST_ERR_CUDA. */
+priest_status priest_read_elites(priest_ctx *ctx, const priest_loaded *h, int *elite_out, double *resid_out,
+                                 double *cost_out);
+
+/* Instrumentation: the projection kernel of the context's latest projection
+ * launch: 0 the chunked kernel, 1 the point-owner FP32 kernel, 2 the
+ * tensor-core kernel (PRIEST_MIXED_BF16); -1 before the first launch. */
+int priest_last_kernel(const priest_ctx *ctx);
+
 /* The plain per-problem FP32 path: the same computation as priest_plan /
  * priest_project (same readings, same draws, FP32 projection), implemented
  * as one kernel per step with every intermediate (trajectory tiles, residual
@@ -353,6 +406,11 @@ priest_status priest_profile_read(priest_ctx *ctx, int64_t *launches, double *ms
  *   xi_dev (n x D, read), lambda_dev (n x D, updated in place, or NULL),
  *   xi_bar_dev (n x D), resid_dev (n), cost_dev (n): caller-owned DEVICE memory.
  *   cuda_stream: stream to run on (NULL = legacy default stream).
+ * Kernels: those of priest_project with the cost-model tiling (no timing of
+ * candidate tilings): in FP32 the point-owner kernel for the degree-10
+ * shapes it covers (five free coefficients, or seven in 2-D), the chunked
+ * kernel otherwise; obstacles are reordered static-first on the device, as
+ * priest_project orders them.
  * Scratch: one fixed 1 MiB device array inside the library, held by every
  * device that loads it until the process exits; every call shares it and it
  * keeps the last call's contents, so calls that overlap on the GPU (other

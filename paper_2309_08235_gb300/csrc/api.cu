@@ -41,6 +41,24 @@ struct BatchPlan {
     int *counters_dev = nullptr;    // L
     int dims = 0, nf = 0, nv = 0, dbl = 0;
     int kind = 0, R = 4;            // projection kernel of the batch (Tiling::kind) and its points per item
+    std::vector<int2> items_host;   // the uploaded items (a refresh must reproduce them)
+    std::vector<cudaEvent_t> ev;    // 2 L events recorded around the projection launches of the graph
+    std::vector<cudaGraphNode_t> ev_nodes;  // their record nodes, in the same order
+    bool ev_swapped = false;        // the nodes point at events of the context's pool
+};
+
+// Resident problems, draws and results of the batched solve through host
+// buffers (priest_plan_batch_host).
+struct HostBatch {
+    std::vector<double> key;                // layout of every problem (host_layout_key)
+    std::vector<priest_loaded *> h;
+    int n = 0;
+    double *zdev = nullptr;                 // draws of all problems
+    double *odev = nullptr;                 // results, ostride doubles per problem
+    size_t ostride = 0;
+    char *stage = nullptr;                  // pinned: obstacle spans, then results, then means
+    size_t out_off = 0, mu_off = 0;
+    std::vector<size_t> z_off, ob_off, ob_bytes;
 };
 }  // namespace priest
 
@@ -622,6 +640,7 @@ bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, cons
     }
     cudaError_t e = launch_project_tc(q, st);
     ctx->launches++;
+    ctx->last_kind = 2;
     if (ev.first) {
         cudaEventRecord(ev.second, st);
         ctx->prof_used.push_back(ev);
@@ -676,6 +695,7 @@ priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode
     }
     cudaError_t e = launch_project<Real>(p, t, st);
     ctx->launches++;
+    ctx->last_kind = t.kind;
     if (ev.first) {
         cudaEventRecord(ev.second, st);
         ctx->prof_used.push_back(ev);
@@ -891,7 +911,22 @@ void free_batch(BatchPlan *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->dev) cudaFree(b->dev);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     delete b;
+}
+
+// A pair of timing events from the context's pool (created on demand).
+std::pair<cudaEvent_t, cudaEvent_t> prof_pair(priest_ctx *ctx)
+{
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!ctx->prof_free.empty()) {
+        ev = ctx->prof_free.back();
+        ctx->prof_free.pop_back();
+    } else {
+        cudaEventCreate(&ev.first);
+        cudaEventCreate(&ev.second);
+    }
+    return ev;
 }
 
 // Autotuner of the batched launch: per class of problem shape (dims,
@@ -919,15 +954,23 @@ Tiling batch_tiling_for(priest_ctx *ctx, const Shape &sh)
     return t;
 }
 
+// shapes[i]: problem i's shape with the sample count of the launch; base[i]:
+// its projection parameters (inputs, outputs, mode) -- the trials write its
+// outputs, which the real launch rewrites, and never its multipliers.
+// setups != null: the tables are formed first (one setup launch, waited for),
+// only when some class needs tuning; *formed tells whether that launch ran.
 template <typename Real>
-priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
-                         const std::vector<SetupParams> &setups)
+priest_status tune_batch(priest_ctx *ctx, int n, const std::vector<Shape> &shapes,
+                         const std::vector<ProjParams<Real>> &base, const std::vector<SetupParams> *setups,
+                         bool *formed = nullptr)
 {
+    if (formed) *formed = false;
     std::vector<int> reps;  // one representative problem per untuned class
     {
         std::map<std::vector<int>, int> seen;
         for (int i = 0; i < n; ++i) {
-            const std::vector<int> key = batch_class(probs[i]->sh, sizeof(Real) == 8);
+            if (shapes[i].N < 1) continue;
+            const std::vector<int> key = batch_class(shapes[i], sizeof(Real) == 8);
             if (ctx->tuned.count(key) || seen.count(key)) continue;
             seen[key] = i;
             reps.push_back(i);
@@ -935,18 +978,20 @@ priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
     }
     if (reps.empty()) return PRIEST_OK;
     cudaStream_t st = ctx->stream;
-    // tables, means and first sampling factors of every problem
-    void *dsetup = nullptr;
-    PRIEST_CUDA(ctx, cudaMalloc(&dsetup, sizeof(SetupParams) * n));
-    size_t smem_setup = 0;
-    for (int i = 0; i < n; ++i) smem_setup = std::max(smem_setup, setup_smem_bytes(probs[i]->sh));
-    cudaError_t e = cudaMemcpyAsync(dsetup, setups.data(), sizeof(SetupParams) * n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_setup_batch(static_cast<SetupParams *>(dsetup), n, smem_setup, st);
-    ctx->launches++;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(dsetup);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "setup before tuning");
-    for (int i = 0; i < n; ++i) probs[i]->shape_ready = true;
+    cudaError_t e = cudaSuccess;
+    if (setups) {
+        void *dsetup = nullptr;
+        PRIEST_CUDA(ctx, cudaMalloc(&dsetup, sizeof(SetupParams) * n));
+        size_t smem_setup = 0;
+        for (int i = 0; i < n; ++i) smem_setup = std::max(smem_setup, setup_smem_bytes(shapes[i]));
+        e = cudaMemcpyAsync(dsetup, setups->data(), sizeof(SetupParams) * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = launch_setup_batch(static_cast<SetupParams *>(dsetup), n, smem_setup, st);
+        ctx->launches++;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dsetup);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "setup before tuning");
+        if (formed) *formed = true;
+    }
     const int fill = 2 * ctx->n_sm;
     void *dbuf = nullptr;
     size_t dcap = 0;
@@ -954,20 +999,17 @@ priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int i : reps) {
-        priest_loaded *h = probs[i];
-        const Shape &sh = h->sh;
+        const Shape &sh = shapes[i];
         Tiling best = batch_tiling<Real>(sh);
         float best_us = 1e30f;
         for (const Tiling &t : batch_candidates<Real>(sh)) {
-            ProjParams<Real> p = proj_params<Real>(ctx, h, t);
+            ProjParams<Real> p = base[i];
+            p.S = t.S;
+            p.C = t.C;
+            p.WS = t.ws;
             p.N = sh.N;
-            p.mode = 1;
-            p.mu = h->mu;
-            p.Lc = h->L;
-            p.z = z[i];
-            p.xi_bar = h->xb;
-            p.r_out = h->r;
-            p.c1_out = h->c1;
+            p.lam_out = nullptr;
+            p.want_lambda = 0;
             std::vector<int2> it;
             while (int(it.size()) < fill)
                 for (int s = 0; s < sh.N; s += t.S) it.push_back(make_int2(0, s));
@@ -1034,6 +1076,150 @@ priest_status tune_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
     return PRIEST_OK;
 }
 
+// Per-problem tilings of one persistent launch and the kernel they share:
+// the point-owner kernel when every problem's tiling uses it, the chunked one
+// otherwise (one kernel kind per launch).
+template <typename Real>
+priest_status batch_tiles(priest_ctx *ctx, const std::vector<Shape> &shapes, std::vector<Tiling> &tiles, int &kind,
+                          int &R)
+{
+    const int n = int(shapes.size());
+    tiles.resize(n);
+    bool all_pts = true;
+    for (int i = 0; i < n; ++i) {
+        tiles[i] = batch_tiling_for<Real>(ctx, shapes[i]);
+        all_pts = all_pts && tiles[i].kind == 1;
+    }
+    for (int i = 0; i < n && !all_pts; ++i)
+        if (tiles[i].kind == 1) {
+            for (const Tiling &c : batch_candidates<Real>(shapes[i]))
+                if (c.kind == 0) {
+                    tiles[i] = c;
+                    break;
+                }
+        }
+    kind = all_pts ? 1 : 0;
+    R = all_pts ? tiles[0].R : 4;
+    for (int i = 0; i < n; ++i)
+        if (tiles[i].smem == 0 || tiles[i].kind != kind)
+            return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
+    return PRIEST_OK;
+}
+
+// Host-side descriptors of one batched solve (Alg. 1 for every problem).
+template <typename Real>
+struct BatchDesc {
+    std::vector<ProjParams<Real>> params;  // L x n
+    std::vector<SetupParams> setups, setups_ready;
+    std::vector<CemArgs> cem;
+    std::vector<int2> items;               // (problem, first sample), most expensive first
+    int kind = 0, R = 4, D_max = 0;
+    size_t smem_proj = 0, smem_setup = 0, smem_select = 0, smem_refit = 0;
+};
+
+template <typename Real>
+priest_status batch_describe(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
+                             double *const *out, BatchDesc<Real> &d)
+{
+    const int L = ctx->cfg.cem_iters;
+    const Shape &s0 = probs[0]->sh;
+    std::vector<Shape> shapes(n);
+    for (int i = 0; i < n; ++i) {
+        shapes[i] = probs[i]->sh;
+        if (shapes[i].dims != s0.dims || shapes[i].nv != s0.nv || shapes[i].bc_mask != s0.bc_mask)
+            return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
+    }
+    std::vector<Tiling> tiles;
+    priest_status s = batch_tiles<Real>(ctx, shapes, tiles, d.kind, d.R);
+    if (s != PRIEST_OK) return s;
+    d.params.assign(size_t(L) * n, ProjParams<Real>{});
+    d.setups.resize(n);
+    d.setups_ready.resize(n);
+    d.cem.resize(n);
+    std::vector<std::pair<double, int2>> items;
+    for (int i = 0; i < n; ++i) {
+        priest_loaded *h = probs[i];
+        const Shape &sh = h->sh;
+        const Tiling t = tiles[i];
+        d.smem_proj = std::max(d.smem_proj, t.smem);
+        ProjParams<Real> p = proj_params<Real>(ctx, h, t);
+        p.N = sh.N;
+        p.mode = 1;
+        p.mu = h->mu;
+        p.Lc = h->L;
+        p.want_lambda = 0;
+        p.xi_bar = h->xb;
+        p.r_out = h->r;
+        p.c1_out = h->c1;
+        for (int l = 0; l < L; ++l) {
+            p.z = z[i] + size_t(l) * sh.N * sh.D;
+            d.params[size_t(l) * n + i] = p;
+        }
+        const double cost = double(sh.n_p) * (double(sh.n_obs) + 12.0);
+        for (int s0i = 0; s0i < sh.N; s0i += t.S) items.push_back({cost * std::min(t.S, sh.N - s0i), make_int2(i, s0i)});
+        SetupParams sp = setup_params(ctx, h, true, ctx->d_status);
+        sp.default_mu = 1;
+        sp.default_cov = 1;
+        sp.shape_ready = 0;
+        d.setups[i] = sp;
+        sp.shape_ready = 1;
+        d.setups_ready[i] = sp;
+        d.smem_setup = std::max(d.smem_setup, setup_smem_bytes(sh));
+        d.cem[i] = cem_args(ctx, h, ctx->d_status, out[i]);
+        d.smem_select = std::max(d.smem_select, select_smem_bytes(sh.N));
+        d.smem_refit = std::max(d.smem_refit, refit_smem_bytes(sh.D, sh.n_elite));
+        d.D_max = std::max(d.D_max, sh.D);
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) { return x.first > y.first; });
+    d.items.resize(items.size());
+    for (size_t k = 0; k < items.size(); ++k) d.items[k] = items[k].second;
+    return PRIEST_OK;
+}
+
+// Offsets of the descriptor block of a batched solve.
+struct BatchOffsets {
+    size_t params, setup, setup_r, cem, items, cnt, total;
+};
+
+template <typename Real>
+BatchOffsets batch_offsets(const BatchDesc<Real> &d, int n, int L)
+{
+    BatchOffsets o;
+    size_t at = 0;
+    auto take = [&](size_t bytes) {
+        const size_t here = at;
+        at = round_up(at + bytes);
+        return here;
+    };
+    o.params = take(sizeof(ProjParams<Real>) * d.params.size());
+    o.setup = take(sizeof(SetupParams) * n);
+    o.setup_r = take(sizeof(SetupParams) * n);
+    o.cem = take(sizeof(CemArgs) * n);
+    o.items = take(sizeof(int2) * d.items.size());
+    o.cnt = take(sizeof(int) * L);
+    o.total = at;
+    return o;
+}
+
+template <typename Real>
+priest_status batch_upload(priest_ctx *ctx, BatchPlan *b, const BatchDesc<Real> &d)
+{
+    cudaStream_t st = ctx->stream;
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->params_dev, d.params.data(), sizeof(ProjParams<Real>) * d.params.size(),
+                                     cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev, d.setups.data(), sizeof(SetupParams) * b->n,
+                                     cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev_ready, d.setups_ready.data(), sizeof(SetupParams) * b->n,
+                                     cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->cem_dev, d.cem.data(), sizeof(CemArgs) * b->n, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->items_dev, d.items.data(), sizeof(int2) * d.items.size(),
+                                     cudaMemcpyHostToDevice, st));
+    // the host vectors are released when the caller returns
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
+    return PRIEST_OK;
+}
+
 template <typename Real>
 priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
                           double *const *out, BatchPlan *b)
@@ -1047,139 +1233,151 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
     b->nv = s0.nv;
     b->dbl = sizeof(Real) == 8;
     if (ctx->cfg.autotune) {
+        std::vector<Shape> shapes(n);
         std::vector<SetupParams> sps(n);
+        std::vector<ProjParams<Real>> base(n);
+        Tiling t0;
+        std::memset(&t0, 0, sizeof(t0));
+        t0.S = t0.C = t0.ws = 1;
         for (int i = 0; i < n; ++i) {
-            sps[i] = setup_params(ctx, probs[i], true, ctx->d_status);
+            priest_loaded *h = probs[i];
+            shapes[i] = h->sh;
+            sps[i] = setup_params(ctx, h, true, ctx->d_status);
             sps[i].default_mu = 1;
             sps[i].default_cov = 1;
+            ProjParams<Real> p = proj_params<Real>(ctx, h, t0);
+            p.N = h->sh.N;
+            p.mode = 1;
+            p.mu = h->mu;
+            p.Lc = h->L;
+            p.z = z[i];
+            p.xi_bar = h->xb;
+            p.r_out = h->r;
+            p.c1_out = h->c1;
+            base[i] = p;
         }
-        const priest_status ts = tune_batch<Real>(ctx, n, probs, z, sps);
+        bool formed = false;
+        const priest_status ts = tune_batch<Real>(ctx, n, shapes, base, &sps, &formed);
         if (ts != PRIEST_OK) return ts;
+        // the tables exist only if the tuner ran the setup launch
+        if (formed)
+            for (int i = 0; i < n; ++i) probs[i]->shape_ready = true;
     }
-    std::vector<ProjParams<Real>> params(size_t(L) * n);
-    std::vector<SetupParams> setups(n), setups_ready(n);
-    std::vector<CemArgs> cem(n);
-    std::vector<std::pair<double, int2>> items;
-    // one projection kernel for the whole launch: the point-owner kernel when
-    // every problem's tiling uses it, the chunked one otherwise
-    std::vector<Tiling> tiles(n);
-    bool all_pts = true;
-    for (int i = 0; i < n; ++i) {
-        tiles[i] = batch_tiling_for<Real>(ctx, probs[i]->sh);
-        all_pts = all_pts && tiles[i].kind == 1;
-    }
-    for (int i = 0; i < n && !all_pts; ++i)
-        if (tiles[i].kind == 1) {
-            Shape sh = probs[i]->sh;
-            for (const Tiling &c : batch_candidates<Real>(sh))
-                if (c.kind == 0) {
-                    tiles[i] = c;
-                    break;
-                }
-        }
-    b->kind = all_pts ? 1 : 0;
-    b->R = all_pts ? tiles[0].R : 4;
-    for (int i = 0; i < n; ++i) {
-        priest_loaded *h = probs[i];
-        const Shape &sh = h->sh;
-        if (sh.dims != s0.dims || sh.nv != s0.nv || sh.bc_mask != s0.bc_mask)
-            return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
-        const Tiling t = tiles[i];
-        if (t.smem == 0) return fail(ctx, PRIEST_ERR_INVALID, "problem too large for one CTA's shared memory");
-        b->smem_proj = std::max(b->smem_proj, t.smem);
-        ProjParams<Real> p = proj_params<Real>(ctx, h, t);
-        p.N = sh.N;
-        p.mode = 1;
-        p.mu = h->mu;
-        p.Lc = h->L;
-        p.want_lambda = 0;
-        p.xi_bar = h->xb;
-        p.r_out = h->r;
-        p.c1_out = h->c1;
-        for (int l = 0; l < L; ++l) {
-            p.z = z[i] + size_t(l) * sh.N * sh.D;
-            params[size_t(l) * n + i] = p;
-        }
-        const double cost = double(sh.n_p) * (double(sh.n_obs) + 12.0);
-        for (int s = 0; s < sh.N; s += t.S) items.push_back({cost * std::min(t.S, sh.N - s), make_int2(i, s)});
-        SetupParams sp = setup_params(ctx, h, true, ctx->d_status);
-        sp.default_mu = 1;
-        sp.default_cov = 1;
-        setups[i] = sp;
-        sp.shape_ready = 1;
-        setups_ready[i] = sp;
-        b->smem_setup = std::max(b->smem_setup, setup_smem_bytes(sh));
-        const CemArgs a = cem_args(ctx, h, ctx->d_status, out[i]);
-        cem[i] = a;
-        b->smem_select = std::max(b->smem_select, select_smem_bytes(sh.N));
-        b->smem_refit = std::max(b->smem_refit, refit_smem_bytes(sh.D, sh.n_elite));
-        b->D_max = std::max(b->D_max, sh.D);
-    }
-    std::stable_sort(items.begin(), items.end(),
-                     [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) { return x.first > y.first; });
-    std::vector<int2> it(items.size());
-    for (size_t k = 0; k < items.size(); ++k) it[k] = items[k].second;
-    b->n_items = int(it.size());
-    // one device allocation for all descriptors
-    size_t o = 0;
-    auto take = [&](size_t bytes) {
-        const size_t at = o;
-        o = round_up(o + bytes);
-        return at;
-    };
-    const size_t o_params = take(sizeof(ProjParams<Real>) * params.size());
-    const size_t o_setup = take(sizeof(SetupParams) * n);
-    const size_t o_setup_r = take(sizeof(SetupParams) * n);
-    const size_t o_cem = take(sizeof(CemArgs) * n);
-    const size_t o_items = take(sizeof(int2) * it.size());
-    const size_t o_cnt = take(sizeof(int) * L);
-    cudaError_t e = cudaMalloc(&b->dev, o);
+    BatchDesc<Real> d;
+    priest_status s = batch_describe<Real>(ctx, n, probs, z, out, d);
+    if (s != PRIEST_OK) return s;
+    b->kind = d.kind;
+    b->R = d.R;
+    b->D_max = d.D_max;
+    b->smem_proj = d.smem_proj;
+    b->smem_setup = d.smem_setup;
+    b->smem_select = d.smem_select;
+    b->smem_refit = d.smem_refit;
+    b->n_items = int(d.items.size());
+    const BatchOffsets o = batch_offsets(d, n, L);
+    cudaError_t e = cudaMalloc(&b->dev, o.total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, PRIEST_ERR_NOMEM, "batch descriptors");
     }
-    char *d = static_cast<char *>(b->dev);
-    b->params_dev = d + o_params;
-    b->setup_dev = reinterpret_cast<SetupParams *>(d + o_setup);
-    b->setup_dev_ready = reinterpret_cast<SetupParams *>(d + o_setup_r);
-    b->cem_dev = reinterpret_cast<CemArgs *>(d + o_cem);
-    b->items_dev = reinterpret_cast<int2 *>(d + o_items);
-    b->counters_dev = reinterpret_cast<int *>(d + o_cnt);
-    cudaStream_t st = ctx->stream;
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->params_dev, params.data(), sizeof(ProjParams<Real>) * params.size(),
-                                     cudaMemcpyHostToDevice, st));
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev, setups.data(), sizeof(SetupParams) * n, cudaMemcpyHostToDevice, st));
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev_ready, setups_ready.data(), sizeof(SetupParams) * n,
-                                     cudaMemcpyHostToDevice, st));
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->cem_dev, cem.data(), sizeof(CemArgs) * n, cudaMemcpyHostToDevice, st));
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->items_dev, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice, st));
-    PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
-    return PRIEST_OK;
+    char *dv = static_cast<char *>(b->dev);
+    b->params_dev = dv + o.params;
+    b->setup_dev = reinterpret_cast<SetupParams *>(dv + o.setup);
+    b->setup_dev_ready = reinterpret_cast<SetupParams *>(dv + o.setup_r);
+    b->cem_dev = reinterpret_cast<CemArgs *>(dv + o.cem);
+    b->items_dev = reinterpret_cast<int2 *>(dv + o.items);
+    b->counters_dev = reinterpret_cast<int *>(dv + o.cnt);
+    b->items_host = d.items;
+    return batch_upload<Real>(ctx, b, d);
 }
 
-// The launch sequence of one batched solve.
+// New problem data (obstacles, boundary values, bounds) behind the same
+// handles: the descriptors are formed again and uploaded in place, so the
+// recorded graph stays valid.  Returns false when the launch layout changed
+// (items, kernel, shared memory), which needs a new plan.
 template <typename Real>
-priest_status batch_enqueue(priest_ctx *ctx, BatchPlan *b, bool shape_ready, cudaStream_t st)
+bool batch_refresh(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
+                   double *const *out, BatchPlan *b, priest_status *st)
+{
+    BatchDesc<Real> d;
+    *st = batch_describe<Real>(ctx, n, probs, z, out, d);
+    if (*st != PRIEST_OK) return false;
+    if (d.kind != b->kind || d.R != b->R || d.smem_proj != b->smem_proj || d.smem_setup > b->smem_setup ||
+        d.smem_select > b->smem_select || d.smem_refit > b->smem_refit || d.D_max != b->D_max ||
+        d.items.size() != b->items_host.size())
+        return false;
+    for (size_t k = 0; k < d.items.size(); ++k)
+        if (d.items[k].x != b->items_host[k].x || d.items[k].y != b->items_host[k].y) return false;
+    *st = batch_upload<Real>(ctx, b, d);
+    return *st == PRIEST_OK;
+}
+
+// The launch sequence of one batched solve.  When `capture` is set the
+// projection launches are bracketed by external event-record nodes (the
+// plan's own events), so that a replay can be timed per projection launch;
+// a direct run while profiling brackets them with the context's events.
+template <typename Real>
+priest_status batch_enqueue(priest_ctx *ctx, BatchPlan *b, bool shape_ready, cudaStream_t st, bool capture)
 {
     cudaError_t e = cudaMemsetAsync(b->counters_dev, 0, sizeof(int) * b->L, st);
     if (e == cudaSuccess)
         e = launch_setup_batch(shape_ready ? b->setup_dev_ready : b->setup_dev, b->n, b->smem_setup, st);
     ctx->launches++;
     const ProjParams<Real> *params = static_cast<const ProjParams<Real> *>(b->params_dev);
+    const bool mark = capture && int(b->ev.size()) == 2 * b->L;
     for (int l = 0; l < b->L && e == cudaSuccess; ++l) {
-        e = launch_project_batch<Real>(params + size_t(l) * b->n, b->items_dev, b->n_items, b->counters_dev + l,
-                                       b->dims, b->R, 0, b->nf, b->nv, 0, b->smem_proj, 0, st, b->kind);
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (mark) {
+            e = cudaEventRecordWithFlags(b->ev[2 * l], st, cudaEventRecordExternal);
+        } else if (!capture && ctx->profile && st == ctx->stream) {
+            ev = prof_pair(ctx);
+            cudaEventRecord(ev.first, st);
+        }
+        if (e == cudaSuccess)
+            e = launch_project_batch<Real>(params + size_t(l) * b->n, b->items_dev, b->n_items, b->counters_dev + l,
+                                           b->dims, b->R, 0, b->nf, b->nv, 0, b->smem_proj, 0, st, b->kind);
+        if (mark && e == cudaSuccess) e = cudaEventRecordWithFlags(b->ev[2 * l + 1], st, cudaEventRecordExternal);
+        if (ev.first) {
+            cudaEventRecord(ev.second, st);
+            ctx->prof_used.push_back(ev);
+        }
         if (e == cudaSuccess) e = launch_select_batch(b->cem_dev, b->n, b->smem_select, st);
         if (e == cudaSuccess) e = launch_refit_batch(b->cem_dev, b->n, b->D_max, b->smem_refit, st);
         ctx->launches += 3;
     }
+    ctx->last_kind = b->kind;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batched launch");
     return PRIEST_OK;
 }
 
-template <typename Real>
-priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
-                         double *const *out)
+// Replay of a recorded batched solve.  While profiling, the event-record
+// nodes around the projection launches are pointed at fresh events of the
+// context's pool (read back by priest_profile_read); otherwise at the plan's
+// own events.
+priest_status batch_replay(priest_ctx *ctx, BatchPlan *b)
+{
+    const bool timed = ctx->profile && int(b->ev_nodes.size()) == 2 * b->L;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+    if (timed || b->ev_swapped) {
+        for (int l = 0; l < b->L; ++l) {
+            std::pair<cudaEvent_t, cudaEvent_t> ev{b->ev[2 * l], b->ev[2 * l + 1]};
+            if (timed) ev = prof_pair(ctx);
+            if (cudaGraphExecEventRecordNodeSetEvent(b->exec, b->ev_nodes[2 * l], ev.first) != cudaSuccess ||
+                cudaGraphExecEventRecordNodeSetEvent(b->exec, b->ev_nodes[2 * l + 1], ev.second) != cudaSuccess)
+                return cuda_fail(ctx, cudaGetLastError(), "graph event node update");
+            if (timed) evs.push_back(ev);
+        }
+        b->ev_swapped = timed;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, ctx->stream);
+    ctx->launches += 1 + 3 * b->L;
+    ctx->last_kind = b->kind;
+    ctx->prof_used.insert(ctx->prof_used.end(), evs.begin(), evs.end());
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    return PRIEST_OK;
+}
+
+std::vector<uintptr_t> batch_key(int n, priest_loaded *const *probs, const double *const *z, double *const *out)
 {
     std::vector<uintptr_t> key;
     key.reserve(3 * size_t(n) + 1);
@@ -1189,12 +1387,26 @@ priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
         key.push_back(reinterpret_cast<uintptr_t>(z[i]));
         key.push_back(reinterpret_cast<uintptr_t>(out[i]));
     }
+    return key;
+}
+
+// refresh: the problems behind the handles may have new data (see
+// batch_refresh); otherwise a recorded plan is replayed as it is.
+template <typename Real>
+priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
+                         double *const *out, bool refresh = false)
+{
+    const std::vector<uintptr_t> key = batch_key(n, probs, z, out);
     auto it = ctx->batches.find(key);
     if (it != ctx->batches.end() && it->second->exec) {
-        cudaError_t e = cudaGraphLaunch(it->second->exec, ctx->stream);
-        ctx->launches += 1 + 3 * it->second->L;
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
-        return PRIEST_OK;
+        priest_status s = PRIEST_OK;
+        if (!refresh || batch_refresh<Real>(ctx, n, probs, z, out, it->second, &s)) return batch_replay(ctx, it->second);
+        if (s != PRIEST_OK) return s;
+    }
+    if (it != ctx->batches.end()) {
+        cudaStreamSynchronize(ctx->stream);
+        free_batch(it->second);
+        ctx->batches.erase(it);
     }
     BatchPlan *b = new BatchPlan();
     priest_status s = batch_build<Real>(ctx, n, probs, z, out, b);
@@ -1204,18 +1416,27 @@ priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
     }
     bool ready = true;
     for (int i = 0; i < n; ++i) ready = ready && probs[i]->shape_ready;
-    s = batch_enqueue<Real>(ctx, b, ready, ctx->stream);  // direct run (also sets kernel attributes)
+    s = batch_enqueue<Real>(ctx, b, ready, ctx->stream, false);  // direct run (also sets kernel attributes)
     if (s != PRIEST_OK) {
         free_batch(b);
         return s;
     }
     for (int i = 0; i < n; ++i) probs[i]->shape_ready = true;
-    // record the sequence for replay
+    // record the sequence for replay, with timing events around the projections
+    b->ev.assign(2 * size_t(b->L), nullptr);
+    for (cudaEvent_t &ev : b->ev)
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaEvent_t &x : b->ev)
+                if (x) cudaEventDestroy(x);
+            b->ev.clear();
+            break;
+        }
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess) {
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
             const int64_t before = ctx->launches.load();
-            const priest_status ok = batch_enqueue<Real>(ctx, b, true, cap);
+            const priest_status ok = batch_enqueue<Real>(ctx, b, true, cap, true);
             ctx->launches = before;
             cudaGraph_t g = nullptr;
             if (cudaStreamEndCapture(cap, &g) == cudaSuccess && ok == PRIEST_OK && g) {
@@ -1228,12 +1449,296 @@ priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
         cudaGetLastError();
         cudaStreamDestroy(cap);
     }
-    if (it != ctx->batches.end()) {
-        free_batch(it->second);
-        ctx->batches.erase(it);
+    // the record nodes of the timing events, in the order of b->ev
+    if (b->graph && !b->ev.empty()) {
+        size_t count = 0;
+        if (cudaGraphGetNodes(b->graph, nullptr, &count) == cudaSuccess && count > 0) {
+            std::vector<cudaGraphNode_t> nodes(count);
+            std::vector<cudaGraphNode_t> found(b->ev.size(), nullptr);
+            if (cudaGraphGetNodes(b->graph, nodes.data(), &count) == cudaSuccess) {
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    cudaEvent_t ev = nullptr;
+                    if (cudaGraphNodeGetType(nd, &ty) != cudaSuccess || ty != cudaGraphNodeTypeEventRecord) continue;
+                    if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+                    for (size_t k = 0; k < b->ev.size(); ++k)
+                        if (b->ev[k] == ev) found[k] = nd;
+                }
+                bool all = true;
+                for (cudaGraphNode_t nd : found) all = all && nd != nullptr;
+                if (all) b->ev_nodes = found;
+            }
+        }
+        cudaGetLastError();
     }
     ctx->batches[key] = b;
     return PRIEST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched projection of caller-given samples: one setup launch for all
+// problems, then one persistent projection launch over every problem's
+// (problem, first sample) items, with the tilings of the batched solves.
+// ---------------------------------------------------------------------------
+
+// Grows the context's descriptor block (device) and its pinned staging copy
+// to at least `bytes`; waits for the previous user of the staging first.
+priest_status descriptor_block(priest_ctx *ctx, size_t bytes)
+{
+    if (ctx->pb_done) PRIEST_CUDA(ctx, cudaEventSynchronize(ctx->pb_done));
+    if (bytes <= ctx->pb_cap) return PRIEST_OK;
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->pb_dev) cudaFree(ctx->pb_dev);
+    if (ctx->pb_host) cudaFreeHost(ctx->pb_host);
+    ctx->pb_dev = ctx->pb_host = nullptr;
+    ctx->pb_cap = 0;
+    const size_t cap = round_up(bytes + bytes / 2);
+    if (cudaMalloc(&ctx->pb_dev, cap) != cudaSuccess || cudaMallocHost(&ctx->pb_host, cap) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->pb_dev) cudaFree(ctx->pb_dev);
+        ctx->pb_dev = nullptr;
+        return fail(ctx, PRIEST_ERR_NOMEM, "batched projection descriptors");
+    }
+    if (!ctx->pb_done) PRIEST_CUDA(ctx, cudaEventCreateWithFlags(&ctx->pb_done, cudaEventDisableTiming));
+    ctx->pb_cap = cap;
+    return PRIEST_OK;
+}
+
+template <typename Real>
+priest_status project_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const int *rows,
+                            const double *const *xi, double *const *lam, double *const *xb, double *const *r,
+                            double *const *c1)
+{
+    cudaStream_t st = ctx->stream;
+    std::vector<Shape> shapes(n);
+    std::vector<SetupParams> sps(n);
+    std::vector<ProjParams<Real>> base(n);
+    Tiling t0;
+    std::memset(&t0, 0, sizeof(t0));
+    t0.S = t0.C = t0.ws = 1;
+    size_t smem_setup = 0, n_rows = 0;
+    int want_lambda = 0;
+    for (int i = 0; i < n; ++i) {
+        priest_loaded *h = probs[i];
+        shapes[i] = h->sh;
+        shapes[i].N = rows[i];
+        sps[i] = setup_params(ctx, h, false, ctx->d_status);
+        smem_setup = std::max(smem_setup, setup_smem_bytes(h->sh));
+        ProjParams<Real> p = proj_params<Real>(ctx, h, t0);
+        p.N = rows[i];
+        p.mode = 0;
+        p.xi_in = xi[i];
+        p.lam_in = lam ? lam[i] : nullptr;
+        p.lam_out = p.lam_in ? lam[i] : nullptr;
+        p.want_lambda = p.lam_out != nullptr;
+        want_lambda |= p.want_lambda;
+        p.xi_bar = xb[i];
+        p.r_out = r[i];
+        p.c1_out = c1[i];
+        base[i] = p;
+        n_rows += size_t(rows[i]);
+    }
+    // descriptor block: counter | setups | params | items (at most one per row)
+    const size_t o_set = 256, o_par = round_up(o_set + sizeof(SetupParams) * n),
+                 o_it = round_up(o_par + sizeof(ProjParams<Real>) * n), total = o_it + sizeof(int2) * (n_rows + 1);
+    priest_status s = descriptor_block(ctx, total);
+    if (s != PRIEST_OK) return s;
+    char *hb = static_cast<char *>(ctx->pb_host), *db = static_cast<char *>(ctx->pb_dev);
+    std::memcpy(hb + o_set, sps.data(), sizeof(SetupParams) * n);
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(db + o_set, hb + o_set, sizeof(SetupParams) * n, cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, launch_setup_batch(reinterpret_cast<SetupParams *>(db + o_set), n, smem_setup, st));
+    ctx->launches++;
+    for (int i = 0; i < n; ++i) probs[i]->shape_ready = true;
+    if (ctx->cfg.autotune) {
+        s = tune_batch<Real>(ctx, n, shapes, base, nullptr);
+        if (s != PRIEST_OK) return s;
+    }
+    std::vector<Tiling> tiles;
+    int kind = 0, R = 4;
+    s = batch_tiles<Real>(ctx, shapes, tiles, kind, R);
+    if (s != PRIEST_OK) return s;
+    size_t smem = 0;
+    std::vector<std::pair<double, int2>> items;
+    ProjParams<Real> *hp = reinterpret_cast<ProjParams<Real> *>(hb + o_par);
+    for (int i = 0; i < n; ++i) {
+        ProjParams<Real> p = base[i];
+        p.S = tiles[i].S;
+        p.C = tiles[i].C;
+        p.WS = tiles[i].ws;
+        hp[i] = p;
+        smem = std::max(smem, tiles[i].smem);
+        const double cost = double(shapes[i].n_p) * (double(shapes[i].n_obs) + 12.0);
+        for (int s0 = 0; s0 < rows[i]; s0 += tiles[i].S)
+            items.push_back({cost * std::min(tiles[i].S, rows[i] - s0), make_int2(i, s0)});
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) { return x.first > y.first; });
+    int2 *hi = reinterpret_cast<int2 *>(hb + o_it);
+    for (size_t k = 0; k < items.size(); ++k) hi[k] = items[k].second;
+    std::memset(hb, 0, sizeof(int));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(db, hb, sizeof(int), cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(db + o_par, hb + o_par, o_it - o_par + sizeof(int2) * items.size(),
+                                     cudaMemcpyHostToDevice, st));
+    PRIEST_CUDA(ctx, cudaEventRecord(ctx->pb_done, st));
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (ctx->profile) {
+        ev = prof_pair(ctx);
+        cudaEventRecord(ev.first, st);
+    }
+    const Shape &s0 = shapes[0];
+    cudaError_t e = launch_project_batch<Real>(reinterpret_cast<const ProjParams<Real> *>(db + o_par),
+                                               reinterpret_cast<const int2 *>(db + o_it), int(items.size()),
+                                               reinterpret_cast<int *>(db), s0.dims, R, 0, s0.nf, s0.nv, want_lambda,
+                                               smem, 0, st, kind);
+    ctx->launches++;
+    ctx->last_kind = kind;
+    if (ev.first) {
+        cudaEventRecord(ev.second, st);
+        ctx->prof_used.push_back(ev);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched projection");
+    return PRIEST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves through host buffers: the problems stay resident behind
+// handles the context owns while their layout (sizes, obstacle counts, the
+// tilings they imply) is unchanged; each call uploads the problems' data and
+// draws, replays the recorded solve and copies the results back.
+// ---------------------------------------------------------------------------
+
+// Layout of a problem as far as the resident buffers and recorded launches
+// depend on it (the rest -- obstacle values, boundary values, bounds, costs
+// -- is uploaded by every call).
+std::vector<double> host_layout_key(const Shape &sh)
+{
+    return {double(sh.dims), double(sh.nv), double(sh.nf), double(sh.n_p), double(sh.n_obs), double(sh.n_static),
+            double(sh.N), double(sh.n_proj), double(sh.n_elite), double(sh.use_bounds), sh.horizon};
+}
+
+void free_host_batch(priest_ctx *ctx)
+{
+    HostBatch *hb = ctx->hbatch;
+    if (!hb) return;
+    cudaStreamSynchronize(ctx->stream);
+    std::vector<double *> zp(hb->n), op(hb->n);
+    for (int i = 0; i < hb->n; ++i) {
+        zp[i] = hb->zdev + hb->z_off[i];
+        op[i] = hb->odev + size_t(i) * hb->ostride;
+    }
+    if (hb->n > 0) {
+        auto it = ctx->batches.find(batch_key(hb->n, hb->h.data(), zp.data(), op.data()));
+        if (it != ctx->batches.end()) {
+            free_batch(it->second);
+            ctx->batches.erase(it);
+        }
+    }
+    for (priest_loaded *h : hb->h) free_loaded(h);
+    if (hb->zdev) cudaFree(hb->zdev);
+    if (hb->odev) cudaFree(hb->odev);
+    if (hb->stage) cudaFreeHost(hb->stage);
+    delete hb;
+    ctx->hbatch = nullptr;
+}
+
+template <typename Real>
+priest_status plan_batch_host(priest_ctx *ctx, int n, const priest_problem *probs, const double *const *z,
+                              priest_result *out)
+{
+    cudaStream_t st = ctx->stream;
+    const int L = ctx->cfg.cem_iters;
+    std::vector<Shape> shapes(n);
+    std::vector<std::vector<double>> oc(n), ov(n), os(n);
+    std::vector<double> key;
+    for (int i = 0; i < n; ++i) {
+        priest_status s = resolve(ctx, &probs[i], -1, shapes[i]);
+        if (s != PRIEST_OK) return s;
+        if (shapes[i].dims != shapes[0].dims || shapes[i].bc_mask != shapes[0].bc_mask)
+            return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
+        order_obstacles(shapes[i], probs[i].center, probs[i].vel, probs[i].semi, oc[i], ov[i], os[i],
+                        shapes[i].n_static);
+        const std::vector<double> k = host_layout_key(shapes[i]);
+        key.insert(key.end(), k.begin(), k.end());
+    }
+    const bool fp32 = ctx->cfg.precision != PRIEST_FP64_CHECK;
+    const int D = shapes[0].D;
+    bool reuse = ctx->hbatch && ctx->hbatch->key == key;
+    if (!reuse) {
+        free_host_batch(ctx);
+        HostBatch *hb = new HostBatch();
+        ctx->hbatch = hb;
+        hb->key = key;
+        hb->ostride = size_t(D) + 8;
+        size_t zt = 0, sb = 0;
+        for (int i = 0; i < n; ++i) {
+            hb->z_off.push_back(zt);
+            zt += size_t(L) * shapes[i].N * D;
+            const Carve k = carve(shapes[i], fp32, 0, false);
+            hb->ob_off.push_back(sb);
+            hb->ob_bytes.push_back(k.semi - k.center + sizeof(double) * 2 * std::max(shapes[i].n_obs, 1));
+            sb = round_up(sb + hb->ob_bytes.back());
+        }
+        hb->out_off = sb;
+        hb->mu_off = round_up(sb + sizeof(double) * hb->ostride * n);
+        const size_t stage_bytes = hb->mu_off + sizeof(double) * size_t(D) * n;
+        if (cudaMalloc(&hb->zdev, sizeof(double) * std::max<size_t>(zt, 1)) != cudaSuccess ||
+            cudaMalloc(&hb->odev, sizeof(double) * hb->ostride * n) != cudaSuccess ||
+            cudaMallocHost(&hb->stage, stage_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_host_batch(ctx);
+            return fail(ctx, PRIEST_ERR_NOMEM, "batched solve buffers");
+        }
+        for (int i = 0; i < n; ++i) {
+            priest_loaded *h = nullptr;
+            priest_status s = make_loaded(ctx, shapes[i], probs[i].center, probs[i].vel, probs[i].semi, 0, false, st, &h);
+            if (s != PRIEST_OK) {
+                free_host_batch(ctx);
+                return s;
+            }
+            hb->h.push_back(h);
+            hb->n = int(hb->h.size());
+        }
+    } else {
+        // same layout: new problem data into the resident buffers
+        HostBatch *hb = ctx->hbatch;
+        for (int i = 0; i < n; ++i) {
+            priest_loaded *h = hb->h[i];
+            const bool ready = h->shape_ready;
+            h->sh = shapes[i];
+            h->shape_ready = ready;
+            char *dst = hb->stage + hb->ob_off[i];
+            const size_t vo = reinterpret_cast<char *>(h->vel) - reinterpret_cast<char *>(h->center),
+                         so = reinterpret_cast<char *>(h->semi) - reinterpret_cast<char *>(h->center);
+            std::memcpy(dst, oc[i].data(), sizeof(double) * oc[i].size());
+            std::memcpy(dst + vo, ov[i].data(), sizeof(double) * ov[i].size());
+            std::memcpy(dst + so, os[i].data(), sizeof(double) * os[i].size());
+            PRIEST_CUDA(ctx, cudaMemcpyAsync(h->center, dst, hb->ob_bytes[i], cudaMemcpyHostToDevice, st));
+        }
+    }
+    HostBatch *hb = ctx->hbatch;
+    std::vector<const double *> zp(n);
+    std::vector<double *> op(n);
+    for (int i = 0; i < n; ++i) {
+        double *zd = hb->zdev + hb->z_off[i];
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(zd, z[i], sizeof(double) * size_t(L) * shapes[i].N * D,
+                                         cudaMemcpyHostToDevice, st));
+        zp[i] = zd;
+        op[i] = hb->odev + size_t(i) * hb->ostride;
+    }
+    priest_status s = plan_batch<Real>(ctx, n, hb->h.data(), zp.data(), op.data(), reuse);
+    if (s != PRIEST_OK) return s;
+    double *ho = reinterpret_cast<double *>(hb->stage + hb->out_off);
+    double *hm = reinterpret_cast<double *>(hb->stage + hb->mu_off);
+    PRIEST_CUDA(ctx, cudaMemcpyAsync(ho, hb->odev, sizeof(double) * hb->ostride * n, cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < n; ++i)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(hm + size_t(i) * D, hb->h[i]->mu, sizeof(double) * D,
+                                         cudaMemcpyDeviceToHost, st));
+    s = check_status(ctx, ctx->d_status, st);
+    for (int i = 0; i < n; ++i) {
+        fill_result(shapes[i], ho + size_t(i) * hb->ostride, hm + size_t(i) * D, &out[i]);
+        out[i].status = s;
+    }
+    return s;
 }
 
 // D-PRIEST default means: the straight-line coefficients with every
@@ -1411,6 +1916,59 @@ priest_status priest_plan_batch(priest_ctx *ctx, int n, priest_loaded *const *pr
     return plan_batch<float>(ctx, n, probs, z_dev, out_dev);
 }
 
+priest_status priest_plan_batch_host(priest_ctx *ctx, int n, const priest_problem *probs, const double *const *z,
+                                     priest_result *out)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    if (n < 1 || !probs || !z || !out) return fail(ctx, PRIEST_ERR_INVALID, "empty batch or NULL lists");
+    for (int i = 0; i < n; ++i)
+        if (!z[i]) return fail(ctx, PRIEST_ERR_INVALID, "NULL draws in the batch");
+    if (ctx->cfg.precision == PRIEST_FP64_CHECK) return plan_batch_host<double>(ctx, n, probs, z, out);
+    return plan_batch_host<float>(ctx, n, probs, z, out);
+}
+
+priest_status priest_project_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const int *rows,
+                                   const double *const *xi_dev, double *const *lambda_dev,
+                                   double *const *xi_bar_dev, double *const *resid_dev, double *const *cost_dev)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    if (n < 1 || !probs || !rows || !xi_dev || !xi_bar_dev || !resid_dev || !cost_dev)
+        return fail(ctx, PRIEST_ERR_INVALID, "empty batch or NULL lists");
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!probs[i]) return fail(ctx, PRIEST_ERR_INVALID, "NULL handle in the batch");
+        if (rows[i] < 0 || rows[i] > probs[i]->sh.N)
+            return fail(ctx, PRIEST_ERR_INVALID, "row count exceeds the loaded sample count");
+        if (rows[i] > 0 && (!xi_dev[i] || !xi_bar_dev[i] || !resid_dev[i] || !cost_dev[i]))
+            return fail(ctx, PRIEST_ERR_INVALID, "NULL pointer in the batch");
+        if (probs[i]->sh.dims != probs[0]->sh.dims || probs[i]->sh.nv != probs[0]->sh.nv ||
+            probs[i]->sh.bc_mask != probs[0]->sh.bc_mask)
+            return fail(ctx, PRIEST_ERR_INVALID, "batched problems must share dims, degree and bc_final_mask");
+        total += rows[i];
+    }
+    if (total == 0) return PRIEST_OK;
+    if (ctx->cfg.precision == PRIEST_FP64_CHECK)
+        return project_batch<double>(ctx, n, probs, rows, xi_dev, lambda_dev, xi_bar_dev, resid_dev, cost_dev);
+    return project_batch<float>(ctx, n, probs, rows, xi_dev, lambda_dev, xi_bar_dev, resid_dev, cost_dev);
+}
+
+priest_status priest_read_elites(priest_ctx *ctx, const priest_loaded *h, int *elite_out, double *resid_out,
+                                 double *cost_out)
+{
+    if (!ctx) return PRIEST_ERR_INVALID;
+    const priest_loaded *src = h ? h : ctx->scratch;
+    if (!src) return fail(ctx, PRIEST_ERR_INVALID, "no solve to read");
+    const Shape &sh = src->sh;
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (elite_out)
+        PRIEST_CUDA(ctx, cudaMemcpy(elite_out, src->elite, sizeof(int) * sh.n_elite, cudaMemcpyDeviceToHost));
+    if (resid_out) PRIEST_CUDA(ctx, cudaMemcpy(resid_out, src->r, sizeof(double) * sh.N, cudaMemcpyDeviceToHost));
+    if (cost_out) PRIEST_CUDA(ctx, cudaMemcpy(cost_out, src->c1, sizeof(double) * sh.N, cudaMemcpyDeviceToHost));
+    return PRIEST_OK;
+}
+
+int priest_last_kernel(const priest_ctx *ctx) { return ctx ? ctx->last_kind : -1; }
+
 
 priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out)
 {
@@ -1473,7 +2031,11 @@ priest_status priest_destroy(priest_ctx *ctx)
     if (!ctx) return PRIEST_OK;
     server_destroy(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_host_batch(ctx);
     free_loaded(ctx->scratch);
+    if (ctx->pb_dev) cudaFree(ctx->pb_dev);
+    if (ctx->pb_host) cudaFreeHost(ctx->pb_host);
+    if (ctx->pb_done) cudaEventDestroy(ctx->pb_done);
     if (ctx->plain_work) cudaFree(ctx->plain_work);
     for (auto &kv : ctx->batches) free_batch(kv.second);
     for (auto &ev : ctx->prof_used) {

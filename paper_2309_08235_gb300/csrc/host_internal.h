@@ -38,6 +38,7 @@ struct priest_loaded {
 
 namespace priest {
 struct BatchPlan;
+struct HostBatch;
 struct Server;
 }  // namespace priest
 
@@ -61,9 +62,17 @@ struct priest_ctx {
     // workspace of the plain per-problem path (floats)
     float *plain_work = nullptr;
     size_t plain_cap = 0;
+    // batched solves through host buffers: resident problems, draws and results
+    priest::HostBatch *hbatch = nullptr;
+    // descriptors of batched projections: device block, pinned host staging
+    // and the event that marks the staging free again
+    void *pb_dev = nullptr, *pb_host = nullptr;
+    size_t pb_cap = 0;
+    cudaEvent_t pb_done = nullptr;
     // instrumentation
     bool profile = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_used, prof_free;
+    int last_kind = -1;  // projection kernel of the latest launch (Tiling::kind, 2 = tensor core)
 };
 
 namespace priest {

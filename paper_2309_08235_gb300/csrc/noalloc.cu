@@ -31,6 +31,33 @@ std::mutex g_scratch_mu;
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Stable static-first order of the obstacle list, formed on the device from
+// the raw copy in the scratch (the kernels test static obstacles four at a
+// time and moving ones by their time-dependent offsets): obstacle j goes to
+// the count of earlier obstacles of its own kind (plus n_static for a moving
+// one).  2-D records keep b = a.
+__global__ void order_obstacles_kernel(const double *c_in, const double *v_in, const double *s_in, int n, int dims,
+                                       int n_static, double *c, double *v, double *s)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        auto moving = [&](int i) {
+            if (!v_in) return false;
+            for (int ax = 0; ax < dims; ++ax)
+                if (v_in[i * dims + ax] != 0.0) return true;
+            return false;
+        };
+        const bool mj = moving(j);
+        int k = mj ? n_static : 0;
+        for (int i = 0; i < j; ++i) k += moving(i) == mj ? 1 : 0;
+        for (int ax = 0; ax < dims; ++ax) {
+            c[k * dims + ax] = c_in[j * dims + ax];
+            v[k * dims + ax] = v_in ? v_in[j * dims + ax] : 0.0;
+        }
+        s[2 * k] = s_in[2 * j];
+        s[2 * k + 1] = dims == 3 ? s_in[2 * j + 1] : s_in[2 * j];
+    }
+}
+
 bool fin(double x) { return std::isfinite(x); }
 
 }  // namespace
@@ -94,9 +121,13 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     sh.nf = sh.nv - kFree0 - final_fixed(sh.bc_mask);
     sh.D = sh.dims * sh.nv;
     sh.N = n;
-    // Every obstacle goes through the moving-obstacle branch of the kernel
-    // (a static one simply has zero velocity), so the list is used as given.
+    // static obstacles (zero velocity) first, as priest_project orders them
     sh.n_static = 0;
+    for (int j = 0; j < sh.n_obs; ++j) {
+        bool mv = false;
+        for (int ax = 0; ax < sh.dims && pr->vel; ++ax) mv = mv || pr->vel[j * sh.dims + ax] != 0.0;
+        sh.n_static += mv ? 0 : 1;
+    }
     if (n == 0) return PRIEST_OK;
 
     // ---- scratch layout inside g_noalloc_scratch
@@ -112,6 +143,8 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     o = up256(o + sizeof(double) * nob * sh.dims);
     const size_t off_semi = o;
     o = up256(o + sizeof(double) * nob * 2);
+    const size_t off_raw = o;  // the caller's obstacle list as given: centres, velocities, semi-axes
+    o = up256(o + sizeof(double) * nob * (2 * sh.dims + 2));
     const size_t off_cB = o;
     o = up256(o + sizeof(double) * kAuxDoubles);
     const size_t off_tab64 = o;
@@ -143,16 +176,24 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     double *center = reinterpret_cast<double *>(base + off_center);
     double *vel = reinterpret_cast<double *>(base + off_vel);
     double *semi = reinterpret_cast<double *>(base + off_semi);
+    double *raw_c = reinterpret_cast<double *>(base + off_raw);
+    double *raw_v = raw_c + size_t(nob) * sh.dims, *raw_s = raw_v + size_t(nob) * sh.dims;
 
-    // ---- inputs into the scratch; the status word must start at zero
+    // ---- inputs into the scratch (raw copy, then the static-first order);
+    //      the status word must start at zero
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
     if (e == cudaSuccess && sh.n_obs > 0) {
-        e = cudaMemcpyAsync(center, pr->center, sizeof(double) * sh.n_obs * sh.dims, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(raw_c, pr->center, sizeof(double) * sh.n_obs * sh.dims, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && pr->vel)
+            e = cudaMemcpyAsync(raw_v, pr->vel, sizeof(double) * sh.n_obs * sh.dims, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
-            e = pr->vel ? cudaMemcpyAsync(vel, pr->vel, sizeof(double) * sh.n_obs * sh.dims, cudaMemcpyHostToDevice, st)
-                        : cudaMemsetAsync(vel, 0, sizeof(double) * sh.n_obs * sh.dims, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(semi, pr->semi, sizeof(double) * sh.n_obs * 2, cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(raw_s, pr->semi, sizeof(double) * sh.n_obs * 2, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            order_obstacles_kernel<<<(sh.n_obs + 127) / 128, 128, 0, st>>>(raw_c, pr->vel ? raw_v : nullptr, raw_s,
+                                                                         sh.n_obs, sh.dims, sh.n_static, center, vel,
+                                                                         semi);
+            e = cudaGetLastError();
+        }
     }
     if (e != cudaSuccess) return PRIEST_ERR_CUDA;
 
@@ -176,7 +217,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         ProjParams<float> p;
         std::memset(&p, 0, sizeof(p));
         p.dims = sh.dims; p.nv = sh.nv; p.nf = sh.nf; p.n_p = sh.n_p; p.n_obs = sh.n_obs;
-        p.n_static = 0; p.use_bounds = sh.use_bounds; p.N = n; p.K = cfg->proj_iters;
+        p.n_static = sh.n_static; p.use_bounds = sh.use_bounds; p.N = n; p.K = cfg->proj_iters;
         p.S = t.S; p.C = t.C; p.WS = t.ws; p.mode = 0;
         p.rho = float(sh.rho); p.vmax = float(sh.vmax); p.amax = float(sh.amax);
         for (int ax = 0; ax < 3; ++ax) { p.smin[ax] = float(sh.smin[ax]); p.smax[ax] = float(sh.smax[ax]); }
@@ -193,7 +234,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         ProjParams<double> p;
         std::memset(&p, 0, sizeof(p));
         p.dims = sh.dims; p.nv = sh.nv; p.nf = sh.nf; p.n_p = sh.n_p; p.n_obs = sh.n_obs;
-        p.n_static = 0; p.use_bounds = sh.use_bounds; p.N = n; p.K = cfg->proj_iters;
+        p.n_static = sh.n_static; p.use_bounds = sh.use_bounds; p.N = n; p.K = cfg->proj_iters;
         p.S = t.S; p.C = t.C; p.WS = t.ws; p.mode = 0;
         p.rho = sh.rho; p.vmax = sh.vmax; p.amax = sh.amax;
         for (int ax = 0; ax < 3; ++ax) { p.smin[ax] = sh.smin[ax]; p.smax[ax] = sh.smax[ax]; }

@@ -34,7 +34,8 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_kernel_launches", "priest_profile_enable", "priest_profile_read",
            "priest_project_noalloc", "priest_plan_batch", "priest_wait", "priest_serve_stats_get",
            "priest_rng_normal_device", "priest_plan_plain", "priest_plan_plain_device",
-           "priest_project_plain", "priest_tc_selftest", "priest_plan_multi", "priest_chol_selftest"]
+           "priest_project_plain", "priest_tc_selftest", "priest_plan_multi", "priest_chol_selftest",
+           "priest_plan_batch_host", "priest_project_batch", "priest_read_elites", "priest_last_kernel"]
 
 
 class PriestError(RuntimeError):
@@ -121,6 +122,12 @@ def lib():
             "priest_project_noalloc": (C.c_int, [C.POINTER(priest_config), C.POINTER(priest_problem), C.c_int,
                                                  vp, vp, vp, vp, vp, vp]),
             "priest_plan_batch": (C.c_int, [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
+            "priest_plan_batch_host": (C.c_int, [vp, C.c_int, C.POINTER(priest_problem), C.POINTER(vp),
+                                                 C.POINTER(priest_result)]),
+            "priest_project_batch": (C.c_int, [vp, C.c_int, C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp),
+                                               C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
+            "priest_read_elites": (C.c_int, [vp, vp, C.POINTER(C.c_int), _P, _P]),
+            "priest_last_kernel": (C.c_int, [vp]),
             "priest_wait": (C.c_int, [vp, C.c_uint64, C.c_double, C.POINTER(priest_result)]),
             "priest_serve_stats_get": (C.c_int, [vp, C.POINTER(priest_serve_stats)]),
             "priest_rng_normal_device": (C.c_int, [C.c_uint64, C.c_int64, vp, vp]),
@@ -372,6 +379,44 @@ def priest_plan_batch(ctx, handles, z_ptrs, out_ptrs):
     zs = arr(*[int(z) for z in z_ptrs])
     os_ = arr(*[int(o) for o in out_ptrs])
     return _check(ctx, lib().priest_plan_batch(ctx, n, hs, zs, os_))
+
+
+def priest_plan_batch_host(ctx, problems, z_list, results):
+    """Batched solve through host buffers.  problems: priest_problem structs;
+    z_list: host float64 arrays (L x N_i x D, pinned or pageable); results: a
+    ctypes array of priest_result (len(problems)), written."""
+    n = len(problems)
+    parr = (priest_problem * n)(*problems)
+    zs = (C.c_void_p * n)(*[z.ctypes.data if hasattr(z, "ctypes") else int(z) for z in z_list])
+    return _check(ctx, lib().priest_plan_batch_host(ctx, n, parr, zs, results))
+
+
+def priest_project_batch(ctx, handles, rows, xi_ptrs, lam_ptrs, xb_ptrs, r_ptrs, c1_ptrs):
+    """Batched projection of caller samples; device pointers as ints (lam_ptrs
+    may be None or hold 0 entries)."""
+    n = len(handles)
+    arr = C.c_void_p * n
+    hs = arr(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    rr = (C.c_int * n)(*[int(x) for x in rows])
+    lam = None if lam_ptrs is None else arr(*[int(x) if x else None for x in lam_ptrs])
+    return _check(ctx, lib().priest_project_batch(ctx, n, hs, rr, arr(*[int(x) for x in xi_ptrs]), lam,
+                                                  arr(*[int(x) for x in xb_ptrs]), arr(*[int(x) for x in r_ptrs]),
+                                                  arr(*[int(x) for x in c1_ptrs])))
+
+
+def priest_read_elites(ctx, h, n_elite, n):
+    """(EliteSet indices, r, c_1) of the last CEM iteration of a solve; h a
+    loaded handle or None for the context's last host-buffer solve."""
+    el = np.zeros(int(n_elite), dtype=np.int32)
+    r = np.zeros(int(n))
+    c1 = np.zeros(int(n))
+    _check(ctx, lib().priest_read_elites(ctx, h, el.ctypes.data_as(C.POINTER(C.c_int)), r.ctypes.data_as(_P),
+                                         c1.ctypes.data_as(_P)))
+    return el, r, c1
+
+
+def priest_last_kernel(ctx):
+    return int(lib().priest_last_kernel(ctx))
 
 
 def priest_project_device(ctx, h, n, xi_ptr, lam_ptr, xb_ptr, r_ptr, c1_ptr):

@@ -4,7 +4,7 @@ FP64 oracle's orc_plan_multi, with the same standard-normal draws."""
 import numpy as np
 import pytest
 
-from gpu_common import TOL_FP32, TOL_FP64, rel_err, scale_of, scene
+from gpu_common import TOL_FP32, TOL_FP64, plan_under_gap_rule, rel_err, scale_of, scene
 from paper_2309_08235_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -51,17 +51,26 @@ def test_fp32_dpriest_close_to_oracle(P, oracle):
     p = scene(dims=2, n_obs=16, n_dyn=2, n_p=40)
     M, nj = 4, 64
     cem = W.cem_settings(M * nj, 20, 3, dims=2)
-    z = W.normals(44, (3, M * nj, 22))
+    z = W.normals(49, (3, M * nj, 22))
     want = oracle.plan_multi(p, cem, M, z=z)
+    # each distribution is Alg. 1 on its own rows (pinned on the oracle side)
+    sub = dict(cem, n_samples=nj, n_proj=cem["n_proj"] // M, n_elite=max(1, cem["n_elite"] // M))
+    means = oracle.multi_default_means(p, M, 2.0 * cem["init_std"])
     for prec in (P.PRIEST_FP32, P.PRIEST_MIXED_BF16):
         with P.Context(p, cem, precision=prec) as ctx:
             got = ctx.plan_multi(p, M, z=z)
         best = got["best"]
-        # every distribution's answer re-evaluated by the oracle
+        checked = 0
         for j, res in enumerate(got["per_dist"]):
+            # every distribution's answer re-evaluated by the oracle
             r_o, c1_o = oracle.residual_cost(p, res["best"][None])
             assert abs(res["r"] - r_o[0]) < TOL_FP32 * max(1.0, r_o[0])
             assert abs(res["c_aug"] - (r_o[0] + c1_o[0])) < TOL_FP32 * max(1.0, c1_o[0])
+            # the gap rule per distribution: the oracle's sample where every cut has a large gap
+            if plan_under_gap_rule(oracle, p, sub, z[:, j * nj:(j + 1) * nj], res, 10 * TOL_FP32, mu0=means[j]):
+                assert rel_err(res["best"], want["dist_best"][j], scale_of(p)) < 10 * TOL_FP32
+                checked += 1
+        assert checked >= 3  # distributions 0, 1 and 3 of this draw have large gaps at every cut
         assert best["c_aug"] == min(r["c_aug"] for r in got["per_dist"])
         assert best["c_aug"] <= want["c_aug"] * (1 + 1e-3) + 1e-3
 

@@ -5,7 +5,7 @@ same draws."""
 import numpy as np
 import pytest
 
-from gpu_common import TOL_FP32, rel_err, samples, scale_of, scene
+from gpu_common import plan_under_gap_rule, TOL_FP32, rel_err, samples, scale_of, scene
 from paper_2309_08235_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -51,7 +51,7 @@ def test_plain_and_fused_agree(P, oracle):
 def test_plain_plan_close_to_oracle(P, oracle):
     p = scene(dims=2, n_obs=16, n_dyn=2, n_p=50)
     cem = W.cem_settings(128, 25, 3, dims=2)
-    z = W.normals(12, (3, 128, 22))
+    z = W.normals(10, (3, 128, 22))  # every elite cut of this draw has a gap > 1e-3
     want = oracle.plan(p, cem, z=z)
     with P.Context(p, cem, precision=P.PRIEST_FP32) as ctx:
         got = ctx.plan_plain(p, z=z)
@@ -59,11 +59,11 @@ def test_plain_plan_close_to_oracle(P, oracle):
     r_o, c1_o = oracle.residual_cost(p, got["best"][None])
     assert abs(got["r"] - r_o[0]) < TOL_FP32 * max(1.0, r_o[0])
     assert abs(got["c_aug"] - (r_o[0] + c1_o[0])) < TOL_FP32 * max(1.0, c1_o[0])
-    if got["best_index"] == want["elites"][0]:
-        assert rel_err(got["best"], want["best"], scale_of(p)) < 10 * TOL_FP32
-    if got["best_index"] == fused["best_index"]:
-        assert rel_err(got["best"], fused["best"], scale_of(p)) < 10 * TOL_FP32
-    assert got["c_aug"] <= want["c_aug"] * (1 + 1e-3) + 1e-3
+    # the gap rule holds at every cut, so both paths return the oracle's sample
+    assert plan_under_gap_rule(oracle, p, cem, z, got, 10 * TOL_FP32)
+    assert plan_under_gap_rule(oracle, p, cem, z, fused, 10 * TOL_FP32)
+    assert rel_err(got["best"], want["best"], scale_of(p)) < 10 * TOL_FP32
+    assert rel_err(got["best"], fused["best"], scale_of(p)) < 10 * TOL_FP32
 
 
 def test_plain_rejects_fp64_context(P, oracle):

@@ -8,7 +8,7 @@ than 256 obstacle columns, and no obstacles at all."""
 import numpy as np
 import pytest
 
-from gpu_common import TOL_FP32, rel_err, samples, scale_of, scene
+from gpu_common import TOL_FP32, plan_under_gap_rule, rel_err, samples, scale_of, scene
 from paper_2309_08235_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -64,13 +64,12 @@ def test_mixed_without_obstacles(P, oracle):
 def test_mixed_plan_close_to_oracle(P, oracle):
     p = scene(dims=3, n_obs=20, n_dyn=2, n_p=40)
     cem = W.cem_settings(96, 20, 3, dims=3)
-    z = W.normals(13, (3, 96, 33))
+    z = W.normals(23, (3, 96, 33))  # every elite cut of this draw has a gap > 1e-3
     want = oracle.plan(p, cem, z=z)
     with P.Context(p, cem, precision=P.PRIEST_MIXED_BF16) as ctx:
         got = ctx.plan(p, z=z)
     r_o, c1_o = oracle.residual_cost(p, got["best"][None])
     assert abs(got["r"] - r_o[0]) < TOL_FP32 * max(1.0, r_o[0])
     assert abs(got["c_aug"] - (r_o[0] + c1_o[0])) < TOL_FP32 * max(1.0, c1_o[0])
-    if got["best_index"] == want["elites"][0]:
-        assert rel_err(got["best"], want["best"], scale_of(p)) < 10 * TOL_FP32
-    assert got["c_aug"] <= want["c_aug"] * (1 + 1e-3) + 1e-3
+    assert plan_under_gap_rule(oracle, p, cem, z, got, 10 * TOL_FP32)
+    assert rel_err(got["best"], want["best"], scale_of(p)) < 10 * TOL_FP32

@@ -110,6 +110,22 @@ def test_rng_stream_statistics(oracle):
     assert abs(np.corrcoef(z[0::2], z[1::2])[0, 1]) < 0.01
 
 
+def test_rng_stream_splitmix64_reference_outputs(oracle):
+    """The integer generator of the host stream is SplitMix64 (Steele, Lea,
+    Flood 2014).  Its published reference outputs for seed 1234567, mapped by
+    the stream's stated recipe (u = (x >> 11) 2^-53, Box-Muller on (1 - u1,
+    u2), cos then sin), give the first four normals; a wrong increment, shift
+    or multiplier in the generator changes every one of them."""
+    published = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431]
+    u = [(x >> 11) * 2.0 ** -53 for x in published]
+    want = []
+    for k in (0, 2):
+        rad = np.sqrt(-2.0 * np.log(1.0 - u[k]))
+        th = 2.0 * np.pi * u[k + 1]
+        want += [rad * np.cos(th), rad * np.sin(th)]
+    np.testing.assert_allclose(oracle.rng_normal(1234567, 4), want, rtol=1e-14, atol=0)
+
+
 def test_plan_composes_alg1(oracle):
     """orc_plan equals Alg. 1 assembled from the oracle's own stage functions."""
     p = W.scene_small_2d(n_obs=6, n_p=30)

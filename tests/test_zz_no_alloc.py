@@ -1,9 +1,9 @@
 """priest_project_noalloc, the projection entry point that allocates no device
 memory (for callers that cannot call cudaMalloc, e.g. real-time loops with a
 fixed memory budget), checked through the C ABI against the regular
-priest_project on the same inputs, on two calls in a row with different
-problems so that state left in the shared scratch by the first call cannot
-leak into the second.  Collected last on purpose."""
+priest_project and against the FP64 oracle on the same inputs, on two calls
+in a row with different problems so that state left in the shared scratch by
+the first call cannot leak into the second.  Collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -28,7 +28,7 @@ def inputs(p, n, seed):
 
 
 @pytest.mark.parametrize("precision,tol", [(1, TOL_FP32), (0, TOL_FP64)])
-def test_noalloc_matches_priest_project_twice(P, precision, tol):
+def test_noalloc_matches_priest_project_twice(P, oracle, precision, tol):
     import torch
 
     dev = torch.device("cuda", 0)
@@ -60,6 +60,13 @@ def test_noalloc_matches_priest_project_twice(P, precision, tol):
         assert rel_err(t_lam.cpu().numpy(), lam_ref, 1.0) < tol
         assert rel_err(t_r.cpu().numpy(), r_ref, 1.0) < tol
         assert rel_err(t_c.cpu().numpy(), c1_ref, max(1.0, np.abs(c1_ref).max())) < tol
+        # and against the oracle (Sec. III-A, Appendix eqs. comp_alpha .. comp_zeta)
+        xb_o, lam_o = oracle.project(p, xi, cem["proj_iters"], lam=lam0)
+        r_o, c1_o = oracle.residual_cost(p, xb_o)
+        assert rel_err(t_xb.cpu().numpy(), xb_o, s) < tol
+        assert rel_err(t_lam.cpu().numpy(), lam_o, 1.0) < tol
+        assert rel_err(t_r.cpu().numpy(), r_o, 1.0) < tol
+        assert rel_err(t_c.cpu().numpy(), c1_o, max(1.0, np.abs(c1_o).max())) < tol
 
 
 def test_noalloc_rejects_bad_sizes(P):
