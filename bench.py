@@ -99,21 +99,6 @@ def free_coefficients(p):
     return p.get("degree", 10) + 1 - 3 - fixed_end
 
 
-def fma_pipe_flops_per_sample_iter(p, nf=None):
-    """FP32 flops the kernel itself issues per projected sample-iteration on
-    the FMA pipe (FMA = 2): the expanded pre-filter (2 FMA per static pair,
-    4 in 3-D), the moving-obstacle scaled offsets (6 FMA per pair, 9 in 3-D),
-    the trajectory and transposed products on the nf free columns (2 x 3 x
-    dims x nf FMA per point), ~10 per point for the velocity / acceleration
-    blocks and the shared-inverse step (dims x nf^2 FMA)."""
-    dims, n_p, n_o = p["dims"], p["n_p"], p["n_obs"]
-    nf = free_coefficients(p) if nf is None else nf
-    n_mov = int(np.count_nonzero(np.abs(np.asarray(p["vel"])).sum(1))) if n_o else 0
-    st, mv = (4, 12) if dims == 2 else (8, 18)
-    return (n_p * ((n_o - n_mov) * st + n_mov * mv) + n_p * (2 * (2 * 3 * dims * nf) + 10)
-            + 2 * dims * nf * nf)
-
-
 def sm_count(dev=None):
     import torch
 
@@ -195,16 +180,32 @@ def dist_env():
     return R.env()
 
 
-def stored_traffic(key):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary (profiles/traffic.txt), or None."""
+def stored_profile(key):
+    """A figure of the committed ncu summary (profiles/traffic.txt: DRAM bytes
+    per launch, issue / pipe utilisation of the dominant kernels), or None."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     for ln in open(path):
         if ln.startswith(key + ":"):
-            return int(float(ln.split(":", 1)[1]))
+            return float(ln.split(":", 1)[1].split()[0])
     return None
+
+
+SCREEN_NOTE = ("achieved counts the scope table's per-unit work: the direct polar test of every (point, obstacle) pair "
+               "in every iteration.  The point-owner kernel screens every pair only when it rebuilds its neighbour "
+               "lists (the first iteration, and after a point of the CTA moved 7/8 of the list margin) and otherwise "
+               "tests only the listed pairs exactly; the pairs left out are provably inactive (zero residual rows), "
+               "so its results equal full screening and achieved can exceed the FP32 peak.  'executed' holds the "
+               "kernel's own issue and FMA-pipe utilisation from the committed ncu capture.")
+
+
+def executed(prefix):
+    out = {k: stored_profile(f"{prefix}_{k}") for k in ("issue_active_pct", "fma_pipe_pct", "alu_pipe_pct")}
+    if all(v is None for v in out.values()):
+        return None
+    out["note"] = "ncu capture committed under profiles/ (not measured in this run)"
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -396,10 +397,10 @@ def measure_single(args, name, steps, warmup, precision="fp32", plain_steps=0, e
     mhz = sm_max_mhz(clocks)
     peak = fp32_peak_tflops(n_sm, mhz)
     achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
-    pipe = fma_pipe_flops_per_sample_iter(p) * N * K / (avg_proj_ms / 1e3) / 1e12
     kname = {0: "project_kernel (FP32 chunked projection)", 1: "pts_kernel (FP32 point-owner projection)",
              2: "project_tc_kernel (tcgen05 pair tests)"}.get(kind, "projection kernel")
-    traffic = stored_traffic("pts_kernel_bytes_per_launch") if (name == "clutter2d" and kind == 1) else None
+    traffic = stored_profile("pts_kernel_bytes_per_launch") if (name == "clutter2d" and kind == 1) else None
+    traffic = None if traffic is None else int(traffic)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"{kname}, {p['dims']}-D", "avg_launch_ms": avg_proj_ms,
                 "launches": n_proj_launch, "flops_per_launch": flops_launch,
@@ -407,10 +408,11 @@ def measure_single(args, name, steps, warmup, precision="fp32", plain_steps=0, e
                               "vel/acc blocks, both basis products over all n_v columns, shared-inverse step",
                 "peak_note": f"FP32 FMA peak derived: {n_sm} SMs x 128 lanes x 2 flop x {mhz:g} MHz",
                 "traffic_note": ("dram bytes per launch from one ncu capture (profiles/traffic.txt), not measured "
-                                 "in this run") if traffic else None,
-                "fma_pipe": {"achieved": pipe, "frac": pipe / peak,
-                             "note": "flops the kernel issues on the FMA pipe (expanded 2-FMA pair pre-filter, "
-                                     "free-column basis products)"}}
+                                 "in this run") if traffic else None}
+    if kind == 1:
+        roofline["note"] = SCREEN_NOTE
+        if name == "clutter2d":
+            roofline["executed"] = executed("pts_kernel")
     if clocks.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(n_sm, clocks["sm_mhz"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -522,7 +524,7 @@ def run_batched(args):
     p0, n0 = probs[0]
     ctx = P.Context(p0, W.cem_settings(n0, K, L), precision=P.PRIEST_FP32, stream=stream.cuda_stream)
     handles, structs, keep, z_host, z_dev, outs = [], [], [], [], [], []
-    units = flops_launch = pipe_launch = pairs = 0
+    units = flops_launch = pairs = 0
     h2d_obs = 0
     for i, (p, N) in enumerate(probs):
         cem = W.cem_settings(N, K, L)
@@ -537,7 +539,6 @@ def run_batched(args):
         units += N * K * L
         pairs += N * K * L * p["n_p"] * p["n_obs"]
         flops_launch += flops_per_sample_iter(p) * N * K
-        pipe_launch += fma_pipe_flops_per_sample_iter(p) * N * K
         h2d_obs += 8 * (p["n_obs"] * (2 * p["dims"] + 2) + 18)
     zp = [z.data_ptr() for z in z_dev]
     op = [o.data_ptr() for o in outs]
@@ -583,10 +584,10 @@ def run_batched(args):
     mhz = sm_max_mhz(clocks)
     peak = fp32_peak_tflops(n_sm, mhz)
     achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
-    pipe = pipe_launch / (avg_proj_ms / 1e3) / 1e12
     kname = {0: "project_batch_kernel (FP32 chunked, persistent)",
              1: "pts_batch_kernel (FP32 point-owner, persistent)"}.get(kind, "batched projection kernel")
-    traffic = stored_traffic("pts_batch_kernel_bytes_per_launch") if kind == 1 else None
+    traffic = stored_profile("pts_batch_kernel_bytes_per_launch") if kind == 1 else None
+    traffic = None if traffic is None else int(traffic)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "avg_launch_ms": avg_proj_ms, "launches": n_proj_launch,
                 "flops_per_launch": flops_launch,
@@ -594,12 +595,11 @@ def run_batched(args):
                               "direct polar pair test + vel/acc blocks + both basis products over all n_v columns "
                               "+ shared-inverse step)",
                 "peak_note": f"FP32 FMA peak derived: {n_sm} SMs x 128 lanes x 2 flop x {mhz:g} MHz",
-                "traffic_note": ("dram bytes per launch from one ncu capture of a smaller batch scaled by its "
-                                 "sample-iterations (profiles/traffic.txt), not measured in this run")
-                if traffic else None,
-                "fma_pipe": {"achieved": pipe, "frac": pipe / peak,
-                             "note": "flops the kernel issues on the FMA pipe (expanded 2-FMA pair pre-filter, "
-                                     "moving-obstacle offsets, free-column basis products)"}}
+                "traffic_note": ("dram bytes per launch from one ncu capture of this workload "
+                                 "(profiles/traffic.txt), not measured in this run") if traffic else None}
+    if kind == 1:
+        roofline["note"] = SCREEN_NOTE
+        roofline["executed"] = executed("pts_batch_kernel")
     if clocks.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(n_sm, clocks["sm_mhz"])
 
@@ -670,7 +670,7 @@ def run_batched(args):
                                                  "plain_gpu")}
         extra["clutter2d"]["roofline"] = {k: c2["roofline"].get(k) for k in
                                           ("kernel", "achieved", "peak", "frac", "avg_launch_ms", "traffic")}
-        extra["clutter2d"]["roofline"]["fma_pipe_frac"] = c2["roofline"]["fma_pipe"]["frac"]
+        extra["clutter2d"]["roofline"]["executed"] = c2["roofline"].get("executed")
         for name in ("p2p2d", "p2p3d", "dynamic2d"):
             r = measure_single(args, name, 20, 3, e2e=False, dist=dist)
             extra[name] = {"ms_per_solve": r["ms_per_step"], "value": r["value"],

@@ -60,9 +60,13 @@ typedef enum {
     PRIEST_MIXED_BF16 = 2      /* FP32 projection whose (point, obstacle) tests are one BF16 tensor-core
                                   product per CTA (split high/low operands, FP32 accumulation) that
                                   selects the pairs for the exact FP32 test; same results as FP32 up
-                                  to summation order.  Shapes the tensor-core kernel cannot hold
-                                  (more than ~500 obstacle columns) and the batched / serving paths
-                                  run the FP32 kernel. */
+                                  to summation order.  With cfg.autotune set, the first call of a
+                                  projection shape times this kernel against the FP32 kernel and
+                                  keeps the faster one (the FP32 kernel, whose neighbour lists skip
+                                  most pair tests, on every shape measured so far); with autotune 0
+                                  the tensor-core kernel runs.  Shapes it cannot hold (more than ~500
+                                  obstacle columns) and the batched / serving paths run the FP32
+                                  kernel. */
 } priest_precision;
 
 typedef struct priest_ctx priest_ctx;

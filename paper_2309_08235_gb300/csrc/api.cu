@@ -135,6 +135,7 @@ priest_status resolve(const priest_config &c, const priest_problem *pr, int n_ov
     sh.w_curv = pr->w_curv;
     sh.w_path = pr->w_path;
     sh.curv_eps = pr->curv_eps;
+    sh.list_delta = list_margin(sh.dims, sh.n_obs, pr->semi);
     if (sh.cost_kind != 0 && sh.cost_kind != 1) return fail(PRIEST_ERR_INVALID, "cost_kind must be 0 or 1");
     if (sh.cost_kind == 1 &&
         (!(sh.w_acc >= 0) || !(sh.w_curv >= 0) || !(sh.w_path >= 0) || !std::isfinite(sh.w_acc) ||
@@ -250,6 +251,18 @@ void carve_ptrs(priest_loaded *h, char *b, const Carve &k, bool fp32, int z_iter
     h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
 }
 
+// PRIEST_NEIGHBOUR_LISTS=0 in the environment makes the point-owner kernel
+// screen every obstacle in every iteration (comparisons); lists are on
+// otherwise.
+bool neighbour_lists()
+{
+    static const bool on = [] {
+        const char *v = getenv("PRIEST_NEIGHBOUR_LISTS");
+        return !(v && std::string(v) == "0");
+    }();
+    return on;
+}
+
 template <typename Real>
 ProjParams<Real> proj_params(const priest_ctx *ctx, const priest_loaded *h, const Tiling &t)
 {
@@ -280,6 +293,7 @@ ProjParams<Real> proj_params(const priest_ctx *ctx, const priest_loaded *h, cons
     p.cB = h->cB;
     p.seg_len = h->seg_len;
     p.cost = make_cost<Real>(sh);
+    p.list_delta = neighbour_lists() ? Real(sh.list_delta) : Real(0);
     return p;
 }
 
@@ -472,9 +486,10 @@ priest_status enqueue_setup(priest_ctx *ctx, priest_loaded *h, bool plan_mode, c
 }
 
 // Optional persistent record of tuned tilings: the file named by the
-// environment variable PRIEST_TUNE_CACHE holds one line per shape,
-// "<10 key integers> S C R threads ws kind".  Read once per context, appended
-// to after each new tuning.
+// environment variable PRIEST_TUNE_CACHE holds one line per shape class,
+// "<key integers> S C R threads ws kind" (10 key integers for a single
+// launch's shape, 11 starting with -1 for a batched launch's class).  Read
+// once per context, appended to after each new tuning.
 void load_tune_cache(priest_ctx *ctx)
 {
     const char *path = getenv("PRIEST_TUNE_CACHE");
@@ -490,16 +505,17 @@ void load_tune_cache(priest_ctx *ctx)
             v.push_back(int(x));
             c = end;
         }
-        if (v.size() != 16) continue;  // lines of another format are ignored
+        const size_t nk = v.size() >= 6 ? v.size() - 6 : 0;
+        if (nk != 10 && !(nk == 11 && v[0] == -1)) continue;  // lines of another format are ignored
         Tiling t;
-        t.S = v[10];
-        t.C = v[11];
-        t.R = v[12];
-        t.threads = v[13];
-        t.ws = v[14];
-        t.kind = v[15];
+        t.S = v[nk];
+        t.C = v[nk + 1];
+        t.R = v[nk + 2];
+        t.threads = v[nk + 3];
+        t.ws = v[nk + 4];
+        t.kind = v[nk + 5];
         t.smem = 0;
-        ctx->tuned[std::vector<int>(v.begin(), v.begin() + 10)] = t;
+        ctx->tuned[std::vector<int>(v.begin(), v.begin() + nk)] = t;
     }
     fclose(f);
 }
@@ -589,12 +605,12 @@ Tiling pick_tiling(priest_ctx *ctx, const Shape &sh, int N, ProjParams<Real> p, 
 }
 
 // PRIEST_MIXED_BF16: the projection with the pair tests on the tensor core
-// (project_tc.cu).  Returns false when the shape does not fit that kernel
+// (project_tc.cu).  tc_params fills the launch's parameters; it and
+// enqueue_project_tc return false when the shape does not fit that kernel
 // (too many obstacles for tensor memory, or shared memory); the caller then
 // runs the FMA kernel.
-bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi, const double *z,
-                        const double *lam_in, double *lam_out, double *xb, double *r, double *c1, cudaStream_t st,
-                        priest_status *out)
+bool tc_params(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi, const double *z,
+               const double *lam_in, double *lam_out, double *xb, double *r, double *c1, TcParams &q)
 {
     Shape sh = h->sh;
     sh.N = N;
@@ -606,7 +622,6 @@ bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, cons
     t.S = S;
     t.C = tp.nseg;
     t.ws = 1;
-    TcParams q;
     std::memset(&q, 0, sizeof(q));
     q.p = proj_params<float>(ctx, h, t);
     q.p.N = N;
@@ -627,6 +642,15 @@ bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, cons
     q.origin64 = h->tab64 + table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs).origin;
     q.status = ctx->d_status;
     q.tp = tp;
+    return true;
+}
+
+bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi, const double *z,
+                        const double *lam_in, double *lam_out, double *xb, double *r, double *c1, cudaStream_t st,
+                        priest_status *out)
+{
+    TcParams q;
+    if (!tc_params(ctx, h, N, mode, xi, z, lam_in, lam_out, xb, r, c1, q)) return false;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->profile && st == ctx->stream) {
         if (!ctx->prof_free.empty()) {
@@ -649,17 +673,91 @@ bool enqueue_project_tc(priest_ctx *ctx, priest_loaded *h, int N, int mode, cons
     return true;
 }
 
+// Marginal device time of one projection iteration of a launch: the fastest
+// of two launches at K = 22 minus the fastest of two at K = 2, over 20 (a
+// warm-up launch first); +inf when a launch fails.
+template <typename Launch>
+float marginal_iteration_ms(priest_ctx *ctx, cudaStream_t st, Launch launch)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float t_k[2] = {1e30f, 1e30f};
+    bool ok = true;
+    for (int rep = 0; rep < 5 && ok; ++rep) {
+        const int slot = rep == 0 ? -1 : (rep - 1) & 1;
+        cudaEventRecord(e0, st);
+        const cudaError_t e = launch(slot == 1 ? 22 : 2);
+        cudaEventRecord(e1, st);
+        ctx->launches++;
+        if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (slot >= 0) t_k[slot] = std::min(t_k[slot], ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) return 1e30f;
+    const float ms = (t_k[1] - t_k[0]) / 20.f;
+    return ms > 0.f ? ms : t_k[1] / 23.f;
+}
+
+// PRIEST_MIXED_BF16: which kernel runs a projection shape.  With the
+// autotuner on, the tensor-core kernel and the FP32 kernel are timed once per
+// shape on the actual inputs and the faster one is kept (their results agree
+// to FP32 summation order); with it off, or with PRIEST_MIXED_KERNEL=tensor in
+// the environment, the tensor-core kernel runs.  Returns true for the
+// tensor-core kernel.
+bool mixed_uses_tensor(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi, const double *z,
+                       const double *lam_in, double *xb, double *r, double *c1, const Tiling &t_fp32,
+                       const ProjParams<float> &p_fp32, cudaStream_t st)
+{
+    static const bool forced = [] {
+        const char *v = getenv("PRIEST_MIXED_KERNEL");
+        return v && std::string(v) == "tensor";
+    }();
+    if (forced || !ctx->cfg.autotune) return true;
+    const Shape &sh = h->sh;
+    const std::vector<int> key = {3, sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs, sh.n_static, N, sh.use_bounds};
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) return it->second.kind == 2;
+    TcParams q;
+    float ms_tc = 1e30f;
+    if (tc_params(ctx, h, N, mode, xi, z, lam_in, nullptr, xb, r, c1, q)) {
+        q.p.want_lambda = 0;
+        ms_tc = marginal_iteration_ms(ctx, st, [&](int k) {
+            TcParams qk = q;
+            qk.p.K = k;
+            return launch_project_tc(qk, st);
+        });
+    }
+    ProjParams<float> pf = p_fp32;
+    pf.lam_out = nullptr;
+    pf.want_lambda = 0;
+    const float ms_fp32 = marginal_iteration_ms(ctx, st, [&](int k) {
+        ProjParams<float> pk = pf;
+        pk.K = k;
+        return launch_project<float>(pk, t_fp32, st);
+    });
+    Tiling choice = t_fp32;
+    if (ms_tc < ms_fp32) choice.kind = 2;
+    ctx->tuned[key] = choice;
+    if (getenv("PRIEST_AUTOTUNE_LOG"))
+        fprintf(stderr, "priest mixed precision: n_p=%d n_obs=%d N=%d tensor %.4f ms / FP32 kernel %.4f ms per iteration -> %s\n",
+                sh.n_p, sh.n_obs, N, ms_tc, ms_fp32, ms_tc < ms_fp32 ? "tensor" : "FP32");
+    return ms_tc < ms_fp32;
+}
+
 template <typename Real>
 priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode, const double *xi,
                               const double *z, const double *lam_in, double *lam_out, double *xb, double *r,
                               double *c1, cudaStream_t st)
 {
-    if constexpr (sizeof(Real) == 4) {
-        priest_status ts;
-        if (ctx->cfg.precision == PRIEST_MIXED_BF16 &&
-            enqueue_project_tc(ctx, h, N, mode, xi, z, lam_in, lam_out, xb, r, c1, st, &ts))
-            return ts;
-    }
+    const bool mixed = sizeof(Real) == 4 && ctx->cfg.precision == PRIEST_MIXED_BF16;
     Shape sh = h->sh;
     sh.N = N;
     Tiling t = choose_tiling<Real>(sh, N, ctx->n_sm);
@@ -682,6 +780,12 @@ priest_status enqueue_project(priest_ctx *ctx, priest_loaded *h, int N, int mode
     p.S = t.S;
     p.C = t.C;
     p.WS = t.ws;
+    if constexpr (sizeof(Real) == 4) {
+        priest_status ts;
+        if (mixed && mixed_uses_tensor(ctx, h, N, mode, xi, z, lam_in, xb, r, c1, t, p, st) &&
+            enqueue_project_tc(ctx, h, N, mode, xi, z, lam_in, lam_out, xb, r, c1, st, &ts))
+            return ts;
+    }
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (ctx->profile && st == ctx->stream) {
         if (!ctx->prof_free.empty()) {
@@ -951,6 +1055,8 @@ Tiling batch_tiling_for(priest_ctx *ctx, const Shape &sh)
     t.S = std::max(1, std::min(t.S, sh.N));
     t.smem = t.kind == 1 ? pts_smem_bytes(sh, t.S, t.R) : project_smem_bytes<Real>(sh, t.S, t.C);
     if (t.smem > size_t(227) * 1024) return batch_tiling<Real>(sh);
+    // an entry from a cache file written for another CTA size
+    if (t.kind == 1 && (t.R != 2 || pts_threads(sh, t.S, 2) > pts_batch_threads(sh))) return batch_tiling<Real>(sh);
     return t;
 }
 
@@ -976,6 +1082,12 @@ priest_status tune_batch(priest_ctx *ctx, int n, const std::vector<Shape> &shape
             reps.push_back(i);
         }
     }
+    load_tune_cache(ctx);
+    for (size_t k = 0; k < reps.size();)  // classes a cache file already holds
+        if (ctx->tuned.count(batch_class(shapes[reps[k]], sizeof(Real) == 8)))
+            reps.erase(reps.begin() + k);
+        else
+            ++k;
     if (reps.empty()) return PRIEST_OK;
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaSuccess;
@@ -1066,6 +1178,7 @@ priest_status tune_batch(priest_ctx *ctx, int n, const std::vector<Shape> &shape
             }
         }
         ctx->tuned[batch_class(sh, sizeof(Real) == 8)] = best;
+        save_tune_entry(batch_class(sh, sizeof(Real) == 8), best);
         if (getenv("PRIEST_AUTOTUNE_LOG"))
             fprintf(stderr, "priest batch autotune: n_p=%d n_obs=%d -> kind=%d S=%d C=%d ws=%d (%.4f us / sample-iteration)\n",
                     sh.n_p, sh.n_obs, best.kind, best.S, best.C, best.ws, best_us);

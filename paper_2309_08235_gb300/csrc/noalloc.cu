@@ -114,6 +114,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     sh.w_curv = pr->w_curv;
     sh.w_path = pr->w_path;
     sh.curv_eps = pr->curv_eps;
+    sh.list_delta = list_margin(sh.dims, sh.n_obs, pr->semi);
     if ((sh.cost_kind != 0 && sh.cost_kind != 1) ||
         (sh.cost_kind == 1 && (!(sh.w_acc >= 0) || !(sh.w_curv >= 0) || !(sh.w_path >= 0) || !fin(sh.w_acc) ||
                                !fin(sh.w_curv) || !fin(sh.w_path) || !(sh.curv_eps > 0) || !fin(sh.curv_eps))))
@@ -227,6 +228,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         p.xi_in = xi_dev; p.lam_in = lambda_dev; p.lam_out = lambda_dev; p.want_lambda = lambda_dev != nullptr;
         p.xi_bar = xi_bar_dev; p.r_out = resid_dev; p.c1_out = cost_dev;
         p.cost = make_cost<float>(sh);
+        p.list_delta = float(sh.list_delta);
         if (launch_project<float>(p, t, st) != cudaSuccess) return PRIEST_ERR_CUDA;
     } else {
         const Tiling t = choose_tiling<double>(sh, n, n_sm);

@@ -36,7 +36,24 @@ struct Shape {
     int N, n_proj, n_elite, D;
     int cost_kind;                          // c_1: 0 = sum |a|^2; 1 = BARN-style
     double w_acc, w_curv, w_path, curv_eps;
+    double list_delta;                      // neighbour-list margin: 3/4 of the mean of min(a_j, b_j)
+                                            // (0 without obstacles)
 };
+
+// Neighbour-list margin of a problem: 3/4 of the mean of the obstacles'
+// smallest semi-axes (b_j = a_j in 2-D), 0 without obstacles (semi: n_obs x
+// 2).  Any positive margin gives the same results; this one balanced list
+// length against rebuild frequency on the measured workloads (a margin of
+// 0.5 to 1 mean semi-axis changed the batched rate by under 2 %).
+inline double list_margin(int dims, int n_obs, const double *semi)
+{
+    double s = 0.0;
+    for (int j = 0; j < n_obs; ++j) {
+        const double a = semi[2 * j], b = dims == 3 ? semi[2 * j + 1] : a;
+        s += a < b ? a : b;
+    }
+    return n_obs > 0 ? 0.75 * s / n_obs : 0.0;
+}
 
 // c_1 of the final pass (Alg. 1 cost): the point-to-point benchmark's
 // squared acceleration, or the BARN-style cost w_acc |a|^2 + w_curv kappa^2 +
@@ -180,6 +197,8 @@ struct ProjParams {
     int N, K, S, C, WS, want_lambda, mode;  // mode 0: xi_in given; 1: xi = mu + L z; WS warps per sample
     int seg_len;                            // mode 1: samples per distribution (mu, Lc hold one per
                                             // segment of seg_len rows; 0 = a single distribution)
+    Real list_delta;                        // point-owner kernel: neighbour-list margin (0: screen every
+                                            // obstacle in every iteration)
     CostParams<Real> cost;
     Real rho, vmax, amax, smin[3], smax[3];
     const Real *tab;
@@ -229,7 +248,8 @@ bool pts_span_ok(const Shape &sh, int R);
 bool pts_batch_ok(const Shape &sh);
 size_t pts_smem_bytes(const Shape &sh, int S, int R);
 int pts_threads(const Shape &sh, int S, int R);
-int pts_max_threads(int R);
+int pts_max_threads(int R);                 // largest CTA of the single-problem variants
+int pts_batch_threads(const Shape &sh);     // CTA of the persistent variant for sh
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` (the default limit
 // counts static shared memory too, so it is raised whenever more is asked

@@ -167,11 +167,25 @@ std::vector<Tiling> tiling_candidates(const Shape &sh, int n_samples, int n_sm)
 
 // Point-owner tiling of one problem inside a persistent launch: two points
 // per thread, the samples that fill the variant's CTA (at most N).
+// Most samples of one problem that fill the persistent variant's CTA.
+int pts_batch_samples(const Shape &sh)
+{
+    int S = std::max(1, pts_batch_threads(sh) / std::max(1, (sh.n_p + 1) / 2));
+    while (S > 1 && pts_threads(sh, S, 2) > pts_batch_threads(sh)) --S;
+    return S;
+}
+
 Tiling pts_batch_tiling(const Shape &sh, int S)
 {
-    Tiling t = pts_tiling(sh, std::max(1, std::min(S, sh.N)), 2);
-    t.threads = pts_max_threads(2);
-    if (pts_threads(sh, t.S, 2) > t.threads) t.smem = 0;
+    Tiling t;
+    t.kind = 1;
+    t.R = 2;
+    t.S = std::max(1, std::min(S, sh.N));
+    t.C = 1;
+    t.ws = 0;
+    t.threads = pts_batch_threads(sh);
+    t.smem = pts_smem_bytes(sh, t.S, 2);
+    if (pts_threads(sh, t.S, 2) > t.threads || t.smem > kSmemCap || !pts_span_ok(sh, 2)) t.smem = 0;
     return t;
 }
 
@@ -195,7 +209,7 @@ template <typename Real>
 Tiling batch_tiling(const Shape &sh)
 {
     if (sizeof(Real) == 4 && pts_batch_ok(sh)) {
-        const Tiling p = pts_batch_tiling(sh, pts_max_threads(2) / ((sh.n_p + 1) / 2));
+        const Tiling p = pts_batch_tiling(sh, pts_batch_samples(sh));
         if (p.smem > 0) return p;
     }
     Tiling t;
@@ -219,7 +233,7 @@ std::vector<Tiling> batch_candidates(const Shape &sh)
 {
     std::vector<Tiling> out;
     if (sizeof(Real) == 4 && pts_batch_ok(sh)) {
-        const int s_full = pts_max_threads(2) / ((sh.n_p + 1) / 2);
+        const int s_full = pts_batch_samples(sh);
         for (int S : {s_full, (s_full + 1) / 2}) {
             const Tiling t = pts_batch_tiling(sh, S);
             if (t.smem > 0 && (out.empty() || out.back().S != t.S)) out.push_back(t);

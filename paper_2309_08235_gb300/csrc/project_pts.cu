@@ -16,6 +16,11 @@ int pts_threads(const Shape &sh, int S, int R) { return ((S * pts::pts_tps(sh.n_
 
 int pts_max_threads(int R) { return R <= 2 ? pts::pts_max_threads<2>() : pts::pts_max_threads<4>(); }
 
+int pts_batch_threads(const Shape &sh)
+{
+    return (sh.dims == 2 && sh.nf == 5) ? pts::pts_batch_threads<2, 2, 5>() : pts::pts_batch_threads<3, 2, 5>();
+}
+
 // Degree 10 with the "at rest" end (5 free coefficients per axis), 2-D or
 // 3-D; or 2-D with the end position only (7 free coefficients: the paper's
 // four boundary rows per axis).
@@ -56,7 +61,7 @@ cudaError_t launch_pts_batch_one(const ProjParams<float> *params, const int2 *it
     auto kern = pts::pts_batch_kernel<DIMS, R, NF, WL>;
     cudaError_t e = reserve_smem(kern, smem, granted);
     if (e != cudaSuccess) return e;
-    constexpr int threads = pts::pts_max_threads<R>();
+    constexpr int threads = pts::pts_batch_threads<DIMS, R, NF>();
     if (grid <= 0) {
         int per_sm = 0, dev = 0, n_sm = 0;
         cudaGetDevice(&dev);
@@ -71,7 +76,7 @@ cudaError_t launch_pts_batch_one(const ProjParams<float> *params, const int2 *it
 }  // namespace
 
 // Persistent point-owner launch over (problem, first sample) items; every
-// problem's p.S * TPS fits the variant's CTA (pts_max_threads(R)).
+// problem's p.S * TPS fits the variant's CTA (pts_batch_threads).
 cudaError_t launch_project_pts_batch(const ProjParams<float> *params, const int2 *items, int n_items, int *counter,
                                      int dims, int nf, int R, int want_lambda, size_t smem, int grid, cudaStream_t st)
 {

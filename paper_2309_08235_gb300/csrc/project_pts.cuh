@@ -10,12 +10,27 @@
 //     stamps j, j + TPS, ..., TPS = ceil(n_p / R), of sample s for all K
 //     iterations, with its rows of the free-column basis (P, Pd, Pdd) and of
 //     the fixed-coefficient part in registers (loaded once per launch);
-//   * phase B tests the thread's points against every obstacle (no obstacle
-//     chunks): static obstacles four at a time from "quad" records (one f32x2
-//     FMA evaluates a point against two obstacles), moving ones two at a time;
-//     three-input minima find the rare candidates, each thread records its
-//     candidate batches and, after the loop, recomputes them with the same
-//     operations and tests them exactly; residuals S_o accumulate in registers;
+//   * phase B tests the thread's points against the obstacles through
+//     neighbour lists: each thread keeps, per point, the obstacles within
+//     a_j + delta of the point's position at the last rebuild (at most
+//     list_cap(dims), in obstacle order, each with the obstacle's offset terms
+//     at the point's time) and tests only those exactly.  The CTA
+//     rebuilds its lists when one of its points has moved farther than
+//     7/8 delta since the last rebuild (always in the first iteration; one
+//     vote of the whole CTA, so rebuilds do not hold warps at the barrier
+//     of phase C one warp at a time): every
+//     obstacle is screened then -- static ones four at a time from "quad"
+//     records whose thresholds are inflated by delta (one f32x2 FMA evaluates
+//     a point against two obstacles), moving ones two at a time by their
+//     scaled offsets -- and the flagged ones are appended to the lists.  An
+//     obstacle left out lies at least a_j + delta from the point's rebuild
+//     position, so while the point stays within 7/8 delta of it the pair is
+//     inactive (its residual row is zero) and skipping it changes nothing; the
+//     eighth of delta held back covers the FP32 rounding of the screening.
+//     The exact tests run in obstacle order, so the sums are those of testing
+//     every obstacle.  A warp whose lists overflowed screens every obstacle
+//     and tests its candidates exactly in every iteration until its next
+//     rebuild; residuals S_o accumulate in registers;
 //   * phase C forms each thread's share of g on the free columns and reduces
 //     it over the sample's threads with a segmented warp reduction (a warp may
 //     hold the end of one sample and the start of the next; lanes 2i, 2i + 1
@@ -54,10 +69,20 @@ using detail::kFull;
 //   part  [2][S][maxw][dims*nv] per-(sample, warp) partial sums, double-buffered by
 //                           iteration parity
 //   part2 [S][maxw][2]      (doubles) residual / cost partials of the final pass
+//   ref   [R][dims][tl]     each thread's point positions at the last list rebuild
+//   list  [R][cap][tl]      (float4) each thread's neighbour lists, tl = threads rounded
+//                           to 32: per entry the obstacle's scaled offset terms at the
+//                           point's time, 2-D (1/a, -o_x(t)/a, -o_y(t)/a, a), 3-D
+//                           (1/a, 1/b, -o_x(t)/a, -o_y(t)/a)
+//   listz [R][cap][tl]      3-D: -o_z(t)/b
+//   listi [R][cap][tl]      3-D (uint16): the obstacle's index (its a, b for active pairs)
 struct PtsLayout {
-    int tps, nq, nm2, maxw, cds;
-    size_t obs, srec, mrec, W, cd, lam, xi, part, part2, total;
+    int tps, nq, nm2, maxw, cds, tl, cap;
+    size_t obs, srec, mrec, W, cd, lam, xi, part, part2, ref, list, listz, listi, total;
 };
+
+// Neighbour-list entries per point.
+__host__ __device__ constexpr int list_cap(int dims) { return dims == 2 ? 8 : 6; }
 
 // Threads per sample, rounded up to an even count so the lanes 2i, 2i + 1 of
 // a warp always hold the same sample (the paired reduction of phase C).
@@ -96,6 +121,16 @@ __host__ __device__ inline PtsLayout pts_layout(int dims, int nf, int nv, int n_
     o = align8(o + size_t(2) * S * L.maxw * dims * nv);
     L.part2 = o;
     o = align8(o + size_t(S) * L.maxw * 4);
+    L.tl = ((S * L.tps + 31) / 32) * 32;
+    L.ref = o;
+    o = align8(o + size_t(R) * dims * L.tl);
+    L.cap = list_cap(dims);
+    L.list = o;
+    o = align8(o + size_t(R) * L.cap * L.tl * 4);
+    L.listz = o;
+    o = align8(o + (dims == 3 ? size_t(R) * L.cap * L.tl : 0));
+    L.listi = o;
+    o = align8(o + (dims == 3 ? (size_t(R) * L.cap * L.tl + 1) / 2 : 0));
     L.total = o;
     return L;
 }
@@ -384,6 +419,113 @@ __device__ __forceinline__ void all_pairs(const float *srec, const float *mrec, 
     }
 }
 
+constexpr unsigned kListOverflow = 0x80000000u;
+
+// Shared-memory neighbour lists of one CTA (see PtsLayout).
+struct PtsLists {
+    float4 *w;             // [R][cap][tl]
+    float *z;              // [R][cap][tl] (3-D)
+    unsigned short *idx;   // [R][cap][tl] (3-D)
+    int tl;
+};
+
+// Neighbour lists of the thread's R points (4 bits of count per point in the
+// returned word, kListOverflow set when a point had more than list_cap
+// obstacles): every static quad screened with its inflated thresholds and
+// every moving pair by its scaled offsets against (1 + delta max(1/a, 1/b))^2,
+// the flagged obstacles appended in obstacle order with their offset terms at
+// the point's time.  Padding entries of the quad and pair records are never
+// flagged.
+template <int DIMS, int R>
+__device__ __forceinline__ unsigned build_lists(const float *srec, const float *mrec, const float *sObs, int nq,
+                                                int nm2, int ns, const detail::PackedPoints<DIMS, R> &P, float delta,
+                                                const PtsLists &Ls, int tid)
+{
+    constexpr int QS = DIMS == 2 ? 12 : 20;
+    constexpr int RM = DIMS == 2 ? 12 : 16;
+    constexpr int ST = DIMS == 2 ? 12 : 16;
+    constexpr int CAP = list_cap(DIMS);
+    unsigned cnt = 0u;
+    auto append = [&](int r, int j, float t) {
+        const unsigned c = (cnt >> (4 * r)) & 15u;
+        if (c < unsigned(CAP)) {
+            const int e = (r * CAP + int(c)) * Ls.tl + tid;
+            const float *o = sObs + size_t(j) * ST;
+            if constexpr (DIMS == 2) {
+                Ls.w[e] = make_float4(o[4], fmaf(t, o[8], o[5]), fmaf(t, o[9], o[6]), o[3]);
+            } else {
+                Ls.w[e] = make_float4(o[8], o[12], fmaf(t, o[13], o[9]), fmaf(t, o[14], o[10]));
+                Ls.z[e] = fmaf(t, o[15], o[11]);
+                Ls.idx[e] = static_cast<unsigned short>(j);
+            }
+            cnt += 1u << (4 * r);
+        } else {
+            cnt |= kListOverflow;
+        }
+    };
+    for (int k = 0; k < nq; ++k) {
+        const float *q = srec + size_t(k) * QS;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 v01, v23;
+            quad_values<DIMS>(q, P.x[r], P.y[r], P.z[r], P.zz[r], v01, v23);
+            const float npq = P.npq[r];
+            if (fmin3(v01.x, v01.y, fminf(v23.x, v23.y)) < npq) {
+                const float t = P.t[r].x;
+                if (v01.x < npq) append(r, 4 * k, t);
+                if (v01.y < npq) append(r, 4 * k + 1, t);
+                if (v23.x < npq) append(r, 4 * k + 2, t);
+                if (v23.y < npq) append(r, 4 * k + 3, t);
+            }
+        }
+    }
+    for (int k = 0; k < nm2; ++k) {
+        const float *q = mrec + size_t(k) * RM;
+        const float4 A = *reinterpret_cast<const float4 *>(q);
+        const float i0 = DIMS == 2 ? A.x : fmaxf(A.x, A.z), i1 = DIMS == 2 ? A.y : fmaxf(A.y, A.w);
+        const float b0 = fmaf(delta, i0, 1.f), b1 = fmaf(delta, i1, 1.f);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 dx, dy, dz;
+            const float2 v = detail::moving_value<DIMS>(q, P.x[r], P.y[r], P.z[r], P.t[r], dx, dy, dz);
+            if (v.x < b0 * b0) append(r, ns + 2 * k, P.t[r].x);
+            if (v.y < b1 * b1) append(r, ns + 2 * k + 1, P.t[r].x);
+        }
+    }
+    return cnt;
+}
+
+// Exact tests of the listed obstacles of the thread's points, in list order:
+// the arithmetic of exact_static / moving_rescan with the obstacle's offset
+// terms at the point's time taken from the list entry.
+template <int DIMS, int R>
+__device__ __forceinline__ void list_pairs(const float *sObs, const PtsLists &Ls, unsigned cnt, int tid,
+                                           const detail::PackedPoints<DIMS, R> &P, bool fin, float (&so)[R][DIMS])
+{
+    constexpr int CAP = list_cap(DIMS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int n = int((cnt >> (4 * r)) & 15u);
+        const float x = P.x[r].x, y = P.y[r].x, z = P.z[r].x;
+        for (int e = 0; e < n; ++e) {
+            const int ei = (r * CAP + e) * Ls.tl + tid;
+            const float4 w = Ls.w[ei];
+            if constexpr (DIMS == 2) {
+                const float dx = fmaf(x, w.x, w.y), dy = fmaf(y, w.x, w.z);
+                const float q = fmaf(dx, dx, dy * dy);
+                if (q < 1.f) active_add<DIMS>(dx, dy, 0.f, q, w.w, w.w, fin, so[r]);
+            } else {
+                const float dx = fmaf(x, w.x, w.z), dy = fmaf(y, w.x, w.w), dz = fmaf(z, w.y, Ls.z[ei]);
+                const float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (q < 1.f) {
+                    const float *o = sObs + size_t(Ls.idx[ei]) * 16;
+                    active_add<DIMS>(dx, dy, dz, q, o[5], o[6], fin, so[r]);
+                }
+            }
+        }
+    }
+}
+
 // The projection of samples [s0, s0 + S) of one problem by the calling CTA
 // (blockDim.x >= S * TPS, a multiple of 32; all threads call it).
 // WL: also return the multipliers of the fixed columns.
@@ -415,6 +557,12 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
     float *sObs = sm + L.obs, *sW = sm + L.W, *sCd = sm + L.cd, *sLam = sm + L.lam, *sXi = sm + L.xi,
           *sPart = sm + L.part;
     double *sPart2 = reinterpret_cast<double *>(sm + L.part2);
+    float *sRef = sm + L.ref;
+    PtsLists Ls;
+    Ls.w = reinterpret_cast<float4 *>(sm + L.list);
+    Ls.z = sm + L.listz;
+    Ls.idx = reinterpret_cast<unsigned short *>(sm + L.listi);
+    Ls.tl = L.tl;
     const float rho = p.rho, vmax = p.vmax, amax = p.amax, vmax2 = vmax * vmax, amax2 = amax * amax;
 
     // ---- obstacle records and W -> shared memory; a1/a2 sample set-up
@@ -480,7 +628,9 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
         }
     }
     __syncthreads();
-    // ---- pair records of the obstacle loop
+    // ---- pair records of the obstacle loop (static thresholds inflated by the
+    //      neighbour-list margin: (a + delta)^2 in 2-D, a^2 (1 + delta / min(a, b))^2 in 3-D)
+    const float dl = p.list_delta;
     for (int q = tid; q < L.nq; q += T) {
         float *d = sm + L.srec + size_t(q) * QS;
 #pragma unroll
@@ -491,11 +641,12 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
             d[i] = okj ? o[0] : 0.f;
             d[4 + i] = okj ? o[1] : 0.f;
             if constexpr (DIMS == 2) {
-                d[8 + i] = okj ? -o[2] : 3e38f;  // padding: never below -|p|^2
+                d[8 + i] = okj ? -(o[2] + (2.f * o[3] + dl) * dl) : 3e38f;  // padding: never below -|p|^2
             } else {
+                const float dm = dl * fmaxf(o[8], o[12]);
                 d[8 + i] = okj ? o[2] : 0.f;
                 d[12 + i] = okj ? o[4] : 0.f;
-                d[16 + i] = okj ? -o[3] : 3e38f;
+                d[16 + i] = okj ? -(o[3] + o[5] * o[5] * dm * (2.f + dm)) : 3e38f;
             }
         }
     }
@@ -562,6 +713,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
 #pragma unroll
             for (int ax = 0; ax < DIMS; ++ax) rsum[r][q][ax] = 0.f;
 
+    unsigned lcnt = 0u;  // neighbour-list counts of the thread's points
     for (int k = 0; k <= p.K; ++k) {
         const bool fin = (k == p.K);
         // ---- A: trajectory (pairs of points share one f32x2 FMA per term)
@@ -635,7 +787,40 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
 #pragma unroll
                 for (int ax = 0; ax < DIMS; ++ax) so[r][ax] = 0.f;
             }
-            all_pairs<DIMS, R, (DIMS == 3 ? 2 : (R >= 4 ? 8 : 4))>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
+            constexpr int NQB = DIMS == 3 ? 2 : (R >= 4 ? 4 : 2);
+            if (dl > 0.f) {
+                // rebuild when a point of the CTA moved farther than 7/8 delta:
+                // one vote of the whole CTA, so that all warps rebuild in the same
+                // iteration instead of each one holding the others at the barrier
+                bool moved = k == 0;
+                if (act && !moved) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        float d2 = 0.f;
+#pragma unroll
+                        for (int ax = 0; ax < DIMS; ++ax) {
+                            const float e = pos[r][ax] - sRef[(r * DIMS + ax) * L.tl + tid];
+                            d2 = fmaf(e, e, d2);
+                        }
+                        moved = moved || (ok[r] && d2 > 0.765625f * dl * dl);
+                    }
+                }
+                if (__syncthreads_or(moved)) {
+                    lcnt = build_lists<DIMS, R>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, dl, Ls, tid);
+                    if (act) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+#pragma unroll
+                            for (int ax = 0; ax < DIMS; ++ax) sRef[(r * DIMS + ax) * L.tl + tid] = pos[r][ax];
+                    }
+                }
+                if (__any_sync(kFull, (lcnt & kListOverflow) != 0u))
+                    all_pairs<DIMS, R, NQB>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
+                else
+                    list_pairs<DIMS, R>(sObs, Ls, lcnt, tid, P, fin, so);
+            } else {
+                all_pairs<DIMS, R, NQB>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, fin, so);
+            }
         }
         if (fin) {
             // ---- a9: r = sqrt(sum of squared residual rows), c_1
@@ -821,6 +1006,13 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
 template <int R>
 constexpr int pts_max_threads() { return R <= 2 ? 384 : 256; }
 
+// The persistent form's CTA: the 2-D five-column variant with two points per
+// thread fits 128 registers, so it runs 16 warps (its grid holds every SM);
+// the single-problem launch keeps the larger register budget, since its grid
+// has one CTA per SM anyway.
+template <int DIMS, int R, int NF>
+constexpr int pts_batch_threads() { return (DIMS == 2 && R == 2 && NF == 5) ? 512 : pts_max_threads<R>(); }
+
 template <int DIMS, int R, int NF, bool WL>
 __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const ProjParams<float> p)
 {
@@ -831,20 +1023,24 @@ __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const Proj
 
 // Persistent form over many problems: CTAs take (problem, first sample)
 // items (each problem's p.S samples per item, p.S * TPS <= blockDim.x) through
-// an atomic counter until none is left.  *next must be zero at launch.
+// an atomic counter until none is left; the item's parameters are staged in
+// shared memory (held in registers they would cost the CTA its size).  *next
+// must be zero at launch.
 template <int DIMS, int R, int NF, bool WL>
-__global__ void __launch_bounds__(pts_max_threads<R>(), 1)
+__global__ void __launch_bounds__(pts_batch_threads<DIMS, R, NF>(), 1)
     pts_batch_kernel(const ProjParams<float> *params, const int2 *items, int n_items, int *next)
 {
     __shared__ int s_item;
+    __shared__ ProjParams<float> s_p;  // the item's parameters, read from shared memory where used
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
         const int2 w = items[it];
-        const ProjParams<float> p = params[w.x];
-        pts_body<DIMS, R, NF, WL>(p, w.y);
+        if (threadIdx.x == 0) s_p = params[w.x];
+        __syncthreads();
+        pts_body<DIMS, R, NF, WL>(s_p, w.y);
         __syncthreads();
     }
 }

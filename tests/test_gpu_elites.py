@@ -52,7 +52,8 @@ def test_elites_match_oracle_every_iteration(P, oracle, case, path):
     for it in its:  # the precondition that makes every comparison below active
         assert min(cut_gaps(it["r"], it["c1"], it["proj"], cem["n_elite"])) > GAP_FP32
     prec = P.PRIEST_MIXED_BF16 if path == "mixed" else P.PRIEST_FP32
-    with P.Context(p, dict(cem, cem_iters=1), precision=prec) as ctx:
+    # autotune off: the mixed path runs the tensor-core kernel
+    with P.Context(p, dict(cem, cem_iters=1), precision=prec, autotune=0 if path == "mixed" else 1) as ctx:
         for l, it in enumerate(its):
             got, el, r, c1 = one_iteration(P, ctx, path, p, it, z[l], cem)
             # r and c_1 of every projected sample against the oracle's
@@ -74,7 +75,7 @@ def test_full_plan_matches_oracle_when_gaps_are_large(P, oracle, case, path):
     z = W.normals(zseed, (cem["cem_iters"], cem["n_samples"], D))
     want = oracle.plan(p, cem, z=z)
     prec = P.PRIEST_MIXED_BF16 if path == "mixed" else P.PRIEST_FP32
-    with P.Context(p, cem, precision=prec) as ctx:
+    with P.Context(p, cem, precision=prec, autotune=0 if path == "mixed" else 1) as ctx:
         got = ctx.plan_plain(p, z=z) if path == "plain" else ctx.plan(p, z=z)
         el, _, _ = P.priest_read_elites(ctx.h, None, cem["n_elite"], cem["n_samples"])
     np.testing.assert_array_equal(el, want["elites"])

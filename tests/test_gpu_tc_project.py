@@ -23,8 +23,13 @@ def P():
 
 
 def project(P, p, xi, K, precision, lam=None):
-    with P.Context(p, {"proj_iters": K}, precision=precision) as ctx:
-        return ctx.project(p, xi, lam=lam)
+    # autotune off: PRIEST_MIXED_BF16 runs the tensor-core kernel (no timed routing)
+    mixed = precision == P.PRIEST_MIXED_BF16
+    with P.Context(p, {"proj_iters": K}, precision=precision, autotune=0 if mixed else 1) as ctx:
+        out = ctx.project(p, xi, lam=lam)
+        if mixed and xi.shape[0] > 0:
+            assert P.priest_last_kernel(ctx.h) == 2
+        return out
 
 
 @pytest.mark.parametrize("dims,n_obs,n_dyn,n_p,N,bounds", [
@@ -66,10 +71,29 @@ def test_mixed_plan_close_to_oracle(P, oracle):
     cem = W.cem_settings(96, 20, 3, dims=3)
     z = W.normals(23, (3, 96, 33))  # every elite cut of this draw has a gap > 1e-3
     want = oracle.plan(p, cem, z=z)
-    with P.Context(p, cem, precision=P.PRIEST_MIXED_BF16) as ctx:
+    with P.Context(p, cem, precision=P.PRIEST_MIXED_BF16, autotune=0) as ctx:
         got = ctx.plan(p, z=z)
+        assert P.priest_last_kernel(ctx.h) == 2
     r_o, c1_o = oracle.residual_cost(p, got["best"][None])
     assert abs(got["r"] - r_o[0]) < TOL_FP32 * max(1.0, r_o[0])
     assert abs(got["c_aug"] - (r_o[0] + c1_o[0])) < TOL_FP32 * max(1.0, c1_o[0])
     assert plan_under_gap_rule(oracle, p, cem, z, got, 10 * TOL_FP32)
     assert rel_err(got["best"], want["best"], scale_of(p)) < 10 * TOL_FP32
+
+
+def test_mixed_routes_to_the_faster_kernel(P, oracle):
+    """With the autotuner on, PRIEST_MIXED_BF16 times the tensor-core kernel
+    and the FP32 kernel once per shape and runs the faster one; either way the
+    result is the FP32 result up to summation order."""
+    p = scene(dims=2, n_obs=40, n_dyn=4, n_p=50)
+    xi = samples(oracle, p, 300, seed=4)
+    with P.Context(p, {"proj_iters": 15}, precision=P.PRIEST_MIXED_BF16) as ctx:
+        xb, _, r, _ = ctx.project(p, xi)
+        kind = P.priest_last_kernel(ctx.h)
+        xb2, _, _, _ = ctx.project(p, xi)  # the decision is kept for the shape
+        assert P.priest_last_kernel(ctx.h) == kind
+    assert kind in (1, 2)
+    xb32, _, r32, _ = project(P, p, xi, 15, P.PRIEST_FP32)
+    assert rel_err(xb, xb32, scale_of(p)) < TOL_FP32
+    assert rel_err(r, r32, 1.0) < TOL_FP32
+    np.testing.assert_array_equal(xb, xb2)
