@@ -370,8 +370,12 @@ priest_status priest_project_plain(priest_ctx *ctx, const priest_problem *prob, 
  * bit patterns (host), D 128 x n FP32 (host).  n a multiple of 16 in
  * [16, 256], k a multiple of 16 in [16, 64].  swap = 1 exchanges the two
  * byte strides of the shared-memory descriptors (a layout check: the
- * product is right only for swap = 0).  Allocates and synchronises; for
- * tests.  PRIEST_ERR_TIMEOUT if the MMA completion was not observed. */
+ * product is right only for swap = 0); swap = 2 issues no product and no
+ * completion signal, so the kernel's bounded completion wait (1 s, then 1 s
+ * more for work in flight) runs out: a test of the time-out path, which
+ * frees the tensor memory, returns PRIEST_ERR_TIMEOUT and leaves the device
+ * usable.  Allocates and synchronises; for tests.  PRIEST_ERR_TIMEOUT if
+ * the MMA completion was not observed. */
 priest_status priest_tc_selftest(int n, int k, int swap, const uint16_t *a_host, const uint16_t *b_host,
                                  float *d_host);
 

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const uint16_t *A, con
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tmem_base;
-    if (tid == 0) {
+    // swap == 2: no product and no completion signal, so the bounded wait below
+    // runs out (the time-out path, with no asynchronous work in flight)
+    if (tid == 0 && swap != 2) {
         const uint32_t idesc = tc::idesc_bf16_f32(128, N);
         const uint32_t lbo = swap ? tc::sbo(K) : tc::kLbo, sbo = swap ? tc::kLbo : tc::sbo(K);
         for (int ks = 0; ks < K / 16; ++ks) {
@@ -72,7 +74,8 @@ using namespace priest;
 extern "C" priest_status priest_tc_selftest(int n, int k, int swap, const uint16_t *a_host, const uint16_t *b_host,
                                            float *d_host)
 {
-    if (n < 16 || n > 256 || n % 16 || k < 16 || k > 64 || k % 16 || !a_host || !b_host || !d_host)
+    if (n < 16 || n > 256 || n % 16 || k < 16 || k > 64 || k % 16 || swap < 0 || swap > 2 || !a_host || !b_host ||
+        !d_host)
         return PRIEST_ERR_INVALID;
     uint32_t ncols = 32;
     while (ncols < uint32_t(n)) ncols <<= 1;

@@ -194,3 +194,19 @@ def test_request_over_budget_rejected(P):
         with pytest.raises(P.PriestError) as e:
             ctx.submit(p, cem)
         assert e.value.status == P.PRIEST_ERR_BUDGET
+
+
+def test_wait_timeout_leaves_ticket_pending(P):
+    """priest_wait with a limit shorter than the solve returns
+    PRIEST_ERR_TIMEOUT and leaves the ticket pending; a later wait returns
+    the result (failure detection of the serving loop by its bounded wait)."""
+    p = scene(dims=2, n_obs=120, n_dyn=10, n_p=100, seed=77)
+    cem = W.cem_settings(1024, 60, 3, dims=2)
+    with _ctx(P, P.PRIEST_FP64_CHECK) as ctx:  # an FP64 solve of this size takes far longer than 1 ms
+        t = ctx.submit(p, cem)
+        res = P.priest_result()
+        with pytest.raises(P.PriestError) as e:
+            P.priest_wait(ctx.h, t, res, timeout_ms=1.0)
+        assert e.value.status == P.PRIEST_ERR_TIMEOUT
+        r = ctx.wait(t)  # no limit
+        assert r["status"] == 0 and r["latency_ms"] > 1.0

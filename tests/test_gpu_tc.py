@@ -42,3 +42,18 @@ def test_descriptor_strides_matter(P):
     st, d = P.priest_tc_selftest(bf16_bits(a), bf16_bits(b), swap=1)
     assert st == 0
     assert not np.array_equal(d, a @ b.T)
+
+
+def test_completion_wait_times_out_and_device_stays_usable(P):
+    """The failure path of the tensor-core kernels' bounded waits: with no
+    product and no completion signal issued (swap = 2) the kernel's wait for
+    the MMA completion runs out, it frees its tensor memory and reports
+    PRIEST_ERR_TIMEOUT; the next product on the same device is exact."""
+    rng = np.random.default_rng(5)
+    a = rng.integers(-8, 9, (128, 16)).astype(np.float32)
+    b = rng.integers(-8, 9, (16, 16)).astype(np.float32)
+    st, _ = P.priest_tc_selftest(bf16_bits(a), bf16_bits(b), swap=2)
+    assert st == P.PRIEST_ERR_TIMEOUT
+    st, d = P.priest_tc_selftest(bf16_bits(a), bf16_bits(b))
+    assert st == 0
+    np.testing.assert_array_equal(d, a @ b.T)
