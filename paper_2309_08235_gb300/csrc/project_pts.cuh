@@ -1007,11 +1007,14 @@ template <int R>
 constexpr int pts_max_threads() { return R <= 2 ? 384 : 256; }
 
 // The persistent form's CTA: the 2-D five-column variant with two points per
-// thread fits 128 registers, so it runs 16 warps (its grid holds every SM);
-// the single-problem launch keeps the larger register budget, since its grid
-// has one CTA per SM anyway.
+// thread fits 128 registers, so two CTAs of 256 threads share an SM (16
+// warps; half the warps per barrier than one CTA of 512, and finer items);
+// the other variants keep one CTA of 384 per SM.  The single-problem launch
+// keeps the larger register budget, since its grid has one CTA per SM anyway.
 template <int DIMS, int R, int NF>
-constexpr int pts_batch_threads() { return (DIMS == 2 && R == 2 && NF == 5) ? 512 : pts_max_threads<R>(); }
+constexpr int pts_batch_threads() { return (DIMS == 2 && R == 2 && NF == 5) ? 256 : pts_max_threads<R>(); }
+template <int DIMS, int R, int NF>
+constexpr int pts_batch_ctas_per_sm() { return (DIMS == 2 && R == 2 && NF == 5) ? 2 : 1; }
 
 template <int DIMS, int R, int NF, bool WL>
 __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const ProjParams<float> p)
@@ -1027,7 +1030,7 @@ __global__ void __launch_bounds__(pts_max_threads<R>(), 1) pts_kernel(const Proj
 // shared memory (held in registers they would cost the CTA its size).  *next
 // must be zero at launch.
 template <int DIMS, int R, int NF, bool WL>
-__global__ void __launch_bounds__(pts_batch_threads<DIMS, R, NF>(), 1)
+__global__ void __launch_bounds__(pts_batch_threads<DIMS, R, NF>(), pts_batch_ctas_per_sm<DIMS, R, NF>())
     pts_batch_kernel(const ProjParams<float> *params, const int2 *items, int n_items, int *next)
 {
     __shared__ int s_item;
