@@ -135,7 +135,7 @@ priest_status resolve(const priest_config &c, const priest_problem *pr, int n_ov
     sh.w_curv = pr->w_curv;
     sh.w_path = pr->w_path;
     sh.curv_eps = pr->curv_eps;
-    sh.list_delta = list_margin(sh.dims, sh.n_obs, pr->semi);
+    sh.list_delta = list_margin(sh.dims, sh.n_obs, pr->center, pr->semi);
     if (sh.cost_kind != 0 && sh.cost_kind != 1) return fail(PRIEST_ERR_INVALID, "cost_kind must be 0 or 1");
     if (sh.cost_kind == 1 &&
         (!(sh.w_acc >= 0) || !(sh.w_curv >= 0) || !(sh.w_path >= 0) || !std::isfinite(sh.w_acc) ||

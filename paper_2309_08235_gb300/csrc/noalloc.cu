@@ -114,7 +114,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     sh.w_curv = pr->w_curv;
     sh.w_path = pr->w_path;
     sh.curv_eps = pr->curv_eps;
-    sh.list_delta = list_margin(sh.dims, sh.n_obs, pr->semi);
+    sh.list_delta = list_margin(sh.dims, sh.n_obs, pr->center, pr->semi);
     if ((sh.cost_kind != 0 && sh.cost_kind != 1) ||
         (sh.cost_kind == 1 && (!(sh.w_acc >= 0) || !(sh.w_curv >= 0) || !(sh.w_path >= 0) || !fin(sh.w_acc) ||
                                !fin(sh.w_curv) || !fin(sh.w_path) || !(sh.curv_eps > 0) || !fin(sh.curv_eps))))

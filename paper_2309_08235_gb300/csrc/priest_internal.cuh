@@ -41,18 +41,43 @@ struct Shape {
 };
 
 // Neighbour-list margin of a problem: 3/4 of the mean of the obstacles'
-// smallest semi-axes (b_j = a_j in 2-D), 0 without obstacles (semi: n_obs x
-// 2).  Any positive margin gives the same results; this one balanced list
-// length against rebuild frequency on the measured workloads (a margin of
-// 0.5 to 1 mean semi-axis changed the batched rate by under 2 %).
-inline double list_margin(int dims, int n_obs, const double *semi)
+// smallest semi-axes (b_j = a_j in 2-D), 0 without obstacles (center:
+// n_obs x dims, semi: n_obs x 2).  Any positive margin gives the same
+// results; this one balanced list length against rebuild frequency on the
+// measured workloads (a margin of 0.5 to 1 mean semi-axis changed the
+// batched rate by under 2 %).  In dense scenes (64 obstacles or more) it is
+// capped so that a ball of radius (mean largest semi-axis + margin) holds
+// about two obstacle centres on average at the density of the centres'
+// bounding box, keeping the lists short of overflow; it stays at least a
+// tenth of the mean semi-axis.
+inline double list_margin(int dims, int n_obs, const double *center, const double *semi)
 {
-    double s = 0.0;
+    if (n_obs <= 0) return 0.0;
+    double s = 0.0, big = 0.0, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int j = 0; j < n_obs; ++j) {
         const double a = semi[2 * j], b = dims == 3 ? semi[2 * j + 1] : a;
         s += a < b ? a : b;
+        big += a > b ? a : b;
+        for (int ax = 0; ax < dims; ++ax) {
+            const double c = center[j * dims + ax];
+            lo[ax] = c < lo[ax] ? c : lo[ax];
+            hi[ax] = c > hi[ax] ? c : hi[ax];
+        }
     }
-    return n_obs > 0 ? 0.75 * s / n_obs : 0.0;
+    s /= n_obs;
+    big /= n_obs;
+    double delta = 0.75 * s;
+    if (n_obs >= 64) {
+        double vol = 1.0;
+        for (int ax = 0; ax < dims; ++ax) vol *= (hi[ax] - lo[ax]) + 2.0 * big;
+        const double rho = n_obs / vol, pi = 3.141592653589793;
+        // radius of the ball that holds two centres on average
+        const double r2 = dims == 2 ? __builtin_sqrt(2.0 / (pi * rho)) : __builtin_cbrt(1.5 / (pi * rho));
+        const double cap = r2 - big;
+        if (cap < delta) delta = cap;
+        if (delta < 0.1 * s) delta = 0.1 * s;
+    }
+    return delta;
 }
 
 // c_1 of the final pass (Alg. 1 cost): the point-to-point benchmark's

@@ -103,3 +103,53 @@ def test_edge_shapes(P, oracle, case):
     assert rel_err(c1, c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
     if case == "no_obstacles":
         assert rel_err(xb, oracle.project_eq(p, xi), scale_of(p)) < TOL_FP32
+
+
+@pytest.mark.parametrize("dims", [2, 3])
+def test_list_overflow_falls_back_to_full_screening(P, oracle, dims):
+    """Neighbour lists hold at most 8 (2-D) / 6 (3-D) obstacles per point:
+    twelve coincident obstacles on the start-goal line overflow the lists of
+    every point near them, and those warps screen every obstacle exactly in
+    every iteration until their next rebuild.  The results still equal the
+    oracle's (and multipliers, residuals and costs with them)."""
+    # 3-D needs n_p >= 64: a warp may touch two samples only (dims x 5 state lanes each)
+    p = scene(dims=dims, n_obs=24, n_p=60 if dims == 2 else 100, n_dyn=2)
+    c = np.asarray(p["center"], dtype=float).copy()
+    semi = np.asarray(p["semi"], dtype=float).copy()
+    mid = 0.5 * (np.asarray(p["b0"])[:, 0] + np.asarray(p["bf"])[:, 0])
+    c[:12] = mid  # twelve obstacles with one centre, on the straight line
+    semi[:12] = 0.8
+    p = dict(p, center=c, semi=semi)
+    xi = samples(oracle, p, 150, seed=31 + dims)
+    lam0 = np.random.default_rng(4).normal(0.0, 0.1, xi.shape)
+    K = 25
+    with P.Context(p, {"proj_iters": K}, precision=P.PRIEST_FP32, autotune=0) as ctx:
+        xb, lam, r, c1 = ctx.project(p, xi, lam=lam0)
+        assert P.priest_last_kernel(ctx.h) == 1
+    xb_o, lam_o = oracle.project(p, xi, K, lam=lam0)
+    r_o, c1_o = oracle.residual_cost(p, xb_o)
+    assert rel_err(xb, xb_o, scale_of(p)) < TOL_FP32
+    assert rel_err(lam, lam_o, 1.0) < TOL_FP32
+    assert rel_err(r, r_o, 1.0) < TOL_FP32
+    assert rel_err(c1, c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
+    assert np.count_nonzero(r_o > 1e-6) > 10
+
+
+def test_dense_scene_keeps_lists(P, oracle):
+    """1,500 circles in the 30 x 30 m box (the list margin shrinks with the
+    density so that the lists stay short): sampled rows against the oracle,
+    on the point-owner kernel."""
+    from paper_2309_08235_gb300 import workloads as W
+
+    p = W.scene_clutter_2d(seed=9, n_static=1350, n_dyn=150, n_p=60, horizon=4.8)
+    xi = oracle.default_mean(p) + 2.0 * W.normals(12, (400, 22))
+    K = 20
+    with P.Context(p, {"proj_iters": K}, precision=P.PRIEST_FP32, autotune=0) as ctx:
+        xb, _, r, c1 = ctx.project(p, xi)
+        assert P.priest_last_kernel(ctx.h) == 1
+    idx = np.r_[0:400:53, 399]
+    xb_o, _ = oracle.project(p, xi[idx], K)
+    r_o, c1_o = oracle.residual_cost(p, xb_o)
+    assert rel_err(xb[idx], xb_o, scale_of(p)) < TOL_FP32
+    assert rel_err(r[idx], r_o, 1.0) < TOL_FP32
+    assert rel_err(c1[idx], c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
