@@ -4,7 +4,7 @@ graph) against the FP64 oracle and against single-problem solves."""
 import numpy as np
 import pytest
 
-from gpu_common import TOL_FP32, TOL_FP64, plan_under_gap_rule, rel_err, scale_of, scene
+from gpu_common import TOL_FP32, TOL_FP64, plan_under_gap_rule, rel_err, samples, scale_of, scene
 from paper_2309_08235_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -231,5 +231,45 @@ def test_plan_batch_host_after_tuned_device_batch(P, oracle):
                 assert got["best_index"] == int(w[25]), (call, i)
                 np.testing.assert_array_equal(got["best"], w[:22])
                 assert got["c_aug"] == w[24]
+        for h in handles:
+            P.priest_unload(ctx.h, h)
+
+
+def test_project_batch_edge_cases(P, oracle):
+    """priest_project_batch with a problem of zero rows among others, no
+    multiplier lists at all, a single-row problem, and rows beyond a loaded
+    problem's sample count rejected."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    probs = uneven_problems(dims=2, n=3)
+    K = 12
+    p0, c0 = probs[0]
+    with P.Context(p0, dict(c0, proj_iters=K), precision=P.PRIEST_FP32) as ctx:
+        handles, keep, bufs, xis = [], [], [], []
+        rows = [0, 1, probs[2][1]["n_samples"]]
+        for i, ((p, cem), n) in enumerate(zip(probs, rows)):
+            prob, kp = P.make_problem(p, cem, per_problem_shape=True)
+            keep.append(kp)
+            handles.append(P.priest_load(ctx.h, prob))
+            xi = samples(oracle, p, max(n, 1), seed=60 + i)
+            xis.append(xi)
+            bufs.append([torch.from_numpy(xi).to(dev), torch.zeros_like(torch.from_numpy(xi)).to(dev),
+                         torch.zeros(max(n, 1), dtype=torch.float64, device=dev),
+                         torch.zeros(max(n, 1), dtype=torch.float64, device=dev)])
+        P.priest_project_batch(ctx.h, handles, rows, [b[0].data_ptr() for b in bufs], None,
+                               [b[1].data_ptr() for b in bufs], [b[2].data_ptr() for b in bufs],
+                               [b[3].data_ptr() for b in bufs])
+        P.priest_sync(ctx.h)
+        for (p, cem), n, xi, b in zip(probs, rows, xis, bufs):
+            if n == 0:
+                assert not b[1].abs().sum().item()  # nothing written
+                continue
+            xb_o, _ = oracle.project(p, xi[:n], K)
+            assert rel_err(b[1].cpu().numpy()[:n], xb_o, scale_of(p)) < TOL_FP32
+        with pytest.raises(P.PriestError) as e:
+            P.priest_project_batch(ctx.h, handles[:1], [probs[0][1]["n_samples"] + 1], [bufs[0][0].data_ptr()],
+                                   None, [bufs[0][1].data_ptr()], [bufs[0][2].data_ptr()], [bufs[0][3].data_ptr()])
+        assert e.value.status == P.PRIEST_ERR_INVALID
         for h in handles:
             P.priest_unload(ctx.h, h)
