@@ -348,6 +348,17 @@ priest_status priest_read_elites(priest_ctx *ctx, const priest_loaded *h, int *e
  * tensor-core kernel (PRIEST_MIXED_BF16); -1 before the first launch. */
 int priest_last_kernel(const priest_ctx *ctx);
 
+/* Instrumentation: the uniform grid over the static obstacles that the set-up
+ * step builds into a problem's FP32 tables (Sec. III-A, eq. comp_d: the point-
+ * owner kernel's neighbour-list builds screen a point's cell instead of every
+ * static obstacle).  h a loaded problem after a set-up, or NULL for the
+ * context's last host-buffer solve.  out[3] (host): cells in x, cells in y,
+ * cell entries; all 0 when the problem has no grid (fewer than 16 static
+ * obstacles, no list margin, or a cell of more than 64 obstacles).  Waits for
+ * the context stream.  Errors: PRIEST_ERR_INVALID (NULL ctx / out, nothing
+ * loaded, no FP32 tables), PRIEST_ERR_CUDA. */
+priest_status priest_grid_info(priest_ctx *ctx, const priest_loaded *h, int *out);
+
 /* The plain per-problem FP32 path: the same computation as priest_plan /
  * priest_project (same readings, same draws, FP32 projection), implemented
  * as one kernel per step with every intermediate (trajectory tiles, residual

@@ -209,7 +209,7 @@ Carve carve(const Shape &sh, bool fp32, int z_iters, bool proj_buffers)
     k.vel = take(sizeof(double) * nob * sh.dims);
     k.semi = take(sizeof(double) * nob * 2);
     k.tab64 = take(sizeof(double) * lay.total);
-    k.tab32 = take(fp32 ? sizeof(float) * lay.total : 0);
+    k.tab32 = take(fp32 ? sizeof(float) * lay.total32 : 0);
     k.cB = take(sizeof(double) * kAuxDoubles);
     k.mu = take(sizeof(double) * D);
     k.cov = take(sizeof(double) * D * D);
@@ -251,16 +251,22 @@ void carve_ptrs(priest_loaded *h, char *b, const Carve &k, bool fp32, int z_iter
     h->lam = proj_buffers ? reinterpret_cast<double *>(b + k.lam) : nullptr;
 }
 
-// PRIEST_NEIGHBOUR_LISTS=0 in the environment makes the point-owner kernel
-// screen every obstacle in every iteration (comparisons); lists are on
-// otherwise.
+// PRIEST_NEIGHBOUR_LISTS=0 in the environment (read at every launch set-up)
+// makes the point-owner kernel screen every obstacle in every iteration
+// (comparisons); lists are on otherwise.
 bool neighbour_lists()
 {
-    static const bool on = [] {
-        const char *v = getenv("PRIEST_NEIGHBOUR_LISTS");
-        return !(v && std::string(v) == "0");
-    }();
-    return on;
+    const char *v = getenv("PRIEST_NEIGHBOUR_LISTS");
+    return !(v && std::string(v) == "0");
+}
+
+// PRIEST_LIST_GRID=0 (read at every launch set-up): neighbour-list builds
+// screen every static obstacle instead of the grid's cell (comparisons; the
+// lists, and so the results, are the same).
+bool list_grid()
+{
+    const char *v = getenv("PRIEST_LIST_GRID");
+    return !(v && std::string(v) == "0");
 }
 
 template <typename Real>
@@ -294,6 +300,7 @@ ProjParams<Real> proj_params(const priest_ctx *ctx, const priest_loaded *h, cons
     p.seg_len = h->seg_len;
     p.cost = make_cost<Real>(sh);
     p.list_delta = neighbour_lists() ? Real(sh.list_delta) : Real(0);
+    p.list_grid = list_grid() ? 1 : 0;
     return p;
 }
 
@@ -2081,6 +2088,23 @@ priest_status priest_read_elites(priest_ctx *ctx, const priest_loaded *h, int *e
 }
 
 int priest_last_kernel(const priest_ctx *ctx) { return ctx ? ctx->last_kind : -1; }
+
+priest_status priest_grid_info(priest_ctx *ctx, const priest_loaded *h, int *out)
+{
+    if (!ctx || !out) return PRIEST_ERR_INVALID;
+    const priest_loaded *src = h ? h : ctx->scratch;
+    if (!src) return fail(ctx, PRIEST_ERR_INVALID, "no loaded problem to read");
+    if (!src->tab32) return fail(ctx, PRIEST_ERR_INVALID, "the problem has no FP32 tables");
+    const Shape &sh = src->sh;
+    const TableLayout lay = table_layout(sh.dims, sh.nv, sh.nf, sh.n_p, sh.n_obs);
+    int hdr[8];
+    PRIEST_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    PRIEST_CUDA(ctx, cudaMemcpy(hdr, src->tab32 + lay.grid, sizeof(hdr), cudaMemcpyDeviceToHost));
+    out[0] = hdr[4];
+    out[1] = hdr[5];
+    out[2] = hdr[4] > 0 ? hdr[6] : 0;
+    return PRIEST_OK;
+}
 
 
 priest_status priest_rng_normal(uint64_t seed, int64_t count, double *out)

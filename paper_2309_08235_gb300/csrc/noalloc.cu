@@ -151,7 +151,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
     const size_t off_tab64 = o;
     o = up256(o + sizeof(double) * lay.total);
     const size_t off_tab32 = o;
-    o = up256(o + (fp32 ? sizeof(float) * lay.total : 0));
+    o = up256(o + (fp32 ? sizeof(float) * lay.total32 : 0));
     if (o > kNoAllocScratchBytes) return PRIEST_ERR_BUDGET;  // beyond the fixed 1 MiB scratch
 
     // ---- the scratch's device address for the current device (first call per device)
@@ -229,6 +229,7 @@ extern "C" priest_status priest_project_noalloc(const priest_config *cfg, const 
         p.xi_bar = xi_bar_dev; p.r_out = resid_dev; p.c1_out = cost_dev;
         p.cost = make_cost<float>(sh);
         p.list_delta = float(sh.list_delta);
+        p.list_grid = 1;
         if (launch_project<float>(p, t, st) != cudaSuccess) return PRIEST_ERR_CUDA;
     } else {
         const Tiling t = choose_tiling<double>(sh, n, n_sm);

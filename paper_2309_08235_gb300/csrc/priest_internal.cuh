@@ -163,6 +163,42 @@ __host__ __device__ inline int fb_stride(int nf)
     return ((s / 4) % 2 == 0) ? s + 4 : s;
 }
 
+// Uniform grid over the static obstacles in the x-y plane, built by the set-up
+// kernel into the FP32 tables: the point-owner kernel's neighbour-list builds
+// look up a point's cell instead of screening every static obstacle.  A cell
+// lists, in increasing order, the static obstacles whose screening disc (the
+// radius the inflated pre-filter can accept, plus slack) meets it; cells are
+// at least twice the largest such radius, so an obstacle meets at most 2 x 2
+// cells.  Region (4-byte units): header [x0, y0, 1/h, h, nx, ny, entries, 0]
+// (nx = 0: no grid), cell starts (uint16, nx * ny + 1), entries (uint16, at
+// most 4 per obstacle), then the set-up's per-obstacle cell ranges.
+constexpr int kGridMinStatic = 16;  // fewer static obstacles: screened directly
+constexpr int kGridCellMax = 64;    // a fuller cell turns the grid off for the problem
+__host__ __device__ inline int grid_side(int ns)
+{
+    int g = 4;
+    while (g < 32 && g * g < 2 * ns) ++g;
+    return g;
+}
+struct GridLayout {
+    size_t start, ent, rng, smem, total;  // smem: header, starts and entries (what the kernel stages)
+};
+__host__ __device__ inline GridLayout grid_layout(int ns)
+{
+    GridLayout g;
+    g.start = 8;
+    if (ns < kGridMinStatic) {
+        g.ent = g.rng = g.smem = g.total = 8;
+        return g;
+    }
+    const int gs = grid_side(ns);
+    g.ent = g.start + align8(size_t(gs * gs + 2) / 2);
+    g.rng = g.ent + align8(size_t(2) * ns);
+    g.smem = g.rng;
+    g.total = g.rng + align8(size_t(ns));
+    return g;
+}
+
 // Per-problem device tables, in units of Real, one contiguous buffer.
 struct TableLayout {
     size_t basis;  // [3][n_p][nv]   P, Pd, Pdd
@@ -173,6 +209,8 @@ struct TableLayout {
     size_t tval;   // [n_p]          time stamps
     size_t origin; // [3]            shift applied to positions and obstacle centres
     size_t total;
+    size_t grid;   // FP32 tables only: the static-obstacle grid (grid_layout of n_static <= n_obs)
+    size_t total32; // floats of an FP32 table buffer (total + the grid region)
 };
 
 __host__ __device__ inline TableLayout table_layout(int dims, int nv, int nf, int n_p, int n_obs)
@@ -194,6 +232,8 @@ __host__ __device__ inline TableLayout table_layout(int dims, int nv, int nf, in
     t.origin = o;
     o = align8(o + 3);
     t.total = o;
+    t.grid = o;
+    t.total32 = o + grid_layout(n_obs).total;
     return t;
 }
 
@@ -224,6 +264,7 @@ struct ProjParams {
                                             // segment of seg_len rows; 0 = a single distribution)
     Real list_delta;                        // point-owner kernel: neighbour-list margin (0: screen every
                                             // obstacle in every iteration)
+    int list_grid;                          // 1: list builds use the tables' static-obstacle grid
     CostParams<Real> cost;
     Real rho, vmax, amax, smin[3], smax[3];
     const Real *tab;

@@ -18,17 +18,19 @@
 //     rebuilds its lists when one of its points has moved farther than
 //     7/8 delta since the last rebuild (always in the first iteration; one
 //     vote of the whole CTA, so rebuilds do not hold warps at the barrier
-//     of phase C one warp at a time): every
-//     obstacle is screened then -- static ones four at a time from "quad"
-//     records whose thresholds are inflated by delta (one f32x2 FMA evaluates
-//     a point against two obstacles), moving ones two at a time by their
-//     scaled offsets -- and the flagged ones are appended to the lists.  An
+//     of phase C one warp at a time): a point then screens the static
+//     obstacles of its cell of the tables' uniform grid (or, without a grid,
+//     every static obstacle four at a time from "quad" records, one f32x2 FMA
+//     evaluating a point against two obstacles), with thresholds inflated by
+//     delta, and every moving obstacle, two at a time by their scaled
+//     offsets; the flagged ones are appended to the lists.  An
 //     obstacle left out lies at least a_j + delta from the point's rebuild
 //     position, so while the point stays within 7/8 delta of it the pair is
 //     inactive (its residual row is zero) and skipping it changes nothing; the
 //     eighth of delta held back covers the FP32 rounding of the screening.
-//     The exact tests run in obstacle order, so the sums are those of testing
-//     every obstacle.  A warp whose lists overflowed screens every obstacle
+//     The exact tests run in obstacle order with one FMA per accumulated
+//     term on every path, so the sums are bitwise those of testing every
+//     obstacle.  A warp whose lists overflowed screens every obstacle
 //     and tests its candidates exactly in every iteration until its next
 //     rebuild; residuals S_o accumulate in registers;
 //   * phase C forms each thread's share of g on the free columns and reduces
@@ -76,9 +78,11 @@ using detail::kFull;
 //                           (1/a, 1/b, -o_x(t)/a, -o_y(t)/a)
 //   listz [R][cap][tl]      3-D: -o_z(t)/b
 //   listi [R][cap][tl]      3-D (uint16): the obstacle's index (its a, b for active pairs)
+//   grid  [gl.smem]         the static-obstacle grid of the tables (header, cell starts,
+//                           entries; none below kGridMinStatic static obstacles)
 struct PtsLayout {
     int tps, nq, nm2, maxw, cds, tl, cap;
-    size_t obs, srec, mrec, W, cd, lam, xi, part, part2, ref, list, listz, listi, total;
+    size_t obs, srec, mrec, W, cd, lam, xi, part, part2, ref, list, listz, listi, grid, gsz, total;
 };
 
 // Neighbour-list entries per point.
@@ -131,6 +135,9 @@ __host__ __device__ inline PtsLayout pts_layout(int dims, int nf, int nv, int n_
     o = align8(o + (dims == 3 ? size_t(R) * L.cap * L.tl : 0));
     L.listi = o;
     o = align8(o + (dims == 3 ? (size_t(R) * L.cap * L.tl + 1) / 2 : 0));
+    L.grid = o;
+    L.gsz = n_static >= kGridMinStatic ? grid_layout(n_static).smem : 0;
+    o = align8(o + L.gsz);
     L.total = o;
     return L;
 }
@@ -164,7 +171,8 @@ __device__ __forceinline__ void active_add(float dx, float dy, float dz, float q
             so[1] = fmaf(a * w, dy, so[1]);
             if constexpr (DIMS == 3) so[DIMS - 1] = fmaf(b * w, dz, so[DIMS - 1]);
         } else {
-            const float d2 = (DIMS == 3) ? a * a * fmaf(dx, dx, dy * dy) + b * b * dz * dz : a * a * q;
+            // one explicit FMA: every inlined copy rounds the same way
+            const float d2 = (DIMS == 3) ? fmaf(b * b * dz, dz, a * a * fmaf(dx, dx, dy * dy)) : a * a * q;
             so[0] = fmaf(w * w, d2, so[0]);
         }
     } else {
@@ -222,18 +230,6 @@ __device__ __forceinline__ void quad_values(const float *q, float2 xd, float2 yd
     }
 }
 
-// Contribution of static obstacle j to one point (zero when the exact test
-// fails): x - e (or its squared norm in the final pass) as in active_add.
-template <int DIMS>
-__device__ __forceinline__ float3 static_contrib(const float *sObs, int j, float x, float y, float z, bool fin)
-{
-    float so[DIMS];
-#pragma unroll
-    for (int ax = 0; ax < DIMS; ++ax) so[ax] = 0.f;
-    exact_static<DIMS>(sObs, j, x, y, z, fin, so);
-    return make_float3(so[0], so[1], DIMS == 3 ? so[DIMS - 1] : 0.f);
-}
-
 template <typename T, int R>
 __device__ __forceinline__ T pick(const T (&a)[R], int r)
 {
@@ -248,7 +244,8 @@ __device__ __forceinline__ T pick(const T (&a)[R], int r)
 // of `cand` flags point r against quad k + i.  Candidates are visited point by
 // point in obstacle order; the four obstacles of a flagged quad are
 // re-evaluated with the same operations and the ones below the threshold
-// tested exactly.
+// tested exactly, accumulated into the point's sums as the list path does
+// (one FMA per term), so both paths give the same sums.
 template <int DIMS, int R, int NB>
 __device__ __forceinline__ void quad_candidates(unsigned cand, const float *srec, const float *sObs, int k,
                                                 const detail::PackedPoints<DIMS, R> &P, bool fin,
@@ -268,15 +265,9 @@ __device__ __forceinline__ void quad_candidates(unsigned cand, const float *srec
         while (hb) {
             const int h = __ffs(hb) - 1;
             hb &= hb - 1;
-            const float3 c = static_contrib<DIMS>(sObs, 4 * (k + i) + h, xd.x, yd.x, zd.x, fin);
 #pragma unroll
-            for (int rr = 0; rr < R; ++rr) {
-                if (rr == r) {
-                    so[rr][0] += c.x;
-                    so[rr][1] += c.y;
-                    if constexpr (DIMS == 3) so[rr][DIMS - 1] += c.z;
-                }
-            }
+            for (int rr = 0; rr < R; ++rr)
+                if (rr == r) exact_static<DIMS>(sObs, 4 * (k + i) + h, xd.x, yd.x, zd.x, fin, so[rr]);
         }
     }
 }
@@ -431,14 +422,19 @@ struct PtsLists {
 
 // Neighbour lists of the thread's R points (4 bits of count per point in the
 // returned word, kListOverflow set when a point had more than list_cap
-// obstacles): every static quad screened with its inflated thresholds and
-// every moving pair by its scaled offsets against (1 + delta max(1/a, 1/b))^2,
-// the flagged obstacles appended in obstacle order with their offset terms at
-// the point's time.  Padding entries of the quad and pair records are never
-// flagged.
+// obstacles): the static obstacles screened with the quads' inflated
+// thresholds and every moving pair by its scaled offsets against
+// (1 + delta max(1/a, 1/b))^2, the flagged obstacles appended in obstacle
+// order with their offset terms at the point's time.  With a grid (gsm: its
+// region, nx > 0) a point screens only the static obstacles of its cell, each
+// with the arithmetic of its lane of the quad test, in increasing order; the
+// cell holds every obstacle that test can pass for a point in it, so the lists
+// are the same as with every quad screened.  Padding entries of the quad and
+// pair records are never flagged.
 template <int DIMS, int R>
-__device__ __forceinline__ unsigned build_lists(const float *srec, const float *mrec, const float *sObs, int nq,
-                                                int nm2, int ns, const detail::PackedPoints<DIMS, R> &P, float delta,
+__device__ __forceinline__ unsigned build_lists(const float *srec, const float *mrec, const float *sObs,
+                                                const float *gsm, int nq, int nm2, int ns,
+                                                const detail::PackedPoints<DIMS, R> &P, float delta,
                                                 const PtsLists &Ls, int tid)
 {
     constexpr int QS = DIMS == 2 ? 12 : 20;
@@ -463,6 +459,33 @@ __device__ __forceinline__ unsigned build_lists(const float *srec, const float *
             cnt |= kListOverflow;
         }
     };
+    const int gnx = gsm ? __float_as_int(gsm[4]) : 0;
+    if (gnx > 0) {
+        const int gny = __float_as_int(gsm[5]);
+        const float gx0 = gsm[0], gy0 = gsm[1], gih = gsm[2];
+        const unsigned short *gstart = reinterpret_cast<const unsigned short *>(gsm + 8);
+        const unsigned short *gent = reinterpret_cast<const unsigned short *>(gsm + grid_layout(ns).ent);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float x = P.x[r].x, y = P.y[r].x;
+            const float fx = (x - gx0) * gih, fy = (y - gy0) * gih;
+            if (fx >= 0.f && fx < float(gnx) && fy >= 0.f && fy < float(gny)) {
+                const int c = min(int(fy), gny - 1) * gnx + min(int(fx), gnx - 1);
+                const int e1 = gstart[c + 1];
+                const float npq = P.npq[r], t = P.t[r].x;
+                for (int e = gstart[c]; e < e1; ++e) {
+                    const int jo = gent[e];
+                    const float *q = srec + size_t(jo >> 2) * QS + (jo & 3);
+                    float v;
+                    if constexpr (DIMS == 2)
+                        v = fmaf(x, q[0], fmaf(y, q[4], q[8]));
+                    else
+                        v = fmaf(x, q[0], fmaf(y, q[4], fmaf(P.z[r].x, q[8], fmaf(P.zz[r].x, q[12], q[16]))));
+                    if (v < npq) append(r, jo, t);
+                }
+            }
+        }
+    } else
     for (int k = 0; k < nq; ++k) {
         const float *q = srec + size_t(k) * QS;
 #pragma unroll
@@ -571,6 +594,9 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
         float4 *dst = reinterpret_cast<float4 *>(sObs);
         for (int i = tid; i < nobs * ST / 4; i += T) dst[i] = src[i];
         for (int i = tid; i < NF * NF; i += T) sW[i] = p.tab[p.lay.W + i];
+        const float4 *gsrc = reinterpret_cast<const float4 *>(p.tab + p.lay.grid);
+        float4 *gdst = reinterpret_cast<float4 *>(sm + L.grid);
+        for (int i = tid; i < int(L.gsz / 4); i += T) gdst[i] = gsrc[i];
     }
     for (int e = tid; e < S_act * D; e += T) {
         const int ss = e / D, d = e - ss * D;
@@ -806,7 +832,8 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                     }
                 }
                 if (__syncthreads_or(moved)) {
-                    lcnt = build_lists<DIMS, R>(sm + L.srec, sm + L.mrec, sObs, L.nq, L.nm2, ns, P, dl, Ls, tid);
+                    lcnt = build_lists<DIMS, R>(sm + L.srec, sm + L.mrec, sObs, L.gsz && p.list_grid ? sm + L.grid : nullptr, L.nq,
+                                                L.nm2, ns, P, dl, Ls, tid);
                     if (act) {
 #pragma unroll
                         for (int r = 0; r < R; ++r)

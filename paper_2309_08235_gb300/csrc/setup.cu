@@ -40,6 +40,172 @@ __device__ void bernstein_levels(int n, double tau, double *bn, double *bn1, dou
     for (int j = 0; j <= n; ++j) bn[j] = b[j];
 }
 
+// Rounding margin of the expanded pre-filter of one obstacle record
+// (|o|^2-scaled, so it also bounds the rounding for points near the obstacle).
+__device__ inline double screen_margin(double oo, double a, double kap, int dims, double eps)
+{
+    const double on = double(sqrtf(float(oo)) * 1.001f) + a + 1.0;  // bound only
+    return 64.0 * eps * (4.0 * on * on) * (dims == 3 ? 1.0 + kap : 1.0);
+}
+
+// Step (9), FP32 tables: the uniform grid over the static obstacles (layout in
+// priest_internal.cuh) for the point-owner kernel's neighbour-list builds.
+// The pre-filter of the list build (thresholds inflated by the list margin
+// delta) accepts a point only within the x-y radius
+//   rho^2 = R^2 (1 + 1e-5) + 2 margin,  R = a + delta (2-D),
+//   R = a (1 + delta max(1/a, 1/b)) (3-D),
+// (the factor covers the FP32 evaluation of the expanded test and of the
+// inflation); every obstacle is entered in each cell its square of half-width
+// rho + h/1000 meets, so a cell's list holds every static obstacle that any
+// point the kernel maps to the cell can pass, in increasing order.  Counting
+// and filling use shared-memory atomics, then each cell is sorted; a cell of
+// more than kGridCellMax obstacles (or no margin) leaves nx = 0 (no grid).
+__device__ void build_grid(const SetupParams &p, const double *org, float *reg, double eps)
+{
+    const Shape &sh = p.sh;
+    const int ns = sh.n_static, dims = sh.dims, tid = threadIdx.x, T = blockDim.x;
+    int *ireg = reinterpret_cast<int *>(reg);
+    const GridLayout gl = grid_layout(ns);
+    __shared__ int s_cnt[32 * 32 + 1];
+    __shared__ double s_red[5][kSetupThreads / 32];
+    __shared__ float s_geo[4];  // x0, y0, h, 1/h
+    __shared__ int s_n[3];      // nx, ny, fullest cell
+    if (ns < kGridMinStatic || !(sh.list_delta > 0.0)) {
+        if (tid == 0) {
+            for (int i = 0; i < 8; ++i) ireg[i] = 0;
+        }
+        return;
+    }
+    const double delta = sh.list_delta;
+    auto radius = [&](int j) {
+        const double a = p.semi[2 * j], b = dims == 3 ? p.semi[2 * j + 1] : a;
+        const double kap = (a * a) * (rcp_any(b) * rcp_any(b));
+        double oo = 0.0;
+        for (int ax = 0; ax < dims; ++ax) {
+            const double cc = p.center[j * dims + ax] - org[ax];
+            oo += (ax == 2 ? kap : 1.0) * cc * cc;
+        }
+        const double R = dims == 3 ? a * (1.0 + delta * fmax(rcp_any(a), rcp_any(b))) : a + delta;
+        return sqrt(R * R * (1.0 + 1e-5) + 2.0 * screen_margin(oo, a, kap, dims, eps));
+    };
+    // extent of the screening discs and the largest radius
+    double v[5] = {1e300, 1e300, -1e300, -1e300, 0.0};
+    for (int j = tid; j < ns; j += T) {
+        const double r = radius(j), cx = p.center[j * dims] - org[0], cy = p.center[j * dims + 1] - org[1];
+        v[0] = fmin(v[0], cx - r);
+        v[1] = fmin(v[1], cy - r);
+        v[2] = fmax(v[2], cx + r);
+        v[3] = fmax(v[3], cy + r);
+        v[4] = fmax(v[4], r);
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        for (int i = 0; i < 5; ++i) {
+            const double o = __shfl_xor_sync(0xffffffffu, v[i], off);
+            v[i] = i < 2 ? fmin(v[i], o) : fmax(v[i], o);
+        }
+    if ((tid & 31) == 0)
+        for (int i = 0; i < 5; ++i) s_red[i][tid >> 5] = v[i];
+    for (int c = tid; c <= 32 * 32; c += T) s_cnt[c] = 0;
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < (T + 31) / 32; ++w)
+            for (int i = 0; i < 5; ++i) v[i] = i < 2 ? fmin(v[i], s_red[i][w]) : fmax(v[i], s_red[i][w]);
+        const int gs = grid_side(ns);
+        const double ext = fmax(v[2] - v[0], v[3] - v[1]);
+        const float h = float(fmax(2.02 * v[4], ext / (gs - 0.1)));
+        const float x0 = float(v[0] - 0.02 * h), y0 = float(v[1] - 0.02 * h);
+        s_geo[0] = x0;
+        s_geo[1] = y0;
+        s_geo[2] = h;
+        s_geo[3] = 1.0f / h;
+        s_n[0] = min(gs, max(1, int(ceil((v[2] - x0) / h + 0.01))));
+        s_n[1] = min(gs, max(1, int(ceil((v[3] - y0) / h + 0.01))));
+        s_n[2] = 0;
+    }
+    __syncthreads();
+    const double x0 = s_geo[0], y0 = s_geo[1], h = s_geo[2], ih = s_geo[3];
+    const int nx = s_n[0], ny = s_n[1];
+    unsigned short *start = reinterpret_cast<unsigned short *>(reg + gl.start);
+    unsigned short *ent = reinterpret_cast<unsigned short *>(reg + gl.ent);
+    int *rng = reinterpret_cast<int *>(reg + gl.rng);
+    // cell ranges (8 bits each: x0 x1 y0 y1) and counts
+    for (int j = tid; j < ns; j += T) {
+        const double r = radius(j) + 1e-3 * h;
+        const double cx = p.center[j * dims] - org[0], cy = p.center[j * dims + 1] - org[1];
+        const int ax0 = max(0, int(floor((cx - r - x0) * ih))), ax1 = min(nx - 1, int(floor((cx + r - x0) * ih)));
+        const int ay0 = max(0, int(floor((cy - r - y0) * ih))), ay1 = min(ny - 1, int(floor((cy + r - y0) * ih)));
+        rng[j] = ax0 | (ax1 << 8) | (ay0 << 16) | (ay1 << 24);
+        for (int cy2 = ay0; cy2 <= ay1; ++cy2)
+            for (int cx2 = ax0; cx2 <= ax1; ++cx2) atomicAdd(&s_cnt[cy2 * nx + cx2], 1);
+    }
+    __syncthreads();
+    // cell starts (exclusive prefix sum by one warp) and the fullest cell
+    const int nc = nx * ny;
+    if (tid < 32) {
+        const int per = (nc + 31) / 32, b0 = tid * per;
+        int sum = 0, big = 0;
+        for (int c = b0; c < min(nc, b0 + per); ++c) {
+            sum += s_cnt[c];
+            big = max(big, s_cnt[c]);
+        }
+        int inc = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, inc, off);
+            if (tid >= off) inc += o;
+        }
+        for (int off = 16; off > 0; off >>= 1) big = max(big, __shfl_xor_sync(0xffffffffu, big, off));
+        int run = inc - sum;
+        for (int c = b0; c < min(nc, b0 + per); ++c) {
+            const int n = s_cnt[c];
+            start[c] = static_cast<unsigned short>(run);
+            s_cnt[c] = run;  // fill cursor
+            run += n;
+        }
+        if (tid == 31) {
+            start[nc] = static_cast<unsigned short>(inc);
+            s_n[2] = big;
+            ireg[6] = inc;
+        }
+    }
+    __syncthreads();
+    if (s_n[2] > kGridCellMax) {
+        if (tid == 0) {
+            for (int i = 0; i < 8; ++i) ireg[i] = 0;
+        }
+        return;
+    }
+    for (int j = tid; j < ns; j += T) {
+        const int g = rng[j];
+        const int gx0 = g & 255, gx1 = (g >> 8) & 255, gy0 = (g >> 16) & 255, gy1 = (g >> 24) & 255;
+        for (int cy2 = gy0; cy2 <= gy1; ++cy2)
+            for (int cx2 = gx0; cx2 <= gx1; ++cx2)
+                ent[atomicAdd(&s_cnt[cy2 * nx + cx2], 1)] = static_cast<unsigned short>(j);
+    }
+    __syncthreads();
+    // entries of each cell in increasing obstacle order (insertion sort)
+    for (int c = tid; c < nc; c += T) {
+        const int e0 = start[c], e1 = start[c + 1];
+        for (int e = e0 + 1; e < e1; ++e) {
+            const unsigned short x = ent[e];
+            int i = e - 1;
+            while (i >= e0 && ent[i] > x) {
+                ent[i + 1] = ent[i];
+                --i;
+            }
+            ent[i + 1] = x;
+        }
+    }
+    if (tid == 0) {
+        reg[0] = s_geo[0];
+        reg[1] = s_geo[1];
+        reg[2] = s_geo[3];
+        reg[3] = s_geo[2];
+        ireg[4] = nx;
+        ireg[5] = ny;
+        ireg[7] = 0;
+    }
+}
+
 template <typename Real>
 __device__ void write_tables(const SetupParams &p, const double *src, size_t from, size_t to)
 {
@@ -202,9 +368,7 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
         double c[3];
         for (int ax = 0; ax < 3; ++ax) c[ax] = (ax < dims) ? p.center[j * dims + ax] - s_org[ax] : 0.0;
         const double oo = c[0] * c[0] + c[1] * c[1] + (dims == 3 ? kap * c[2] * c[2] : 0.0);
-        const double on = double(sqrtf(float(oo)) * 1.001f) + a + 1.0;  // bound only
-        const double margin = 64.0 * eps * (4.0 * on * on) * (dims == 3 ? 1.0 + kap : 1.0);
-        const double thr = a * a - oo + margin;
+        const double thr = a * a - oo + screen_margin(oo, a, kap, dims, eps);
         if (dims == 2) {
             o[0] = -2.0 * c[0]; o[1] = -2.0 * c[1]; o[2] = thr; o[3] = a;
             o[4] = ia; o[5] = -c[0] * ia; o[6] = -c[1] * ia; o[7] = 0.0;
@@ -245,8 +409,9 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
         if (tid == 0 && !ok) atomicOr(p.status, kStatusCholesky);
     }
     __syncthreads();
-    // (8) working-precision copy of the tables
+    // (8) working-precision copy of the tables; (9) the static-obstacle grid
     if (!p.real_is_double) {
+        build_grid(p, s_org, reinterpret_cast<float *>(p.tab) + lay.grid, eps);
         if (p.shape_ready)
             write_tables<float>(p, tab64, lay.base, lay.total);  // basis and packed basis unchanged
         else

@@ -35,7 +35,8 @@ EXPORTS = ["priest_create", "priest_destroy", "priest_last_error", "priest_proje
            "priest_project_noalloc", "priest_plan_batch", "priest_wait", "priest_serve_stats_get",
            "priest_rng_normal_device", "priest_plan_plain", "priest_plan_plain_device",
            "priest_project_plain", "priest_tc_selftest", "priest_plan_multi", "priest_chol_selftest",
-           "priest_plan_batch_host", "priest_project_batch", "priest_read_elites", "priest_last_kernel"]
+           "priest_plan_batch_host", "priest_project_batch", "priest_read_elites", "priest_last_kernel",
+           "priest_grid_info"]
 
 
 class PriestError(RuntimeError):
@@ -128,6 +129,7 @@ def lib():
                                                C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]),
             "priest_read_elites": (C.c_int, [vp, vp, C.POINTER(C.c_int), _P, _P]),
             "priest_last_kernel": (C.c_int, [vp]),
+            "priest_grid_info": (C.c_int, [vp, vp, C.POINTER(C.c_int)]),
             "priest_wait": (C.c_int, [vp, C.c_uint64, C.c_double, C.POINTER(priest_result)]),
             "priest_serve_stats_get": (C.c_int, [vp, C.POINTER(priest_serve_stats)]),
             "priest_rng_normal_device": (C.c_int, [C.c_uint64, C.c_int64, vp, vp]),
@@ -417,6 +419,15 @@ def priest_read_elites(ctx, h, n_elite, n):
 
 def priest_last_kernel(ctx):
     return int(lib().priest_last_kernel(ctx))
+
+
+def priest_grid_info(ctx, h=None):
+    """(cells in x, cells in y, entries) of the static-obstacle grid of a
+    loaded problem's FP32 tables (h None: the context's last host-buffer
+    solve); zeros without a grid."""
+    out = (C.c_int * 3)()
+    _check(ctx, lib().priest_grid_info(ctx, h, out))
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def priest_project_device(ctx, h, n, xi_ptr, lam_ptr, xb_ptr, r_ptr, c1_ptr):
