@@ -55,19 +55,21 @@ __device__ inline double screen_margin(double oo, double a, double kap, int dims
 //   rho^2 = R^2 (1 + 1e-5) + 2 margin,  R = a + delta (2-D),
 //   R = a (1 + delta max(1/a, 1/b)) (3-D),
 // (the factor covers the FP32 evaluation of the expanded test and of the
-// inflation); every obstacle is entered in each cell its square of half-width
-// rho + h/1000 meets, so a cell's list holds every static obstacle that any
-// point the kernel maps to the cell can pass, in increasing order.  Counting
-// and filling use shared-memory atomics, then each cell is sorted; a cell of
-// more than kGridCellMax obstacles (or no margin) leaves nx = 0 (no grid).
-__device__ void build_grid(const SetupParams &p, const double *org, float *reg, double eps)
+// inflation; rho itself is evaluated in FP32 and enlarged by another factor
+// 1 + 1e-5, far above that evaluation's rounding); every obstacle is entered
+// in each cell its square of half-width rho + h/1000 meets, so a cell's list
+// holds every static obstacle that any point the kernel maps to the cell can
+// pass, in increasing order.  Counting and filling use shared-memory atomics,
+// then each cell is sorted; a cell of more than kGridCellMax obstacles (or no
+// margin) leaves nx = 0 (no grid).
+__device__ void build_grid(const SetupParams &p, const double *org, float *reg, float eps)
 {
     const Shape &sh = p.sh;
-    const int ns = sh.n_static, dims = sh.dims, tid = threadIdx.x, T = blockDim.x;
+    const int ns = sh.n_static, dims = sh.dims, tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
     int *ireg = reinterpret_cast<int *>(reg);
     const GridLayout gl = grid_layout(ns);
     __shared__ int s_cnt[32 * 32 + 1];
-    __shared__ double s_red[5][kSetupThreads / 32];
+    __shared__ float s_red[5][kSetupThreads / 32];
     __shared__ float s_geo[4];  // x0, y0, h, 1/h
     __shared__ int s_n[3];      // nx, ny, fullest cell
     if (ns < kGridMinStatic || !(sh.list_delta > 0.0)) {
@@ -76,64 +78,78 @@ __device__ void build_grid(const SetupParams &p, const double *org, float *reg, 
         }
         return;
     }
-    const double delta = sh.list_delta;
-    auto radius = [&](int j) {
-        const double a = p.semi[2 * j], b = dims == 3 ? p.semi[2 * j + 1] : a;
-        const double kap = (a * a) * (rcp_any(b) * rcp_any(b));
-        double oo = 0.0;
+    const float delta = float(sh.list_delta);
+    // centre (x, y) relative to the origin and screening radius of obstacle j
+    auto geometry = [&](int j, float &cx, float &cy) {
+        const float a = float(p.semi[2 * j]), b = dims == 3 ? float(p.semi[2 * j + 1]) : a;
+        const float kap = (a * a) / (b * b);
+        float oo = 0.f;
         for (int ax = 0; ax < dims; ++ax) {
-            const double cc = p.center[j * dims + ax] - org[ax];
-            oo += (ax == 2 ? kap : 1.0) * cc * cc;
+            const float c = float(p.center[j * dims + ax] - org[ax]);
+            oo += (ax == 2 ? kap : 1.f) * c * c;
+            if (ax == 0) cx = c;
+            if (ax == 1) cy = c;
         }
-        const double R = dims == 3 ? a * (1.0 + delta * fmax(rcp_any(a), rcp_any(b))) : a + delta;
-        return sqrt(R * R * (1.0 + 1e-5) + 2.0 * screen_margin(oo, a, kap, dims, eps));
+        const float on = sqrtf(oo) * 1.001f + a + 1.f;  // as the record's margin
+        const float margin = 64.f * eps * (4.f * on * on) * (dims == 3 ? 1.f + kap : 1.f);
+        const float R = dims == 3 ? a * (1.f + delta * fmaxf(1.f / a, 1.f / b)) : a + delta;
+        return sqrtf((R * R * (1.f + 1e-5f) + 2.f * margin) * (1.f + 1e-5f));
     };
-    // extent of the screening discs and the largest radius
-    double v[5] = {1e300, 1e300, -1e300, -1e300, 0.0};
+    // extent of the screening discs and the largest radius (warp, then one warp over the warps)
+    const float big = 3.0e38f;
+    float v[5] = {big, big, -big, -big, 0.f};
     for (int j = tid; j < ns; j += T) {
-        const double r = radius(j), cx = p.center[j * dims] - org[0], cy = p.center[j * dims + 1] - org[1];
-        v[0] = fmin(v[0], cx - r);
-        v[1] = fmin(v[1], cy - r);
-        v[2] = fmax(v[2], cx + r);
-        v[3] = fmax(v[3], cy + r);
-        v[4] = fmax(v[4], r);
+        float cx = 0.f, cy = 0.f;
+        const float r = geometry(j, cx, cy);
+        v[0] = fminf(v[0], cx - r);
+        v[1] = fminf(v[1], cy - r);
+        v[2] = fmaxf(v[2], cx + r);
+        v[3] = fmaxf(v[3], cy + r);
+        v[4] = fmaxf(v[4], r);
     }
     for (int off = 16; off > 0; off >>= 1)
         for (int i = 0; i < 5; ++i) {
-            const double o = __shfl_xor_sync(0xffffffffu, v[i], off);
-            v[i] = i < 2 ? fmin(v[i], o) : fmax(v[i], o);
+            const float o = __shfl_xor_sync(0xffffffffu, v[i], off);
+            v[i] = i < 2 ? fminf(v[i], o) : fmaxf(v[i], o);
         }
-    if ((tid & 31) == 0)
+    if (lane == 0)
         for (int i = 0; i < 5; ++i) s_red[i][tid >> 5] = v[i];
     for (int c = tid; c <= 32 * 32; c += T) s_cnt[c] = 0;
     __syncthreads();
-    if (tid == 0) {
-        for (int w = 1; w < (T + 31) / 32; ++w)
-            for (int i = 0; i < 5; ++i) v[i] = i < 2 ? fmin(v[i], s_red[i][w]) : fmax(v[i], s_red[i][w]);
-        const int gs = grid_side(ns);
-        const double ext = fmax(v[2] - v[0], v[3] - v[1]);
-        const float h = float(fmax(2.02 * v[4], ext / (gs - 0.1)));
-        const float x0 = float(v[0] - 0.02 * h), y0 = float(v[1] - 0.02 * h);
-        s_geo[0] = x0;
-        s_geo[1] = y0;
-        s_geo[2] = h;
-        s_geo[3] = 1.0f / h;
-        s_n[0] = min(gs, max(1, int(ceil((v[2] - x0) / h + 0.01))));
-        s_n[1] = min(gs, max(1, int(ceil((v[3] - y0) / h + 0.01))));
-        s_n[2] = 0;
+    if (tid < 32) {
+        const int nw = (T + 31) / 32;
+        for (int i = 0; i < 5; ++i) v[i] = lane < nw ? s_red[i][lane] : (i < 2 ? big : (i < 4 ? -big : 0.f));
+        for (int off = 16; off > 0; off >>= 1)
+            for (int i = 0; i < 5; ++i) {
+                const float o = __shfl_xor_sync(0xffffffffu, v[i], off);
+                v[i] = i < 2 ? fminf(v[i], o) : fmaxf(v[i], o);
+            }
+        if (lane == 0) {
+            const int gs = grid_side(ns);
+            const float ext = fmaxf(v[2] - v[0], v[3] - v[1]);
+            const float h = fmaxf(2.02f * v[4], ext / (float(gs) - 0.1f));
+            const float x0 = v[0] - 0.02f * h, y0 = v[1] - 0.02f * h;
+            s_geo[0] = x0;
+            s_geo[1] = y0;
+            s_geo[2] = h;
+            s_geo[3] = 1.0f / h;
+            s_n[0] = min(gs, max(1, int(ceilf((v[2] - x0) / h + 0.01f))));
+            s_n[1] = min(gs, max(1, int(ceilf((v[3] - y0) / h + 0.01f))));
+            s_n[2] = 0;
+        }
     }
     __syncthreads();
-    const double x0 = s_geo[0], y0 = s_geo[1], h = s_geo[2], ih = s_geo[3];
+    const float x0 = s_geo[0], y0 = s_geo[1], h = s_geo[2], ih = s_geo[3];
     const int nx = s_n[0], ny = s_n[1];
     unsigned short *start = reinterpret_cast<unsigned short *>(reg + gl.start);
     unsigned short *ent = reinterpret_cast<unsigned short *>(reg + gl.ent);
     int *rng = reinterpret_cast<int *>(reg + gl.rng);
     // cell ranges (8 bits each: x0 x1 y0 y1) and counts
     for (int j = tid; j < ns; j += T) {
-        const double r = radius(j) + 1e-3 * h;
-        const double cx = p.center[j * dims] - org[0], cy = p.center[j * dims + 1] - org[1];
-        const int ax0 = max(0, int(floor((cx - r - x0) * ih))), ax1 = min(nx - 1, int(floor((cx + r - x0) * ih)));
-        const int ay0 = max(0, int(floor((cy - r - y0) * ih))), ay1 = min(ny - 1, int(floor((cy + r - y0) * ih)));
+        float cx = 0.f, cy = 0.f;
+        const float r = geometry(j, cx, cy) + 1e-3f * h;
+        const int ax0 = max(0, int(floorf((cx - r - x0) * ih))), ax1 = min(nx - 1, int(floorf((cx + r - x0) * ih)));
+        const int ay0 = max(0, int(floorf((cy - r - y0) * ih))), ay1 = min(ny - 1, int(floorf((cy + r - y0) * ih)));
         rng[j] = ax0 | (ax1 << 8) | (ay0 << 16) | (ay1 << 24);
         for (int cy2 = ay0; cy2 <= ay1; ++cy2)
             for (int cx2 = ax0; cx2 <= ax1; ++cx2) atomicAdd(&s_cnt[cy2 * nx + cx2], 1);
@@ -143,17 +159,17 @@ __device__ void build_grid(const SetupParams &p, const double *org, float *reg, 
     const int nc = nx * ny;
     if (tid < 32) {
         const int per = (nc + 31) / 32, b0 = tid * per;
-        int sum = 0, big = 0;
+        int sum = 0, most = 0;
         for (int c = b0; c < min(nc, b0 + per); ++c) {
             sum += s_cnt[c];
-            big = max(big, s_cnt[c]);
+            most = max(most, s_cnt[c]);
         }
         int inc = sum;
         for (int off = 1; off < 32; off <<= 1) {
             const int o = __shfl_up_sync(0xffffffffu, inc, off);
             if (tid >= off) inc += o;
         }
-        for (int off = 16; off > 0; off >>= 1) big = max(big, __shfl_xor_sync(0xffffffffu, big, off));
+        for (int off = 16; off > 0; off >>= 1) most = max(most, __shfl_xor_sync(0xffffffffu, most, off));
         int run = inc - sum;
         for (int c = b0; c < min(nc, b0 + per); ++c) {
             const int n = s_cnt[c];
@@ -163,7 +179,7 @@ __device__ void build_grid(const SetupParams &p, const double *org, float *reg, 
         }
         if (tid == 31) {
             start[nc] = static_cast<unsigned short>(inc);
-            s_n[2] = big;
+            s_n[2] = most;
             ireg[6] = inc;
         }
     }
@@ -411,7 +427,7 @@ __device__ void setup_body(const SetupParams &p, double *tab64)
     __syncthreads();
     // (8) working-precision copy of the tables; (9) the static-obstacle grid
     if (!p.real_is_double) {
-        build_grid(p, s_org, reinterpret_cast<float *>(p.tab) + lay.grid, eps);
+        build_grid(p, s_org, reinterpret_cast<float *>(p.tab) + lay.grid, float(eps));
         if (p.shape_ready)
             write_tables<float>(p, tab64, lay.base, lay.total);  // basis and packed basis unchanged
         else
