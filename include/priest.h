@@ -297,8 +297,10 @@ priest_status priest_plan_batch(priest_ctx *ctx, int n, priest_loaded *const *pr
 
 /* Batched solve through host buffers (Alg. 1 for every problem, in the shared
  * launches of priest_plan_batch): probs (n host structs, obstacle arrays
- * host memory), z[i] = L x N_i x D standard normals of problem i (host; the
- * copies run as DMA when the caller's buffers are pinned), out[i] = problem
+ * host memory), z[i] = L x N_i x D standard normals of problem i (host;
+ * from page-locked buffers the draws are read in place by a transfer kernel,
+ * those of the second and later CEM iterations while the first projection
+ * runs; pageable buffers are copied by DMA first), out[i] = problem
  * i's result (host; xi_best, resid, cost, c_aug, best_index and the final
  * mean; latency_ms 0).  Problems must share dims, degree and bc_final_mask;
  * every problem starts from the default distribution (straight-line mean,

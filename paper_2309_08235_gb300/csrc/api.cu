@@ -45,6 +45,16 @@ struct BatchPlan {
     std::vector<cudaEvent_t> ev;    // 2 L events recorded around the projection launches of the graph
     std::vector<cudaGraphNode_t> ev_nodes;  // their record nodes, in the same order
     bool ev_swapped = false;        // the nodes point at events of the context's pool
+    cudaEvent_t zwait = nullptr;    // not owned: recorded once the draws of CEM iterations >= 1 are
+                                    // in place (host-buffer solves); the second projection waits on it
+};
+
+// One piece of a transfer for xfer_kernel: count doubles from src to dst
+// (either may be the device view of pinned host memory).
+struct XferChunk {
+    const double *src;
+    double *dst;
+    long long count;
 };
 
 // Resident problems, draws and results of the batched solve through host
@@ -57,8 +67,14 @@ struct HostBatch {
     double *odev = nullptr;                 // results, ostride doubles per problem
     size_t ostride = 0;
     char *stage = nullptr;                  // pinned: obstacle spans, then results, then means
+    char *stage_dev = nullptr;              // the stage's device view (nullptr: copies instead)
     size_t out_off = 0, mu_off = 0;
     std::vector<size_t> z_off, ob_off, ob_bytes;
+    XferChunk *xin = nullptr, *xout = nullptr;  // pinned chunk tables of the two gathers
+    XferChunk *xin_dev = nullptr, *xout_dev = nullptr, *xside = nullptr, *xside_dev = nullptr;
+    size_t xin_cap = 0, xout_cap = 0, xside_cap = 0;
+    cudaStream_t cstream = nullptr;         // transfer of the draws of CEM iterations >= 1, beside the solve
+    cudaEvent_t zev = nullptr;              // recorded on cstream after those copies
 };
 }  // namespace priest
 
@@ -1239,7 +1255,7 @@ struct BatchDesc {
 
 template <typename Real>
 priest_status batch_describe(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
-                             double *const *out, BatchDesc<Real> &d)
+                             double *const *out, BatchDesc<Real> &d, bool with_items = true)
 {
     const int L = ctx->cfg.cem_iters;
     const Shape &s0 = probs[0]->sh;
@@ -1276,7 +1292,9 @@ priest_status batch_describe(priest_ctx *ctx, int n, priest_loaded *const *probs
             d.params[size_t(l) * n + i] = p;
         }
         const double cost = double(sh.n_p) * (double(sh.n_obs) + 12.0);
-        for (int s0i = 0; s0i < sh.N; s0i += t.S) items.push_back({cost * std::min(t.S, sh.N - s0i), make_int2(i, s0i)});
+        if (with_items)
+            for (int s0i = 0; s0i < sh.N; s0i += t.S)
+                items.push_back({cost * std::min(t.S, sh.N - s0i), make_int2(i, s0i)});
         SetupParams sp = setup_params(ctx, h, true, ctx->d_status);
         sp.default_mu = 1;
         sp.default_cov = 1;
@@ -1323,7 +1341,7 @@ BatchOffsets batch_offsets(const BatchDesc<Real> &d, int n, int L)
 }
 
 template <typename Real>
-priest_status batch_upload(priest_ctx *ctx, BatchPlan *b, const BatchDesc<Real> &d)
+priest_status batch_upload(priest_ctx *ctx, BatchPlan *b, const BatchDesc<Real> &d, bool with_items = true)
 {
     cudaStream_t st = ctx->stream;
     PRIEST_CUDA(ctx, cudaMemcpyAsync(b->params_dev, d.params.data(), sizeof(ProjParams<Real>) * d.params.size(),
@@ -1333,8 +1351,9 @@ priest_status batch_upload(priest_ctx *ctx, BatchPlan *b, const BatchDesc<Real> 
     PRIEST_CUDA(ctx, cudaMemcpyAsync(b->setup_dev_ready, d.setups_ready.data(), sizeof(SetupParams) * b->n,
                                      cudaMemcpyHostToDevice, st));
     PRIEST_CUDA(ctx, cudaMemcpyAsync(b->cem_dev, d.cem.data(), sizeof(CemArgs) * b->n, cudaMemcpyHostToDevice, st));
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(b->items_dev, d.items.data(), sizeof(int2) * d.items.size(),
-                                     cudaMemcpyHostToDevice, st));
+    if (with_items)
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(b->items_dev, d.items.data(), sizeof(int2) * d.items.size(),
+                                         cudaMemcpyHostToDevice, st));
     // the host vectors are released when the caller returns
     PRIEST_CUDA(ctx, cudaStreamSynchronize(st));
     return PRIEST_OK;
@@ -1412,23 +1431,25 @@ priest_status batch_build(priest_ctx *ctx, int n, priest_loaded *const *probs, c
 }
 
 // New problem data (obstacles, boundary values, bounds) behind the same
-// handles: the descriptors are formed again and uploaded in place, so the
-// recorded graph stays valid.  Returns false when the launch layout changed
-// (items, kernel, shared memory), which needs a new plan.
+// handles, every problem keeping its layout (the host-buffer path checks its
+// layout key first): the per-problem descriptors are formed again and
+// uploaded in place, the work items stay, and the recorded graph stays
+// valid.  Returns false when the launch layout changed (kernel, shared
+// memory), which needs a new plan.
 template <typename Real>
 bool batch_refresh(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
                    double *const *out, BatchPlan *b, priest_status *st)
 {
+    // the caller keeps every problem's layout (sample count, shape class and
+    // so tiling), so the work items are the recorded ones: only the
+    // per-problem parameters are formed again
     BatchDesc<Real> d;
-    *st = batch_describe<Real>(ctx, n, probs, z, out, d);
+    *st = batch_describe<Real>(ctx, n, probs, z, out, d, false);
     if (*st != PRIEST_OK) return false;
     if (d.kind != b->kind || d.R != b->R || d.smem_proj != b->smem_proj || d.smem_setup > b->smem_setup ||
-        d.smem_select > b->smem_select || d.smem_refit > b->smem_refit || d.D_max != b->D_max ||
-        d.items.size() != b->items_host.size())
+        d.smem_select > b->smem_select || d.smem_refit > b->smem_refit || d.D_max != b->D_max)
         return false;
-    for (size_t k = 0; k < d.items.size(); ++k)
-        if (d.items[k].x != b->items_host[k].x || d.items[k].y != b->items_host[k].y) return false;
-    *st = batch_upload<Real>(ctx, b, d);
+    *st = batch_upload<Real>(ctx, b, d, false);
     return *st == PRIEST_OK;
 }
 
@@ -1447,6 +1468,8 @@ priest_status batch_enqueue(priest_ctx *ctx, BatchPlan *b, bool shape_ready, cud
     const bool mark = capture && int(b->ev.size()) == 2 * b->L;
     for (int l = 0; l < b->L && e == cudaSuccess; ++l) {
         std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (l == 1 && b->zwait) e = cudaStreamWaitEvent(st, b->zwait, capture ? cudaEventWaitExternal : 0);
+        if (e != cudaSuccess) break;
         if (mark) {
             e = cudaEventRecordWithFlags(b->ev[2 * l], st, cudaEventRecordExternal);
         } else if (!capture && ctx->profile && st == ctx->stream) {
@@ -1514,7 +1537,7 @@ std::vector<uintptr_t> batch_key(int n, priest_loaded *const *probs, const doubl
 // batch_refresh); otherwise a recorded plan is replayed as it is.
 template <typename Real>
 priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, const double *const *z,
-                         double *const *out, bool refresh = false)
+                         double *const *out, bool refresh = false, cudaEvent_t zwait = nullptr)
 {
     const std::vector<uintptr_t> key = batch_key(n, probs, z, out);
     auto it = ctx->batches.find(key);
@@ -1529,6 +1552,7 @@ priest_status plan_batch(priest_ctx *ctx, int n, priest_loaded *const *probs, co
         ctx->batches.erase(it);
     }
     BatchPlan *b = new BatchPlan();
+    b->zwait = zwait;
     priest_status s = batch_build<Real>(ctx, n, probs, z, out, b);
     if (s != PRIEST_OK) {
         free_batch(b);
@@ -1736,6 +1760,90 @@ std::vector<double> host_layout_key(const Shape &sh)
             double(sh.N), double(sh.n_proj), double(sh.n_elite), double(sh.use_bounds), sh.horizon};
 }
 
+// ---- transfers of the host-buffer batched solve: every piece of one
+//      direction in a single launch instead of one copy call per problem
+constexpr int kXferThreads = 256;
+constexpr long long kXferChunk = 32768;  // doubles per CTA (256 KB), even: chunks keep 16-byte alignment
+constexpr int kSideCtas = 16;            // CTAs of a transfer that runs beside the solve
+
+// Chunks n_chunks apart per CTA (one each when the grid covers them), plain
+// loads and stores (16 bytes when both ends are 16-byte aligned, four in
+// flight per thread), so pinned host memory is read or written over the host
+// link directly.
+__global__ void __launch_bounds__(kXferThreads) xfer_kernel(const XferChunk *chunks, int n_chunks)
+{
+    const int t = threadIdx.x;
+    for (int k = blockIdx.x; k < n_chunks; k += gridDim.x) {
+        const XferChunk c = chunks[k];
+        if (((reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst)) & 15) == 0) {
+            const long long n2 = c.count >> 1;
+            const double2 *src = reinterpret_cast<const double2 *>(c.src);
+            double2 *dst = reinterpret_cast<double2 *>(c.dst);
+            long long i = t;
+            for (; i + 3 * kXferThreads < n2; i += 4 * kXferThreads) {
+                const double2 a = src[i], b = src[i + kXferThreads], e = src[i + 2 * kXferThreads],
+                              f = src[i + 3 * kXferThreads];
+                dst[i] = a;
+                dst[i + kXferThreads] = b;
+                dst[i + 2 * kXferThreads] = e;
+                dst[i + 3 * kXferThreads] = f;
+            }
+            for (; i < n2; i += kXferThreads) dst[i] = src[i];
+            if (t == 0 && (c.count & 1)) c.dst[c.count - 1] = c.src[c.count - 1];
+        } else {
+            for (long long i = t; i < c.count; i += kXferThreads) c.dst[i] = c.src[i];
+        }
+    }
+}
+
+// The device view of host memory a kernel may access: page-locked, mapped
+// memory only (cudaMallocHost, cudaHostAlloc, cudaHostRegister); nullptr for
+// pageable memory, which is then copied by DMA instead.
+double *device_view(const void *p)
+{
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<double *>(a.devicePointer);
+}
+
+size_t xfer_chunks(size_t count) { return (count + size_t(kXferChunk) - 1) / size_t(kXferChunk); }
+
+void add_xfer(std::vector<XferChunk> &v, const double *src, double *dst, size_t count)
+{
+    for (size_t o = 0; o < count; o += size_t(kXferChunk))
+        v.push_back({src + o, dst + o, (long long)std::min(size_t(kXferChunk), count - o)});
+}
+
+// Writes the chunk list into its pinned table (grown when needed) and
+// launches one transfer over it on st, with at most max_ctas CTAs (0: one
+// per chunk).
+cudaError_t run_xfer(const std::vector<XferChunk> &v, XferChunk *&table, XferChunk *&table_dev, size_t &cap,
+                     cudaStream_t st, int max_ctas = 0)
+{
+    if (v.empty()) return cudaSuccess;
+    if (v.size() > cap) {
+        cudaError_t e = cudaStreamSynchronize(st);  // the old table may still be read
+        if (e != cudaSuccess) return e;
+        if (table) cudaFreeHost(table);
+        table = nullptr;
+        table_dev = nullptr;
+        cap = 0;
+        e = cudaMallocHost(&table, sizeof(XferChunk) * v.size());
+        if (e != cudaSuccess) return e;
+        table_dev = reinterpret_cast<XferChunk *>(device_view(table));
+        if (!table_dev) return cudaErrorInvalidValue;
+        cap = v.size();
+    }
+    std::memcpy(table, v.data(), sizeof(XferChunk) * v.size());
+    const int n = int(v.size());
+    xfer_kernel<<<unsigned(max_ctas > 0 ? std::min(n, max_ctas) : n), kXferThreads, 0, st>>>(table_dev, n);
+    return cudaGetLastError();
+}
+
 void free_host_batch(priest_ctx *ctx)
 {
     HostBatch *hb = ctx->hbatch;
@@ -1757,6 +1865,14 @@ void free_host_batch(priest_ctx *ctx)
     if (hb->zdev) cudaFree(hb->zdev);
     if (hb->odev) cudaFree(hb->odev);
     if (hb->stage) cudaFreeHost(hb->stage);
+    if (hb->xin) cudaFreeHost(hb->xin);
+    if (hb->xout) cudaFreeHost(hb->xout);
+    if (hb->xside) cudaFreeHost(hb->xside);
+    if (hb->cstream) {
+        cudaStreamSynchronize(hb->cstream);
+        cudaStreamDestroy(hb->cstream);
+    }
+    if (hb->zev) cudaEventDestroy(hb->zev);
     delete hb;
     ctx->hbatch = nullptr;
 }
@@ -1808,6 +1924,13 @@ priest_status plan_batch_host(priest_ctx *ctx, int n, const priest_problem *prob
             free_host_batch(ctx);
             return fail(ctx, PRIEST_ERR_NOMEM, "batched solve buffers");
         }
+        hb->stage_dev = reinterpret_cast<char *>(device_view(hb->stage));
+        if (cudaStreamCreateWithFlags(&hb->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&hb->zev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            free_host_batch(ctx);
+            return fail(ctx, PRIEST_ERR_CUDA, "batched solve stream");
+        }
         for (int i = 0; i < n; ++i) {
             priest_loaded *h = nullptr;
             priest_status s = make_loaded(ctx, shapes[i], probs[i].center, probs[i].vel, probs[i].semi, 0, false, st, &h);
@@ -1818,9 +1941,11 @@ priest_status plan_batch_host(priest_ctx *ctx, int n, const priest_problem *prob
             hb->h.push_back(h);
             hb->n = int(hb->h.size());
         }
-    } else {
+    }
+    HostBatch *hb = ctx->hbatch;
+    std::vector<XferChunk> in, out_x, side_x;
+    if (reuse) {
         // same layout: new problem data into the resident buffers
-        HostBatch *hb = ctx->hbatch;
         for (int i = 0; i < n; ++i) {
             priest_loaded *h = hb->h[i];
             const bool ready = h->shape_ready;
@@ -1832,27 +1957,64 @@ priest_status plan_batch_host(priest_ctx *ctx, int n, const priest_problem *prob
             std::memcpy(dst, oc[i].data(), sizeof(double) * oc[i].size());
             std::memcpy(dst + vo, ov[i].data(), sizeof(double) * ov[i].size());
             std::memcpy(dst + so, os[i].data(), sizeof(double) * os[i].size());
-            PRIEST_CUDA(ctx, cudaMemcpyAsync(h->center, dst, hb->ob_bytes[i], cudaMemcpyHostToDevice, st));
+            if (hb->stage_dev)
+                add_xfer(in, reinterpret_cast<const double *>(hb->stage_dev + hb->ob_off[i]), h->center,
+                         hb->ob_bytes[i] / sizeof(double));
+            else
+                PRIEST_CUDA(ctx, cudaMemcpyAsync(h->center, dst, hb->ob_bytes[i], cudaMemcpyHostToDevice, st));
         }
     }
-    HostBatch *hb = ctx->hbatch;
+    // draws: from a pinned buffer, those of the first CEM iteration are read
+    // in place by the transfer kernel on the solve stream and the later
+    // iterations' by a narrow transfer (kSideCtas CTAs) on the side stream,
+    // beside the set-up and the first projection (the recorded launches wait
+    // for hb->zev before the second projection; the persistent projection
+    // takes its items from a counter, so the CTAs the transfer holds for a
+    // while cost it nothing but their slots); a pageable buffer is copied
+    // whole by DMA on the solve stream.  Every return from here waits for
+    // the side stream, since the caller may release the draws.
+    struct SideCopies {
+        cudaStream_t s;
+        ~SideCopies() { cudaStreamSynchronize(s); }
+    } side{hb->cstream};
     std::vector<const double *> zp(n);
     std::vector<double *> op(n);
     for (int i = 0; i < n; ++i) {
         double *zd = hb->zdev + hb->z_off[i];
-        PRIEST_CUDA(ctx, cudaMemcpyAsync(zd, z[i], sizeof(double) * size_t(L) * shapes[i].N * D,
-                                         cudaMemcpyHostToDevice, st));
+        const size_t first = size_t(shapes[i].N) * D, cnt = size_t(L) * first;
+        if (const double *zv = device_view(z[i])) {
+            add_xfer(in, zv, zd, first);
+            add_xfer(side_x, zv + first, zd + first, cnt - first);
+        } else {
+            PRIEST_CUDA(ctx, cudaMemcpyAsync(zd, z[i], sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+        }
         zp[i] = zd;
         op[i] = hb->odev + size_t(i) * hb->ostride;
     }
-    priest_status s = plan_batch<Real>(ctx, n, hb->h.data(), zp.data(), op.data(), reuse);
+    PRIEST_CUDA(ctx, run_xfer(side_x, hb->xside, hb->xside_dev, hb->xside_cap, hb->cstream, kSideCtas));
+    if (!side_x.empty()) ctx->launches++;
+    PRIEST_CUDA(ctx, cudaEventRecord(hb->zev, hb->cstream));
+    if (!in.empty()) {
+        PRIEST_CUDA(ctx, run_xfer(in, hb->xin, hb->xin_dev, hb->xin_cap, st));
+        ctx->launches++;
+    }
+    priest_status s = plan_batch<Real>(ctx, n, hb->h.data(), zp.data(), op.data(), reuse, hb->zev);
     if (s != PRIEST_OK) return s;
     double *ho = reinterpret_cast<double *>(hb->stage + hb->out_off);
     double *hm = reinterpret_cast<double *>(hb->stage + hb->mu_off);
-    PRIEST_CUDA(ctx, cudaMemcpyAsync(ho, hb->odev, sizeof(double) * hb->ostride * n, cudaMemcpyDeviceToHost, st));
-    for (int i = 0; i < n; ++i)
-        PRIEST_CUDA(ctx, cudaMemcpyAsync(hm + size_t(i) * D, hb->h[i]->mu, sizeof(double) * D,
-                                         cudaMemcpyDeviceToHost, st));
+    if (hb->stage_dev) {
+        // results and means written into the pinned stage by one transfer
+        add_xfer(out_x, hb->odev, reinterpret_cast<double *>(hb->stage_dev + hb->out_off), hb->ostride * n);
+        for (int i = 0; i < n; ++i)
+            add_xfer(out_x, hb->h[i]->mu, reinterpret_cast<double *>(hb->stage_dev + hb->mu_off) + size_t(i) * D, D);
+        PRIEST_CUDA(ctx, run_xfer(out_x, hb->xout, hb->xout_dev, hb->xout_cap, st));
+        ctx->launches++;
+    } else {
+        PRIEST_CUDA(ctx, cudaMemcpyAsync(ho, hb->odev, sizeof(double) * hb->ostride * n, cudaMemcpyDeviceToHost, st));
+        for (int i = 0; i < n; ++i)
+            PRIEST_CUDA(ctx, cudaMemcpyAsync(hm + size_t(i) * D, hb->h[i]->mu, sizeof(double) * D,
+                                             cudaMemcpyDeviceToHost, st));
+    }
     s = check_status(ctx, ctx->d_status, st);
     for (int i = 0; i < n; ++i) {
         fill_result(shapes[i], ho + size_t(i) * hb->ostride, hm + size_t(i) * D, &out[i]);

@@ -384,13 +384,28 @@ def priest_plan_batch(ctx, handles, z_ptrs, out_ptrs):
 
 
 def priest_plan_batch_host(ctx, problems, z_list, results):
-    """Batched solve through host buffers.  problems: priest_problem structs;
-    z_list: host float64 arrays (L x N_i x D, pinned or pageable); results: a
-    ctypes array of priest_result (len(problems)), written."""
+    """Batched solve through host buffers.  problems: priest_problem structs,
+    or a ctypes array of them (passed as is); z_list: host float64 arrays
+    (L x N_i x D, pinned or pageable) or their addresses, or a ctypes array of
+    c_void_p (passed as is); results: a ctypes array of priest_result
+    (len(problems)), written.  A caller repeating a batch can keep the two
+    ctypes arrays (priest_problem_array, pointer_array) and skip rebuilding
+    them on every call."""
     n = len(problems)
-    parr = (priest_problem * n)(*problems)
-    zs = (C.c_void_p * n)(*[z.ctypes.data if hasattr(z, "ctypes") else int(z) for z in z_list])
+    parr = problems if isinstance(problems, C.Array) else priest_problem_array(problems)
+    zs = z_list if isinstance(z_list, C.Array) else pointer_array(z_list)
     return _check(ctx, lib().priest_plan_batch_host(ctx, n, parr, zs, results))
+
+
+def priest_problem_array(problems):
+    """A ctypes array of the given priest_problem structs."""
+    return (priest_problem * len(problems))(*problems)
+
+
+def pointer_array(arrays):
+    """A ctypes array of the host addresses of numpy arrays (or ints)."""
+    return (C.c_void_p * len(arrays))(*[a.__array_interface__["data"][0] if hasattr(a, "__array_interface__")
+                                         else int(a) for a in arrays])
 
 
 def priest_project_batch(ctx, handles, rows, xi_ptrs, lam_ptrs, xb_ptrs, r_ptrs, c1_ptrs):

@@ -235,6 +235,52 @@ def test_plan_batch_host_after_tuned_device_batch(P, oracle):
             P.priest_unload(ctx.h, h)
 
 
+@pytest.mark.parametrize("mode", ["pinned", "mixed"])
+def test_plan_batch_host_pinned_draws(P, oracle, mode):
+    """Draws in page-locked host memory are read in place by the transfer
+    kernel (16-byte aligned buffers, buffers at an 8-byte offset, and, in
+    "mixed", pageable ones copied by DMA beside them): the answers equal
+    those of pageable draws bit for bit, on the first call and on a replay."""
+    import torch
+
+    probs = uneven_problems(dims=2, n=5)
+    p0, c0 = probs[0]
+    L = c0["cem_iters"]
+    zs = [W.normals(700 + i, (L, cem["n_samples"], 22)) for i, (p, cem) in enumerate(probs)]
+    keep_t = []
+
+    def pinned(z, shift):
+        t = torch.empty(z.size + shift, dtype=torch.float64).pin_memory()
+        t[shift:] = torch.from_numpy(z.ravel())
+        keep_t.append(t)
+        return t.data_ptr() + 8 * shift
+
+    if mode == "pinned":
+        zp = [pinned(z, 0) for z in zs]
+    else:
+        zp = [pinned(z, 1) if i % 2 == 0 else z for i, z in enumerate(zs)]
+    structs, keep = [], []
+    for p, cem in probs:
+        s, k = P.make_problem(p, cem, per_problem_shape=True)
+        structs.append(s)
+        keep.append(k)
+
+    def call(ctx, z_list):
+        res = (P.priest_result * len(probs))()
+        P.priest_plan_batch_host(ctx.h, structs, z_list, res)
+        return [P.result_dict(res[i]) for i in range(len(probs))]
+
+    with P.Context(p0, c0, precision=P.PRIEST_FP32, autotune=0) as ctx:
+        want = call(ctx, zs)
+        got = [call(ctx, zp), call(ctx, zp)]
+    for g in got:
+        for w, x in zip(want, g):
+            assert x["status"] == 0 and x["best_index"] == w["best_index"]
+            np.testing.assert_array_equal(x["best"], w["best"])
+            np.testing.assert_array_equal(x["mu"], w["mu"])
+            assert x["c_aug"] == w["c_aug"]
+
+
 def test_project_batch_edge_cases(P, oracle):
     """priest_project_batch with a problem of zero rows among others, no
     multiplier lists at all, a single-row problem, and rows beyond a loaded
