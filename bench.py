@@ -399,7 +399,9 @@ def measure_single(args, name, steps, warmup, precision="fp32", plain_steps=0, e
     achieved = flops_launch / (avg_proj_ms / 1e3) / 1e12
     kname = {0: "project_kernel (FP32 chunked projection)", 1: "pts_kernel (FP32 point-owner projection)",
              2: "project_tc_kernel (tcgen05 pair tests)"}.get(kind, "projection kernel")
-    traffic = stored_profile("pts_kernel_bytes_per_launch") if (name == "clutter2d" and kind == 1) else None
+    # the committed ncu figures of this workload's point-owner launch, where one was captured
+    prof = {"clutter2d": "pts_kernel", "ellipsoid3d": "pts_kernel_3d"}.get(name) if kind == 1 else None
+    traffic = stored_profile(f"{prof}_bytes_per_launch") if prof else None
     traffic = None if traffic is None else int(traffic)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"{kname}, {p['dims']}-D", "avg_launch_ms": avg_proj_ms,
@@ -411,8 +413,8 @@ def measure_single(args, name, steps, warmup, precision="fp32", plain_steps=0, e
                                  "in this run") if traffic else None}
     if kind == 1:
         roofline["note"] = SCREEN_NOTE
-        if name == "clutter2d":
-            roofline["executed"] = executed("pts_kernel")
+        if prof:
+            roofline["executed"] = executed(prof)
     if clocks.get("sm_mhz"):
         roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(n_sm, clocks["sm_mhz"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,

@@ -144,12 +144,15 @@ __device__ void build_grid(const SetupParams &p, const double *org, float *reg, 
     unsigned short *start = reinterpret_cast<unsigned short *>(reg + gl.start);
     unsigned short *ent = reinterpret_cast<unsigned short *>(reg + gl.ent);
     int *rng = reinterpret_cast<int *>(reg + gl.rng);
-    // cell ranges (8 bits each: x0 x1 y0 y1) and counts
+    // cell ranges (8 bits each: x0 x1 y0 y1, every bound clamped into the
+    // grid, so the fill pass below decodes exactly the ranges counted here)
+    // and counts
+    auto cell = [](float u, int n) { return min(max(int(floorf(u)), 0), n - 1); };
     for (int j = tid; j < ns; j += T) {
         float cx = 0.f, cy = 0.f;
         const float r = geometry(j, cx, cy) + 1e-3f * h;
-        const int ax0 = max(0, int(floorf((cx - r - x0) * ih))), ax1 = min(nx - 1, int(floorf((cx + r - x0) * ih)));
-        const int ay0 = max(0, int(floorf((cy - r - y0) * ih))), ay1 = min(ny - 1, int(floorf((cy + r - y0) * ih)));
+        const int ax0 = cell((cx - r - x0) * ih, nx), ax1 = cell((cx + r - x0) * ih, nx);
+        const int ay0 = cell((cy - r - y0) * ih, ny), ay1 = cell((cy + r - y0) * ih, ny);
         rng[j] = ax0 | (ax1 << 8) | (ay0 << 16) | (ay1 << 24);
         for (int cy2 = ay0; cy2 <= ay1; ++cy2)
             for (int cx2 = ax0; cx2 <= ax1; ++cx2) atomicAdd(&s_cnt[cy2 * nx + cx2], 1);
