@@ -193,11 +193,12 @@ def stored_profile(key):
 
 
 SCREEN_NOTE = ("achieved counts the scope table's per-unit work: the direct polar test of every (point, obstacle) pair "
-               "in every iteration.  The point-owner kernel screens every pair only when it rebuilds its neighbour "
-               "lists (the first iteration, and after a point of the CTA moved 7/8 of the list margin) and otherwise "
-               "tests only the listed pairs exactly; the pairs left out are provably inactive (zero residual rows), "
-               "so its results equal full screening and achieved can exceed the FP32 peak.  'executed' holds the "
-               "kernel's own issue and FMA-pipe utilisation from the committed ncu capture.")
+               "in every iteration.  The point-owner kernel tests only each point's listed pairs exactly; it screens "
+               "for its lists only when it rebuilds them (the first iteration, and after a point of the CTA moved 7/8 "
+               "of the list margin), then the static obstacles of the point's grid cell and every moving one; the "
+               "pairs left out are provably inactive (zero residual rows), so its results equal full screening "
+               "(bitwise) and achieved can exceed the FP32 peak.  'executed' holds the kernel's own issue and "
+               "FMA-pipe utilisation from the committed ncu capture.")
 
 
 def executed(prefix):

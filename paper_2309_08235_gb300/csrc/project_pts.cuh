@@ -797,7 +797,7 @@ __device__ void pts_body(const ProjParams<float> &p, int s0)
                                 : 0.f;
             }
         }
-        // ---- B: every obstacle against the thread's points
+        // ---- B: the thread's points against their listed obstacles (lists rebuilt when needed)
         float so[R][DIMS];
         {
             detail::PackedPoints<DIMS, R> P;
