@@ -136,11 +136,21 @@ __device__ void build_grid(const SetupParams &p, const double *org, float *reg, 
             s_n[0] = min(gs, max(1, int(ceilf((v[2] - x0) / h + 0.01f))));
             s_n[1] = min(gs, max(1, int(ceilf((v[3] - y0) / h + 0.01f))));
             s_n[2] = 0;
+            // coordinates beyond FP32's range: no grid (the quads screen every static obstacle)
+            if (!(h > 0.f) || !isfinite(h) || !isfinite(s_geo[3]) || !isfinite(x0) || !isfinite(y0) ||
+                !isfinite(v[2] - x0) || !isfinite(v[3] - y0))
+                s_n[0] = 0;
         }
     }
     __syncthreads();
     const float x0 = s_geo[0], y0 = s_geo[1], h = s_geo[2], ih = s_geo[3];
     const int nx = s_n[0], ny = s_n[1];
+    if (nx == 0) {
+        if (tid == 0) {
+            for (int i = 0; i < 8; ++i) ireg[i] = 0;
+        }
+        return;
+    }
     unsigned short *start = reinterpret_cast<unsigned short *>(reg + gl.start);
     unsigned short *ent = reinterpret_cast<unsigned short *>(reg + gl.ent);
     int *rng = reinterpret_cast<int *>(reg + gl.rng);
