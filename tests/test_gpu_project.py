@@ -40,6 +40,39 @@ def test_fp64_check_mode_matches_oracle(P, oracle, dims, bounds, mask, n_dyn):
     assert np.count_nonzero(r_o) > 10  # the scene is active
 
 
+@pytest.mark.parametrize("dims", [2, 3])
+def test_fp64_converged_projection_matches_oracle(P, oracle, dims):
+    """Thousands of iterations on the scenes of the oracle's converged-
+    projection pin (fixed points on the constraint boundary: obstacle contact,
+    a moving circle, an active acceleration bound): the FP64 check mode
+    reaches the oracle's fixed points, and its own output satisfies the
+    fixed-point identity xi_bar_F = xi_F + lambda_F."""
+    from paper_2309_08235_gb300 import workloads as W
+
+    if dims == 2:
+        centre = np.array([[4.0, 0.4], [8.0, -0.5], [12.0, 0.3], [6.0, 3.0]])
+        vel = np.array([[0.0, 0.0], [0.0, 0.0], [0.0, 0.0], [0.3, -0.6]])
+        a = np.array([0.9, 0.8, 0.9, 0.6])
+        p = W.problem(2, 50, 8.0, np.zeros(2), np.array([16.0, 0.0]), centre, vel, np.stack([a, a], 1), 3.0, 2.0,
+                      seed=1)
+        xi = oracle.default_mean(p)[None] + np.random.default_rng(5).normal(0.0, 0.4, (6, 22))
+        K = 8000
+    else:
+        centre = np.array([[4.0, 0.3, 0.8], [8.0, -0.4, 1.2], [10.0, 0.2, 1.8]])
+        semi = np.array([[0.9, 0.6], [0.8, 1.0], [0.7, 0.5]])
+        p = W.problem(3, 50, 8.0, np.zeros(3), np.array([14.0, 0.0, 2.0]), centre, None, semi, 3.0, 1.6, seed=1)
+        xi = oracle.default_mean(p)[None] + np.random.default_rng(7).normal(0.0, 0.4, (4, 33))
+        K = 2000
+    (xb, lam, r, c1), (xb_o, lam_o, r_o, c1_o) = run_both(P, oracle, p, xi, K, P.PRIEST_FP64_CHECK)
+    s = scale_of(p)
+    assert rel_err(xb, xb_o, s) < TOL_FP64
+    assert rel_err(lam, lam_o, 1.0) < TOL_FP64
+    assert np.abs(r).max() < 1e-9 and np.abs(r_o).max() < 1e-9  # feasible fixed points
+    nv = 11
+    free = np.concatenate([ax * nv + np.r_[3:nv - 3] for ax in range(dims)])
+    assert np.abs(xb[:, free] - xi[:, free] - lam[:, free]).max() < 1e-10 * s
+
+
 def test_k0_is_equality_projection(P, oracle):
     p = scene(dims=3, mask=7)
     xi = samples(oracle, p, 50, seed=1)
