@@ -1865,13 +1865,13 @@ void free_host_batch(priest_ctx *ctx)
     if (hb->zdev) cudaFree(hb->zdev);
     if (hb->odev) cudaFree(hb->odev);
     if (hb->stage) cudaFreeHost(hb->stage);
+    if (hb->cstream) {
+        cudaStreamSynchronize(hb->cstream);  // before its chunk table goes
+        cudaStreamDestroy(hb->cstream);
+    }
     if (hb->xin) cudaFreeHost(hb->xin);
     if (hb->xout) cudaFreeHost(hb->xout);
     if (hb->xside) cudaFreeHost(hb->xside);
-    if (hb->cstream) {
-        cudaStreamSynchronize(hb->cstream);
-        cudaStreamDestroy(hb->cstream);
-    }
     if (hb->zev) cudaEventDestroy(hb->zev);
     delete hb;
     ctx->hbatch = nullptr;
