@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <utility>
 #include <vector>
@@ -42,14 +43,24 @@ struct Shape {
 
 // Neighbour-list margin of a problem: 3/4 of the mean of the obstacles'
 // smallest semi-axes (b_j = a_j in 2-D), 0 without obstacles (center:
-// n_obs x dims, semi: n_obs x 2).  Any positive margin gives the same
-// results; this one balanced list length against rebuild frequency on the
-// measured workloads (a margin of 0.5 to 1 mean semi-axis changed the
-// batched rate by under 2 %).  In dense scenes (64 obstacles or more) it is
+// n_obs x dims, semi: n_obs x 2).  Any positive margin gives bitwise the
+// same results; this one balanced list length against rebuild frequency on
+// the measured workloads (a margin of 0.5 to 1 mean semi-axis changed the
+// batched rate by under 2 %).  PRIEST_LIST_MARGIN=<multiple> replaces the
+// 3/4 (comparisons).  In dense scenes (64 obstacles or more) it is
 // capped so that a ball of radius (mean largest semi-axis + margin) holds
 // about two obstacle centres on average at the density of the centres'
 // bounding box, keeping the lists short of overflow; it stays at least a
 // tenth of the mean semi-axis.
+inline double list_margin_scale()
+{
+    const char *v = getenv("PRIEST_LIST_MARGIN");
+    if (!v) return 0.75;
+    char *end = nullptr;
+    const double x = strtod(v, &end);
+    return (end != v && x > 0.0 && x < 1e6) ? x : 0.75;
+}
+
 inline double list_margin(int dims, int n_obs, const double *center, const double *semi)
 {
     if (n_obs <= 0) return 0.0;
@@ -66,7 +77,7 @@ inline double list_margin(int dims, int n_obs, const double *center, const doubl
     }
     s /= n_obs;
     big /= n_obs;
-    double delta = 0.75 * s;
+    double delta = list_margin_scale() * s;
     if (n_obs >= 64) {
         double vol = 1.0;
         for (int ax = 0; ax < dims; ++ax) vol *= (hi[ax] - lo[ax]) + 2.0 * big;

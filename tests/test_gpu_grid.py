@@ -112,3 +112,22 @@ def test_grid_lists_equal_full_screening(P, oracle, name):
     assert rel_err(r[idx], r_o, 1.0) < TOL_FP32
     assert rel_err(c1[idx], c1_o, max(1.0, np.abs(c1_o).max())) < TOL_FP32
     assert np.count_nonzero(r_o > 1e-6) > 0  # obstacles are active
+
+
+def test_list_margin_does_not_change_results(P, oracle):
+    """Any positive list margin gives bitwise the same outputs: the lists hold
+    every obstacle that can be active while a point stays within 7/8 of the
+    margin of its rebuild position.  0.35, 0.75 (the default) and 1.5 mean
+    semi-axes (PRIEST_LIST_MARGIN) on the 2-D clutter scene: the smallest
+    rebuilds most often, the largest keeps the longest lists."""
+    p = W.scene_clutter_2d(seed=3, n_static=90, n_dyn=10, n_p=100)
+    xi = oracle.default_mean(p) + 2.0 * W.normals(77, (300, 22))
+    lam0 = np.random.default_rng(8).normal(0.0, 0.1, xi.shape)
+    outs = []
+    for m in ("0.35", "0.75", "1.5"):
+        out, kind, grid = run(P, p, xi, 40, lam0, {"PRIEST_LIST_MARGIN": m})
+        assert kind == 1 and grid[0] > 0
+        outs.append(out)
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):  # xi_bar, lambda, r, c_1
+            np.testing.assert_array_equal(x, y)
