@@ -281,6 +281,70 @@ def test_plan_batch_host_pinned_draws(P, oracle, mode):
             assert x["c_aug"] == w["c_aug"]
 
 
+def project_batch_numpy(P, oracle, probs, K, env, **over):
+    """priest_project_batch on the given problems with env set; returns
+    (xi_bar, lambda or None, r, c_1) per problem as host arrays and the kernel
+    kind of the launch."""
+    import os
+
+    import torch
+
+    dev = torch.device("cuda", 0)
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        p0, n0 = probs[0]
+        with P.Context(p0, W.cem_settings(n0, K, 1), precision=P.PRIEST_FP32, **over) as ctx:
+            handles, keep, rows, lams, outs = [], [], [], [], []
+            for i, (p, N) in enumerate(probs):
+                prob, kp = P.make_problem(p, W.cem_settings(N, K, 1), per_problem_shape=True)
+                keep.append(kp)
+                handles.append(P.priest_load(ctx.h, prob))
+                xi = oracle.default_mean(p) + 2.0 * W.normals(700 + i, (N, 22))
+                lam = 0.3 * W.normals(800 + i, (N, 22)) if i % 3 == 0 else None
+                rows.append(N)
+                lams.append(None if lam is None else torch.from_numpy(lam).to(dev))
+                outs.append((torch.from_numpy(xi).to(dev), torch.zeros((N, 22), dtype=torch.float64, device=dev),
+                             torch.zeros((N,), dtype=torch.float64, device=dev),
+                             torch.zeros((N,), dtype=torch.float64, device=dev)))
+            P.priest_project_batch(ctx.h, handles, rows, [o[0].data_ptr() for o in outs],
+                                   [0 if l is None else l.data_ptr() for l in lams], [o[1].data_ptr() for o in outs],
+                                   [o[2].data_ptr() for o in outs], [o[3].data_ptr() for o in outs])
+            P.priest_sync(ctx.h)
+            kind = P.priest_last_kernel(ctx.h)
+            for h in handles:
+                P.priest_unload(ctx.h, h)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return [(o[1].cpu().numpy(), None if l is None else l.cpu().numpy(), o[2].cpu().numpy(), o[3].cpu().numpy())
+            for o, l in zip(outs, lams)], kind
+
+
+def test_project_batch_lists_equal_full_screening(P, oracle):
+    """The persistent point-owner launch (its own compilation of the kernel
+    source, at 128 registers) gives bitwise the same outputs with its
+    neighbour lists and grid, with the lists rebuilt from every static
+    obstacle (PRIEST_LIST_GRID=0), and with every obstacle screened in every
+    iteration (PRIEST_NEIGHBOUR_LISTS=0), on problems of the batched workload
+    (cost-model tilings, so the three launches share their layout)."""
+    every = W.batched_problems(64)
+    probs = [every[i] for i in BATCH_PICK[:4]]
+    a, ka = project_batch_numpy(P, oracle, probs, 60, {}, autotune=0)
+    b, kb = project_batch_numpy(P, oracle, probs, 60, {"PRIEST_LIST_GRID": "0"}, autotune=0)
+    c, kc = project_batch_numpy(P, oracle, probs, 60, {"PRIEST_NEIGHBOUR_LISTS": "0"}, autotune=0)
+    assert ka == kb == kc == 1
+    for x, y, z in zip(a, b, c):
+        for u, v, w in zip(x, y, z):  # xi_bar, lambda, r, c_1
+            if u is None:
+                continue
+            np.testing.assert_array_equal(u, v)
+            np.testing.assert_array_equal(u, w)
+
+
 def test_project_batch_edge_cases(P, oracle):
     """priest_project_batch with a problem of zero rows among others, no
     multiplier lists at all, a single-row problem, and rows beyond a loaded
